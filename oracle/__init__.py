@@ -1,0 +1,202 @@
+"""ctypes binding of the CCZ4 oracle (plain FP64 C restatement of the paper).
+
+TEST INFRASTRUCTURE ONLY. The test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only users of this package. The CUDA
+path neither imports nor links it, and the product raises when its own CUDA
+library is missing instead of falling back here.
+
+Array layouts (NumPy, float64, C order):
+  U      (25, n_patches, p, p, p)     interior points, x fastest
+  G      (25, n_ghost)                evolved Sommerfeld ghost cells
+  tiles  (25, n_patches, p+6, p+6, p+6)
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NV = 25
+HALO = 3
+BC = {"periodic": 0, "copy": 1, "sommerfeld": 2}
+SLICING = {"harmonic": 0, "1+log": 1}
+SHIFT = {"zero": 0, "gamma-driver": 1}
+
+_dbl_p = ctypes.POINTER(ctypes.c_double)
+_lng_p = ctypes.POINTER(ctypes.c_long)
+_int_p = ctypes.POINTER(ctypes.c_int)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("kappa1", "kappa2", "kappa3", "e", "c", "tau", "mu", "f", "eta", "s", "K0", "ko_eps")] + [
+        ("slicing", ctypes.c_int), ("shift", ctypes.c_int), ("somm_speed", ctypes.c_double * NV)]
+
+
+def make_params(kappa1=1.0, kappa2=0.0, kappa3=0.0, e=1.0, c=1.0, tau=1.0, mu=0.2, f=0.75,
+                eta=2.0, s=1.0, K0=0.0, ko_eps=0.1, slicing="harmonic", shift="zero",
+                somm_speed=1.0):
+    p = Params()
+    for k, v in dict(kappa1=kappa1, kappa2=kappa2, kappa3=kappa3, e=e, c=c, tau=tau, mu=mu, f=f,
+                     eta=eta, s=s, K0=K0, ko_eps=ko_eps).items():
+        setattr(p, k, float(v))
+    p.slicing = SLICING[slicing] if isinstance(slicing, str) else int(slicing)
+    p.shift = SHIFT[shift] if isinstance(shift, str) else int(shift)
+    sp = np.broadcast_to(np.asarray(somm_speed, dtype=np.float64), (NV,))
+    for i in range(NV):
+        p.somm_speed[i] = float(sp[i])
+    return p
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.og_grid_new.restype = ctypes.c_void_p
+        L.og_grid_new.argtypes = [ctypes.c_int] * 5 + [_int_p] + [ctypes.c_double] * 4 + [ctypes.c_int]
+        L.og_grid_free.argtypes = [ctypes.c_void_p]
+        L.og_n_ghost.restype = ctypes.c_long
+        L.og_n_ghost.argtypes = [ctypes.c_void_p]
+        L.og_ghost_coords.argtypes = [ctypes.c_void_p, _int_p]
+        L.og_fill_tiles.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, _dbl_p]
+        L.og_rhs.argtypes = [ctypes.c_void_p, ctypes.POINTER(Params), _dbl_p, _dbl_p, _dbl_p, _dbl_p, _dbl_p]
+        L.og_rk4_step.argtypes = [ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_double, _dbl_p, _dbl_p, _dbl_p]
+        L.og_enforce.argtypes = [ctypes.c_void_p, _dbl_p]
+        L.og_constraints.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, _dbl_p, _dbl_p, _dbl_p]
+        L.og_rhs_points.argtypes = [ctypes.c_void_p, ctypes.POINTER(Params), _dbl_p, _dbl_p,
+                                    ctypes.c_long, _lng_p, _dbl_p]
+        L.og_constraints_points.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, ctypes.c_long, _lng_p, _dbl_p]
+        L.og_point_derivs.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, ctypes.c_long, ctypes.c_double,
+                                      _dbl_p, _dbl_p, _dbl_p]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dbl_p)
+
+
+def _f64(a, shape):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != tuple(shape):
+        a = a.reshape(shape)
+    return a
+
+
+class Grid:
+    """One uniform level of p^3 patches covering np[0] x np[1] x np[2] patch slots."""
+
+    def __init__(self, p, np_, ijk, origin, dx, bc="periodic"):
+        self.p = int(p)
+        self.np = tuple(int(v) for v in np_)
+        self.ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+        self.n_patches = self.ijk.shape[0]
+        self.origin = tuple(float(v) for v in origin)
+        self.dx = float(dx)
+        self.bc = BC[bc] if isinstance(bc, str) else int(bc)
+        L = lib()
+        self._h = L.og_grid_new(self.p, *self.np, self.n_patches, self.ijk.ctypes.data_as(_int_p),
+                                *self.origin, self.dx, self.bc)
+        if not self._h:
+            raise ValueError("oracle: invalid grid description")
+        self.n_ghost = int(L.og_n_ghost(self._h))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.og_grid_free(h)
+            self._h = None
+
+    @property
+    def ushape(self):
+        return (NV, self.n_patches, self.p, self.p, self.p)
+
+    @property
+    def gshape(self):
+        return (NV, self.n_ghost)
+
+    def _g(self, G):
+        if self.n_ghost == 0:
+            return np.zeros((NV, 1))
+        return _f64(G, self.gshape)
+
+    def ghost_coords(self):
+        out = np.zeros((max(self.n_ghost, 1), 3), dtype=np.int32)
+        lib().og_ghost_coords(self._h, out.ctypes.data_as(_int_p))
+        return out[:self.n_ghost]
+
+    def fill_tiles(self, U, G=None):
+        U = _f64(U, self.ushape)
+        G = self._g(G)
+        T = self.p + 2 * HALO
+        out = np.empty((NV, self.n_patches, T, T, T))
+        lib().og_fill_tiles(self._h, _d(U), _d(G), _d(out))
+        return out
+
+    def rhs(self, P, U, G=None, Gini=None):
+        U = _f64(U, self.ushape)
+        G = self._g(G)
+        Gini = self._g(Gini)
+        rU = np.empty(self.ushape)
+        rG = np.empty((NV, max(self.n_ghost, 1)))
+        lib().og_rhs(self._h, ctypes.byref(P), _d(U), _d(G), _d(Gini), _d(rU), _d(rG))
+        return rU, rG[:, :self.n_ghost]
+
+    def rk4_step(self, P, dt, U, G=None, Gini=None):
+        """One RK4 step; returns new (U, G) (inputs are not modified)."""
+        U = _f64(U, self.ushape).copy()
+        G = self._g(G).copy()
+        Gini = self._g(Gini)
+        lib().og_rk4_step(self._h, ctypes.byref(P), float(dt), _d(U), _d(G), _d(Gini))
+        return U, G[:, :self.n_ghost]
+
+    def enforce(self, U):
+        U = _f64(U, self.ushape).copy()
+        lib().og_enforce(self._h, _d(U))
+        return U
+
+    def constraints(self, U, G=None):
+        U = _f64(U, self.ushape)
+        G = self._g(G)
+        H = np.empty(self.ushape[1:])
+        M = np.empty((3,) + self.ushape[1:])
+        out = np.empty(5)
+        lib().og_constraints(self._h, _d(U), _d(G), _d(H), _d(M), _d(out))
+        return H, M, out
+
+    def rhs_points(self, P, U, G, pts):
+        U = _f64(U, self.ushape)
+        G = self._g(G)
+        pts = np.ascontiguousarray(pts, dtype=np.int64)
+        out = np.empty((len(pts), NV))
+        rc = lib().og_rhs_points(self._h, ctypes.byref(P), _d(U), _d(G), len(pts),
+                                 pts.ctypes.data_as(_lng_p), _d(out))
+        if rc:
+            raise IndexError("oracle: sample point out of range")
+        return out
+
+    def constraints_points(self, U, G, pts):
+        U = _f64(U, self.ushape)
+        G = self._g(G)
+        pts = np.ascontiguousarray(pts, dtype=np.int64)
+        out = np.empty((len(pts), 4))
+        rc = lib().og_constraints_points(self._h, _d(U), _d(G), len(pts), pts.ctypes.data_as(_lng_p), _d(out))
+        if rc:
+            raise IndexError("oracle: sample point out of range")
+        return out
+
+    def point_derivs(self, U, G, pt, ko_eps=0.1):
+        U = _f64(U, self.ushape)
+        G = self._g(G)
+        d1 = np.empty((NV, 3))
+        d2 = np.empty((NV, 3, 3))
+        ko = np.empty(NV)
+        rc = lib().og_point_derivs(self._h, _d(U), _d(G), int(pt), float(ko_eps), _d(d1), _d(d2), _d(ko))
+        if rc:
+            raise IndexError("oracle: sample point out of range")
+        return d1, d2, ko

@@ -1,0 +1,934 @@
+/*
+ * CCZ4 oracle: plain, slow, FP64 CPU restatement of the fourth-order
+ * finite-difference (FD4) CCZ4 method of the ExaGRyPE paper
+ * (arXiv 2406.11626).
+ *
+ * TEST INFRASTRUCTURE ONLY: the test suite, the package smoke check and the
+ * CPU-baseline leg of bench.py are its only users. It shares no code with the
+ * CUDA path. Build with -O2 -ffp-contract=off (no FMA contraction), so that
+ * every operation below is one correctly rounded IEEE double operation.
+ *
+ * What it computes, step by step, with the passage each step follows:
+ *   - patch grid and halo of width K = 3 (Sec. "Spatial Discretisation":
+ *     p^3 patches with K halo layers, cell-centred sample points);
+ *   - halo fill: periodic wrap (Sec. "Gauge Wave": periodic domain), Neumann
+ *     copy filled layer by layer outward (Sec. "Boundary Treatment"), and
+ *     Sommerfeld ghost cells that are evolved in time (Eqs.
+ *     SommerfeldBC_v1 and exa_sommerfeld_inter);
+ *   - FD4 first derivatives (Eq. exa_fd4_central_difference), FD4 second
+ *     derivatives (pure: the five-point fourth-order stencil; mixed: the
+ *     tensor product of two first-derivative stencils, Sec. "Finite
+ *     Differences" speaks of a tensor-product approach) and Kreiss-Oliger
+ *     dissipation of order N = 3 summed over the three directions
+ *     (Eq. exa_fd4_ko);
+ *   - the second-order CCZ4 right-hand side: the nine primary evolution
+ *     equations of the appendix "Spacetime foliation" with the red terms
+ *     removed, closed by the listed relations and the modified Ricci tensor
+ *     of Eq. NR_foccz4_modified_ricci;
+ *   - classic RK4 time stepping (Sec. "Finite Differences": Runge-Kutta up to
+ *     order four) and the algebraic constraint enforcement after each step
+ *     (Sec. "Evolution equations": det g~ = 1 by rescaling, tr A~ = 0 by
+ *     trace removal);
+ *   - the Hamiltonian and momentum constraints (Eqs. hamilton_constraints and
+ *     momentum_constraints), with the Ricci tensor through the Riemann
+ *     relation of the appendix, and their L2 norm (Sec. "Gauge Wave").
+ * Readings of the paper where it is silent or ambiguous are listed in the
+ * header comments of the functions that take them.
+ */
+#include "ccz4_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum {
+  GXX, GXY, GXZ, GYY, GYZ, GZZ, ALPHA, BETAX, BETAY, BETAZ, PHI,
+  AXX, AXY, AXZ, AYY, AYZ, AZZ, KTR, THETA, GHX, GHY, GHZ, BBX, BBY, BBZ
+};
+
+/* index of the symmetric pair (i, j) in the six stored components */
+static const int SYM[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+
+struct og_grid {
+  int p, T;           /* points per patch edge; tile edge p + 2K */
+  int np[3], N[3];    /* patches and points per axis */
+  int n_patches, bc;
+  int *ijk;           /* [n][3] patch coordinates */
+  int *owner;         /* [np2][np1][np0] -> patch id */
+  double origin[3], dx;
+  long n_ghost;
+  int *gcoord;        /* [n_ghost][3] global coordinates (x, y, z) */
+  long *gid;          /* dense map over [-K, N+K)^3 -> ghost id, or -1 */
+  int Mx[3];          /* N + 2K */
+};
+
+/* ------------------------------------------------------------------------ */
+/* grid                                                                     */
+/* ------------------------------------------------------------------------ */
+
+og_grid *og_grid_new(int p, int np0, int np1, int np2, int n_patches, const int *ijk,
+                     double ox, double oy, double oz, double dx, int bc) {
+  if (p < 1 || np0 < 1 || np1 < 1 || np2 < 1 || !(dx > 0.0)) return NULL;
+  if (bc != OG_BC_PERIODIC && bc != OG_BC_COPY && bc != OG_BC_SOMMERFELD) return NULL;
+  if ((long)n_patches != (long)np0 * np1 * np2 || ijk == NULL) return NULL;
+  og_grid *g = (og_grid *)calloc(1, sizeof(og_grid));
+  g->p = p;
+  g->T = p + 2 * OG_HALO;
+  g->np[0] = np0; g->np[1] = np1; g->np[2] = np2;
+  for (int d = 0; d < 3; ++d) {
+    g->N[d] = g->np[d] * p;
+    g->Mx[d] = g->N[d] + 2 * OG_HALO;
+  }
+  g->n_patches = n_patches;
+  g->bc = bc;
+  g->origin[0] = ox; g->origin[1] = oy; g->origin[2] = oz;
+  g->dx = dx;
+  g->ijk = (int *)malloc(sizeof(int) * 3 * (size_t)n_patches);
+  memcpy(g->ijk, ijk, sizeof(int) * 3 * (size_t)n_patches);
+  g->owner = (int *)malloc(sizeof(int) * (size_t)n_patches);
+  for (int i = 0; i < n_patches; ++i) g->owner[i] = -1;
+  for (int n = 0; n < n_patches; ++n) {
+    int a = ijk[3 * n], b = ijk[3 * n + 1], c = ijk[3 * n + 2];
+    if (a < 0 || a >= np0 || b < 0 || b >= np1 || c < 0 || c >= np2) { og_grid_free(g); return NULL; }
+    long cell = ((long)c * np1 + b) * np0 + a;
+    if (g->owner[cell] != -1) { og_grid_free(g); return NULL; }
+    g->owner[cell] = n;
+  }
+  /* ghost shell: every cell within K of the domain and outside it, enumerated
+     in lexicographic (z, y, x) order */
+  long total = (long)g->Mx[0] * g->Mx[1] * g->Mx[2];
+  g->gid = (long *)malloc(sizeof(long) * (size_t)total);
+  long count = 0;
+  for (int z = -OG_HALO; z < g->N[2] + OG_HALO; ++z)
+    for (int y = -OG_HALO; y < g->N[1] + OG_HALO; ++y)
+      for (int x = -OG_HALO; x < g->N[0] + OG_HALO; ++x) {
+        long k = ((long)(z + OG_HALO) * g->Mx[1] + (y + OG_HALO)) * g->Mx[0] + (x + OG_HALO);
+        int inside = x >= 0 && x < g->N[0] && y >= 0 && y < g->N[1] && z >= 0 && z < g->N[2];
+        g->gid[k] = (bc == OG_BC_SOMMERFELD && !inside) ? count++ : -1;
+      }
+  g->n_ghost = count;
+  g->gcoord = (int *)malloc(sizeof(int) * 3 * (size_t)(count > 0 ? count : 1));
+  for (int z = -OG_HALO; z < g->N[2] + OG_HALO; ++z)
+    for (int y = -OG_HALO; y < g->N[1] + OG_HALO; ++y)
+      for (int x = -OG_HALO; x < g->N[0] + OG_HALO; ++x) {
+        long k = ((long)(z + OG_HALO) * g->Mx[1] + (y + OG_HALO)) * g->Mx[0] + (x + OG_HALO);
+        long id = g->gid[k];
+        if (id >= 0) { g->gcoord[3 * id] = x; g->gcoord[3 * id + 1] = y; g->gcoord[3 * id + 2] = z; }
+      }
+  return g;
+}
+
+void og_grid_free(og_grid *g) {
+  if (!g) return;
+  free(g->ijk); free(g->owner); free(g->gid); free(g->gcoord); free(g);
+}
+
+long og_n_ghost(const og_grid *g) { return g->n_ghost; }
+
+void og_ghost_coords(const og_grid *g, int *out) {
+  memcpy(out, g->gcoord, sizeof(int) * 3 * (size_t)g->n_ghost);
+}
+
+static long n_interior(const og_grid *g) { return (long)g->n_patches * g->p * g->p * g->p; }
+
+/* Where the value at global point (x, y, z) lives. Returns 0 for an interior
+   point (linear index into U), 1 for a ghost-shell point (index into G).
+   Periodic: wrap. Copy: the paper fills the K ghost layers outward one at a
+   time with Q_out = Q_in, so every ghost layer equals the last interior
+   layer; with that rule applied face by face, edge and corner ghosts equal
+   the nearest interior point, i.e. the clamped coordinate. Sommerfeld: the
+   ghost cell itself (its value is evolved state). */
+static int locate(const og_grid *g, int x, int y, int z, long *idx) {
+  int c[3] = {x, y, z};
+  int inside = 1;
+  for (int d = 0; d < 3; ++d) if (c[d] < 0 || c[d] >= g->N[d]) inside = 0;
+  if (!inside) {
+    if (g->bc == OG_BC_PERIODIC) {
+      for (int d = 0; d < 3; ++d) c[d] = ((c[d] % g->N[d]) + g->N[d]) % g->N[d];
+    } else if (g->bc == OG_BC_COPY) {
+      for (int d = 0; d < 3; ++d) c[d] = c[d] < 0 ? 0 : (c[d] >= g->N[d] ? g->N[d] - 1 : c[d]);
+    } else {
+      long k = ((long)(z + OG_HALO) * g->Mx[1] + (y + OG_HALO)) * g->Mx[0] + (x + OG_HALO);
+      *idx = g->gid[k];
+      return 1;
+    }
+  }
+  int pa = c[0] / g->p, pb = c[1] / g->p, pc = c[2] / g->p;
+  int lx = c[0] % g->p, ly = c[1] % g->p, lz = c[2] % g->p;
+  int n = g->owner[((long)pc * g->np[1] + pb) * g->np[0] + pa];
+  *idx = (long)n * g->p * g->p * g->p + ((long)lz * g->p + ly) * g->p + lx;
+  return 0;
+}
+
+static double value_at(const og_grid *g, const double *U, const double *G, int v, int x, int y, int z) {
+  long idx;
+  if (locate(g, x, y, z, &idx)) return G[(long)v * g->n_ghost + idx];
+  return U[(long)v * n_interior(g) + idx];
+}
+
+/* Halo'd tile of patch n in the oracle's working layout: point-major, the
+   25 fields of a point contiguous. */
+static void build_tile(const og_grid *g, int n, const double *U, const double *G, double *tile) {
+  int T = g->T, p = g->p;
+  int bx = g->ijk[3 * n] * p, by = g->ijk[3 * n + 1] * p, bz = g->ijk[3 * n + 2] * p;
+  for (int lz = 0; lz < T; ++lz)
+    for (int ly = 0; ly < T; ++ly)
+      for (int lx = 0; lx < T; ++lx) {
+        long t = ((long)lz * T + ly) * T + lx;
+        for (int v = 0; v < OG_NV; ++v)
+          tile[t * OG_NV + v] =
+              value_at(g, U, G, v, bx + lx - OG_HALO, by + ly - OG_HALO, bz + lz - OG_HALO);
+      }
+}
+
+int og_fill_tiles(const og_grid *g, const double *U, const double *G, double *tiles) {
+  int T = g->T;
+  long T3 = (long)T * T * T;
+  double *tile = (double *)malloc(sizeof(double) * (size_t)T3 * OG_NV);
+  for (int n = 0; n < g->n_patches; ++n) {
+    build_tile(g, n, U, G, tile);
+    for (int v = 0; v < OG_NV; ++v)
+      for (long t = 0; t < T3; ++t)
+        tiles[((long)v * g->n_patches + n) * T3 + t] = tile[t * OG_NV + v];
+  }
+  free(tile);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* FD4 stencils (Eqs. exa_fd4_central_difference and exa_fd4_ko)            */
+/* ------------------------------------------------------------------------ */
+
+/* weights of the first-derivative stencil at offsets -2, -1, +1, +2 (times
+   1/(12 dx)): 8 (Q+ - Q-) - (Q++ - Q--) */
+static const int OFF4[4] = {-2, -1, 1, 2};
+static const double W1[4] = {1.0, -8.0, 8.0, -1.0};
+
+typedef struct {
+  const double *tile;
+  long c;          /* centre point in the tile */
+  long st[3];      /* strides of x, y, z in points */
+} tview;
+
+static double tq(const tview *tv, long off, int v) { return tv->tile[(tv->c + off) * OG_NV + v]; }
+
+static double fd1(const tview *tv, int v, int k, double dx) {
+  long s = tv->st[k];
+  return (8.0 * (tq(tv, s, v) - tq(tv, -s, v)) - (tq(tv, 2 * s, v) - tq(tv, -2 * s, v))) / (12.0 * dx);
+}
+
+/* pure second derivative: the five-point fourth-order stencil
+   (-Q++ + 16 Q+ - 30 Q + 16 Q- - Q--) / (12 dx^2) */
+static double fd2pure(const tview *tv, int v, int k, double dx) {
+  long s = tv->st[k];
+  return (-tq(tv, 2 * s, v) + 16.0 * tq(tv, s, v) - 30.0 * tq(tv, 0, v) + 16.0 * tq(tv, -s, v) -
+          tq(tv, -2 * s, v)) / (12.0 * dx * dx);
+}
+
+/* mixed second derivative: first-derivative stencil along k applied to the
+   first-derivative stencil along l */
+static double fd2mixed(const tview *tv, int v, int k, int l, double dx) {
+  double acc = 0.0;
+  for (int a = 0; a < 4; ++a) {
+    double inner = 0.0;
+    for (int b = 0; b < 4; ++b) inner += W1[b] * tq(tv, OFF4[a] * tv->st[k] + OFF4[b] * tv->st[l], v);
+    acc += W1[a] * inner;
+  }
+  return acc / (144.0 * dx * dx);
+}
+
+/* Kreiss-Oliger dissipation of order N = 3, summed over the three directions:
+   eps/(64 dx) (Q--- - 6 Q-- + 15 Q- - 20 Q + 15 Q+ - 6 Q++ + Q+++) */
+static double ko_sum(const tview *tv, int v, double eps, double dx) {
+  double acc = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    long s = tv->st[k];
+    double d = tq(tv, -3 * s, v) - 6.0 * tq(tv, -2 * s, v) + 15.0 * tq(tv, -s, v) - 20.0 * tq(tv, 0, v) +
+               15.0 * tq(tv, s, v) - 6.0 * tq(tv, 2 * s, v) + tq(tv, 3 * s, v);
+    acc += eps / (64.0 * dx) * d;
+  }
+  return acc;
+}
+
+static void point_derivs(const tview *tv, double dx, double d1[OG_NV][3], double d2[OG_NV][3][3]) {
+  for (int v = 0; v < OG_NV; ++v) {
+    for (int k = 0; k < 3; ++k) d1[v][k] = fd1(tv, v, k, dx);
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l)
+        d2[v][k][l] = (k == l) ? fd2pure(tv, v, k, dx) : fd2mixed(tv, v, k, l, dx);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* pointwise geometry shared by the right-hand side and the constraints     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double g[3][3], ig[3][3], det;    /* conformal metric, inverse, determinant */
+  double dg[3][3][3];               /* dg[k][i][j] = d_k g~_ij */
+  double D[3][3][3];                /* D_kij = 1/2 d_k g~_ij */
+  double Gam[3][3][3];              /* Gam[k][i][j] = conformal Christoffel G~^k_ij */
+  double GamL[3][3][3];             /* GamL[k][i][j] = G~_kij = g~_kl G~^l_ij */
+  double Gc[3];                     /* G~^i = g~^jk G~^i_jk */
+  double ph, P[3], ddph[3][3];      /* phi, P_i = d_i phi, d_i d_j phi */
+  double PGam[3][3][3];             /* physical Christoffel Gamma^k_ij */
+} geom;
+
+static void metric_inverse(const double g[3][3], double ig[3][3], double *det) {
+  double d = g[0][0] * (g[1][1] * g[2][2] - g[1][2] * g[2][1]) -
+             g[0][1] * (g[1][0] * g[2][2] - g[1][2] * g[2][0]) +
+             g[0][2] * (g[1][0] * g[2][1] - g[1][1] * g[2][0]);
+  ig[0][0] = (g[1][1] * g[2][2] - g[1][2] * g[2][1]) / d;
+  ig[0][1] = (g[0][2] * g[2][1] - g[0][1] * g[2][2]) / d;
+  ig[0][2] = (g[0][1] * g[1][2] - g[0][2] * g[1][1]) / d;
+  ig[1][0] = (g[1][2] * g[2][0] - g[1][0] * g[2][2]) / d;
+  ig[1][1] = (g[0][0] * g[2][2] - g[0][2] * g[2][0]) / d;
+  ig[1][2] = (g[0][2] * g[1][0] - g[0][0] * g[1][2]) / d;
+  ig[2][0] = (g[1][0] * g[2][1] - g[1][1] * g[2][0]) / d;
+  ig[2][1] = (g[0][1] * g[2][0] - g[0][0] * g[2][1]) / d;
+  ig[2][2] = (g[0][0] * g[1][1] - g[0][1] * g[1][0]) / d;
+  *det = d;
+}
+
+static void build_geom(const double q[OG_NV], const double d1[OG_NV][3], const double d2[OG_NV][3][3], geom *G) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) G->g[i][j] = q[GXX + SYM[i][j]];
+  metric_inverse(G->g, G->ig, &G->det);
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        G->dg[k][i][j] = d1[GXX + SYM[i][j]][k];
+        G->D[k][i][j] = 0.5 * G->dg[k][i][j];
+      }
+  /* G~^k_ij = g~^kl (D_ijl + D_jil - D_lij) */
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int l = 0; l < 3; ++l) s += G->ig[k][l] * (G->D[i][j][l] + G->D[j][i][l] - G->D[l][i][j]);
+        G->Gam[k][i][j] = s;
+      }
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int l = 0; l < 3; ++l) s += G->g[k][l] * G->Gam[l][i][j];
+        G->GamL[k][i][j] = s;
+      }
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k) s += G->ig[j][k] * G->Gam[i][j][k];
+    G->Gc[i] = s;
+  }
+  G->ph = q[PHI];
+  for (int i = 0; i < 3; ++i) {
+    G->P[i] = d1[PHI][i];
+    for (int j = 0; j < 3; ++j) G->ddph[i][j] = d2[PHI][i][j];
+  }
+  /* Gamma^k_ij = G~^k_ij - (1/phi) g~^kl (g~_jl P_i + g~_il P_j - g~_ij P_l) */
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int l = 0; l < 3; ++l)
+          s += G->ig[k][l] * (G->g[j][l] * G->P[i] + G->g[i][l] * G->P[j] - G->g[i][j] * G->P[l]);
+        G->PGam[k][i][j] = G->Gam[k][i][j] - s / G->ph;
+      }
+}
+
+/* ------------------------------------------------------------------------ */
+/* the second-order CCZ4 right-hand side at one point                       */
+/* ------------------------------------------------------------------------ */
+
+/* The nine primary evolution equations of the appendix, red terms removed
+   (the paper keeps them only in the first-order formulation). Auxiliary
+   quantities are the FD4 derivatives of the primaries: A_i = d_i alpha,
+   B_k^i = d_k beta^i, D_kij = 1/2 d_k g~_ij, P_i = d_i phi, and their
+   derivatives are the FD4 second derivatives.
+   Readings taken here:
+   - K0 is a parameter (default 0); the slicing function is g(alpha) = 1
+     (harmonic) or 2/alpha (1+log);
+   - tr A~ = g~^ij A~_ij (conformal metric);
+   - G~^i in the Gamma-hat equation and in Z_i is the contracted Christoffel
+     symbol of the conformal metric computed from its derivatives;
+   - nabla~_i nabla~_j phi = d_i d_j phi - G~^k_ij d_k phi;
+   - the trace-free part is taken with the physical metric, which for a
+     covariant pair equals X_ij - 1/3 g~_ij g~^kl X_kl;
+   - zero shift sets the right-hand sides of beta^i and b^i to zero; the
+     Gamma-driver uses d_t Gamma-hat^i of this same point (before the
+     dissipation term is added) in the b^i equation. */
+static void ccz4_point_rhs(const og_params *P, const double q[OG_NV], const double d1[OG_NV][3],
+                           const double d2[OG_NV][3][3], double rhs[OG_NV]) {
+  geom G;
+  build_geom(q, d1, d2, &G);
+  double (*g)[3] = G.g, (*ig)[3] = G.ig;
+  const double al = q[ALPHA], ph = q[PHI], Kt = q[KTR], Th = q[THETA];
+  double be[3], dal[3], ddal[3][3], dbe[3][3], ddbe[3][3][3], At[3][3], dAt[3][3][3];
+  double dKt[3], dTh[3], Gh[3], dGh[3][3], bb[3], dbb[3][3];
+  for (int i = 0; i < 3; ++i) {
+    be[i] = q[BETAX + i];
+    Gh[i] = q[GHX + i];
+    bb[i] = q[BBX + i];
+    dal[i] = d1[ALPHA][i];
+    dKt[i] = d1[KTR][i];
+    dTh[i] = d1[THETA][i];
+    for (int j = 0; j < 3; ++j) {
+      ddal[i][j] = d2[ALPHA][i][j];
+      At[i][j] = q[AXX + SYM[i][j]];
+    }
+  }
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i) {
+      dbe[k][i] = d1[BETAX + i][k];   /* B_k^i */
+      dGh[k][i] = d1[GHX + i][k];     /* d_k Gamma-hat^i */
+      dbb[k][i] = d1[BBX + i][k];     /* d_k b^i */
+      for (int l = 0; l < 3; ++l) ddbe[k][l][i] = d2[BETAX + i][k][l];
+      for (int j = 0; j < 3; ++j) dAt[k][i][j] = d1[AXX + SYM[i][j]][k];
+    }
+
+  /* Z_i = 1/2 g~_ij (Gh^j - G~^j); Z^i = 1/2 phi^2 (Gh^i - G~^i) */
+  double Zcov[3], Zup[3];
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < 3; ++j) s += g[i][j] * (Gh[j] - G.Gc[j]);
+    Zcov[i] = 0.5 * s;
+    Zup[i] = 0.5 * ph * ph * (Gh[i] - G.Gc[i]);
+  }
+  /* nabla~_i nabla~_j phi */
+  double cdph[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += G.Gam[k][i][j] * G.P[k];
+      cdph[i][j] = G.ddph[i][j] - s;
+    }
+  double trcdph = 0.0, PP = 0.0;
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) {
+      trcdph += ig[k][l] * cdph[k][l];
+      PP += ig[k][l] * G.P[k] * G.P[l];
+    }
+  /* R_ij + 2 nabla_(i Z_j), Eq. NR_foccz4_modified_ricci */
+  double RZ[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double t1 = 0.0;
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) t1 += ig[k][l] * d2[GXX + SYM[i][j]][k][l];
+      double t2 = 0.0, t3 = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        t2 += 0.5 * (g[k][i] * dGh[j][k] + g[k][j] * dGh[i][k]);
+        t3 += Gh[k] * G.dg[k][i][j];
+      }
+      double t4 = 0.0;
+      for (int l = 0; l < 3; ++l)
+        for (int m = 0; m < 3; ++m)
+          for (int k = 0; k < 3; ++k)
+            t4 += ig[l][m] * (G.Gam[k][l][i] * G.GamL[j][k][m] + G.Gam[k][l][j] * G.GamL[i][k][m] +
+                              G.Gam[k][i][m] * G.GamL[k][l][j]);
+      double t7 = 0.0;
+      for (int k = 0; k < 3; ++k) t7 += Zup[k] * (g[i][k] * G.P[j] + g[j][k] * G.P[i] - g[i][j] * G.P[k]);
+      RZ[i][j] = -0.5 * t1 + t2 + 0.5 * t3 + t4 + (cdph[i][j] + g[i][j] * trcdph) / ph -
+                 2.0 / (ph * ph) * g[i][j] * PP + 2.0 / (ph * ph * ph) * t7;
+    }
+  /* nabla_i nabla_j alpha = d_i d_j alpha - Gamma^k_ij A_k (physical) */
+  double DDal[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += G.PGam[k][i][j] * dal[k];
+      DDal[i][j] = ddal[i][j] - s;
+    }
+  /* R + 2 nabla_k Z^k = phi^2 g~^ij (R_ij + 2 nabla_(i Z_j)); nabla^i nabla_i alpha */
+  double RpZ = 0.0, lapal = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      RpZ += ig[i][j] * RZ[i][j];
+      lapal += ig[i][j] * DDal[i][j];
+    }
+  RpZ *= ph * ph;
+  lapal *= ph * ph;
+  /* traces and raised A~ */
+  double trA = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) trA += ig[i][j] * At[i][j];
+  double Aup[3][3], AgA[3][3], AA = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0, u = 0.0;
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) {
+          s += ig[i][k] * ig[j][l] * At[k][l];
+          u += At[i][k] * ig[k][l] * At[l][j];
+        }
+      Aup[i][j] = s;
+      AgA[i][j] = u;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) AA += At[i][j] * Aup[i][j];
+  double trB = dbe[0][0] + dbe[1][1] + dbe[2][2];
+  double gfun = (P->slicing == OG_SLICING_ONE_PLUS_LOG) ? 2.0 / al : 1.0;
+
+  /* d_t g~_ij */
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) {
+      double adv = 0.0, lie = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        adv += be[k] * 2.0 * G.D[k][i][j];
+        lie += g[k][i] * dbe[j][k] + g[k][j] * dbe[i][k];
+      }
+      rhs[GXX + SYM[i][j]] = adv + lie - 2.0 / 3.0 * g[i][j] * trB -
+                             2.0 * al * (At[i][j] - 1.0 / 3.0 * g[i][j] * trA) -
+                             (1.0 / P->tau) * (G.det - 1.0) * g[i][j];
+    }
+  /* d_t alpha */
+  {
+    double adv = 0.0;
+    for (int k = 0; k < 3; ++k) adv += be[k] * dal[k];
+    rhs[ALPHA] = adv - al * al * gfun * (Kt - P->K0 - 2.0 * P->c * Th);
+  }
+  /* d_t phi */
+  {
+    double adv = 0.0;
+    for (int k = 0; k < 3; ++k) adv += be[k] * G.P[k];
+    rhs[PHI] = adv + 1.0 / 3.0 * ph * (al * Kt - trB);
+  }
+  /* d_t A~_ij */
+  {
+    double Mx[3][3], trM = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Mx[i][j] = -DDal[i][j] + al * RZ[i][j];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) trM += ig[i][j] * Mx[i][j];
+    for (int i = 0; i < 3; ++i)
+      for (int j = i; j < 3; ++j) {
+        double adv = 0.0, lie = 0.0;
+        for (int k = 0; k < 3; ++k) {
+          adv += be[k] * dAt[k][i][j];
+          lie += At[k][i] * dbe[j][k] + At[k][j] * dbe[i][k];
+        }
+        rhs[AXX + SYM[i][j]] = adv + ph * ph * (Mx[i][j] - 1.0 / 3.0 * g[i][j] * trM) + lie -
+                               2.0 / 3.0 * At[i][j] * trB + al * At[i][j] * (Kt - 2.0 * Th * P->c) -
+                               2.0 * al * AgA[i][j];
+      }
+  }
+  /* d_t K */
+  {
+    double adv = 0.0;
+    for (int k = 0; k < 3; ++k) adv += be[k] * dKt[k];
+    rhs[KTR] = adv - lapal + al * RpZ + al * Kt * (Kt - 2.0 * Th * P->c) -
+               3.0 * al * P->kappa1 * (1.0 + P->kappa2) * Th;
+  }
+  /* d_t Theta */
+  {
+    double adv = 0.0, ZA = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      adv += be[k] * dTh[k];
+      ZA += Zup[k] * dal[k];
+    }
+    rhs[THETA] = adv + 0.5 * al * P->e * P->e * RpZ +
+                 0.5 * al * P->e * P->e * (2.0 / 3.0 * Kt * Kt - AA) - al * Th * Kt * P->c - ZA -
+                 al * P->kappa1 * (2.0 + P->kappa2) * Th;
+  }
+  /* d_t Gamma-hat^i */
+  double rGh[3], advGh[3];
+  for (int i = 0; i < 3; ++i) {
+    double adv = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0, t4 = 0.0, t5 = 0.0, t6 = 0.0, t7 = 0.0, t8 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      adv += be[k] * dGh[k][i];
+      t1 += 2.0 * al * ig[k][i] * dTh[k];
+      for (int l = 0; l < 3; ++l) {
+        t2 += ig[k][l] * ddbe[k][l][i];
+        t3 += P->s / 3.0 * ig[i][k] * ddbe[k][l][l];
+      }
+      t4 += -4.0 / 3.0 * al * ig[i][k] * dKt[k];
+      t5 += -G.Gc[k] * dbe[k][i];
+    }
+    double GA = 0.0, AP = 0.0, thz = 0.0, AA1 = 0.0, kz = 0.0, k3 = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      for (int k = 0; k < 3; ++k) {
+        GA += G.Gam[i][j][k] * Aup[j][k];
+        k3 += ig[j][k] * Zcov[j] * dbe[k][i];
+      }
+      AP += Aup[i][j] * G.P[j] / ph;
+      thz += ig[j][i] * (Th * dal[j] / al + 2.0 / 3.0 * Kt * Zcov[j]);
+      AA1 += Aup[i][j] * dal[j];
+      kz += ig[i][j] * Zcov[j];
+    }
+    t6 = 2.0 / 3.0 * G.Gc[i] * trB + 2.0 * al * (GA - 3.0 * AP) - 2.0 * al * thz - 2.0 * AA1;
+    t7 = -2.0 * al * P->kappa1 * kz;
+    t8 = 2.0 * P->kappa3 * (2.0 / 3.0 * kz * trB - k3);
+    advGh[i] = adv;
+    rGh[i] = adv + t1 + t2 + t3 + t4 + t5 + t6 + t7 + t8;
+    rhs[GHX + i] = rGh[i];
+  }
+  /* gauge: d_t beta^i, d_t b^i */
+  for (int i = 0; i < 3; ++i) {
+    if (P->shift == OG_SHIFT_GAMMA_DRIVER) {
+      double advb = 0.0, advbb = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        advb += be[k] * dbe[k][i];
+        advbb += be[k] * dbb[k][i];
+      }
+      rhs[BETAX + i] = advb + P->f * bb[i];
+      rhs[BBX + i] = advbb + (rGh[i] - advGh[i]) - P->eta * bb[i];
+    } else {
+      rhs[BETAX + i] = 0.0;
+      rhs[BBX + i] = 0.0;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sommerfeld ghost cells                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Right-hand side of the evolved ghost cell id: the paper's radiative
+   condition d_t Q + c (r / x_d) d_d Q = -(c / r)(Q - Q_ini), with d_d Q the
+   one-sided difference between the ghost cell and its neighbour one layer
+   towards the domain (Eq. exa_sommerfeld_inter), r and x_d taken at the ghost
+   cell. Reading for edges and corners: the paper fills layers face by face;
+   a ghost cell that is outside in several directions belongs to the face
+   filled last, in the order x, then y, then z, i.e. to its highest outside
+   axis. */
+static void ghost_rhs(const og_grid *g, const og_params *P, const double *U, const double *G,
+                      const double *Gini, long id, double out[OG_NV]) {
+  int c[3] = {g->gcoord[3 * id], g->gcoord[3 * id + 1], g->gcoord[3 * id + 2]};
+  int d = -1, side = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (c[a] < 0) { d = a; side = -1; }
+    if (c[a] >= g->N[a]) { d = a; side = +1; }
+  }
+  int nb[3] = {c[0], c[1], c[2]};
+  nb[d] -= side;
+  double xs[3];
+  for (int a = 0; a < 3; ++a) xs[a] = g->origin[a] + (c[a] + 0.5) * g->dx;
+  double r = sqrt(xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2]);
+  for (int v = 0; v < OG_NV; ++v) {
+    double qg = G[(long)v * g->n_ghost + id];
+    double qn = value_at(g, U, G, v, nb[0], nb[1], nb[2]);
+    /* derivative along +x_d from the two points */
+    double dQ = side > 0 ? (qg - qn) / g->dx : (qn - qg) / g->dx;
+    double cv = P->somm_speed[v];
+    out[v] = -cv * (r / xs[d]) * dQ - cv / r * (qg - Gini[(long)v * g->n_ghost + id]);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* full right-hand side, RK4, enforcement                                   */
+/* ------------------------------------------------------------------------ */
+
+static void patch_rhs(const og_grid *g, const og_params *P, int n, const double *tile, double *rU) {
+  int p = g->p, T = g->T;
+  long pts = n_interior(g);
+  double d1[OG_NV][3], d2[OG_NV][3][3];
+  for (int z = 0; z < p; ++z)
+    for (int y = 0; y < p; ++y)
+      for (int x = 0; x < p; ++x) {
+        tview tv;
+        tv.tile = tile;
+        tv.c = ((long)(z + OG_HALO) * T + (y + OG_HALO)) * T + (x + OG_HALO);
+        tv.st[0] = 1; tv.st[1] = T; tv.st[2] = (long)T * T;
+        double q[OG_NV], r[OG_NV];
+        for (int v = 0; v < OG_NV; ++v) q[v] = tq(&tv, 0, v);
+        point_derivs(&tv, g->dx, d1, d2);
+        ccz4_point_rhs(P, q, d1, d2, r);
+        long li = (long)n * p * p * p + ((long)z * p + y) * p + x;
+        for (int v = 0; v < OG_NV; ++v) rU[(long)v * pts + li] = r[v] + ko_sum(&tv, v, P->ko_eps, g->dx);
+      }
+}
+
+int og_rhs(const og_grid *g, const og_params *P, const double *U, const double *G,
+           const double *Gini, double *rU, double *rG) {
+  long T3 = (long)g->T * g->T * g->T;
+  double *tile = (double *)malloc(sizeof(double) * (size_t)T3 * OG_NV);
+  for (int n = 0; n < g->n_patches; ++n) {
+    build_tile(g, n, U, G, tile);
+    patch_rhs(g, P, n, tile, rU);
+  }
+  free(tile);
+  for (long id = 0; id < g->n_ghost; ++id) {
+    double r[OG_NV];
+    ghost_rhs(g, P, U, G, Gini, id, r);
+    for (int v = 0; v < OG_NV; ++v) rG[(long)v * g->n_ghost + id] = r[v];
+  }
+  return 0;
+}
+
+/* Algebraic constraints: det g~ = 1 by rescaling every component with
+   det^(-1/3), then tr A~ = 0 by removing g~_ij / 3 times the trace taken with
+   the rescaled metric. */
+int og_enforce(const og_grid *g, double *U) {
+  long pts = n_interior(g);
+  for (long i = 0; i < pts; ++i) {
+    double m[3][3], im[3][3], det, A[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        m[a][b] = U[(long)(GXX + SYM[a][b]) * pts + i];
+        A[a][b] = U[(long)(AXX + SYM[a][b]) * pts + i];
+      }
+    metric_inverse(m, im, &det);
+    double sc = 1.0 / cbrt(det);
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) m[a][b] *= sc;
+    metric_inverse(m, im, &det);
+    double tr = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) tr += im[a][b] * A[a][b];
+    for (int a = 0; a < 3; ++a)
+      for (int b = a; b < 3; ++b) {
+        U[(long)(GXX + SYM[a][b]) * pts + i] = m[a][b];
+        U[(long)(AXX + SYM[a][b]) * pts + i] = A[a][b] - 1.0 / 3.0 * m[a][b] * tr;
+      }
+  }
+  return 0;
+}
+
+/* Classic RK4 (weights 1/6, 1/3, 1/3, 1/6; nodes 0, 1/2, 1/2, 1) over the
+   interior points and the evolved Sommerfeld ghost cells, then the algebraic
+   enforcement on the interior points. */
+int og_rk4_step(const og_grid *g, const og_params *P, double dt, double *U, double *G,
+                const double *Gini) {
+  long nu = n_interior(g) * OG_NV, ng = g->n_ghost * OG_NV;
+  double *k[4], *kg[4];
+  for (int s = 0; s < 4; ++s) {
+    k[s] = (double *)malloc(sizeof(double) * (size_t)nu);
+    kg[s] = (double *)malloc(sizeof(double) * (size_t)(ng > 0 ? ng : 1));
+  }
+  double *Y = (double *)malloc(sizeof(double) * (size_t)nu);
+  double *YG = (double *)malloc(sizeof(double) * (size_t)(ng > 0 ? ng : 1));
+  const double cnode[4] = {0.0, 0.5, 0.5, 1.0};
+  for (int s = 0; s < 4; ++s) {
+    if (s == 0) {
+      memcpy(Y, U, sizeof(double) * (size_t)nu);
+      if (ng) memcpy(YG, G, sizeof(double) * (size_t)ng);
+    } else {
+      for (long i = 0; i < nu; ++i) Y[i] = U[i] + cnode[s] * dt * k[s - 1][i];
+      for (long i = 0; i < ng; ++i) YG[i] = G[i] + cnode[s] * dt * kg[s - 1][i];
+    }
+    og_rhs(g, P, Y, YG, Gini, k[s], kg[s]);
+  }
+  for (long i = 0; i < nu; ++i) U[i] = U[i] + dt / 6.0 * (k[0][i] + 2.0 * k[1][i] + 2.0 * k[2][i] + k[3][i]);
+  for (long i = 0; i < ng; ++i) G[i] = G[i] + dt / 6.0 * (kg[0][i] + 2.0 * kg[1][i] + 2.0 * kg[2][i] + kg[3][i]);
+  og_enforce(g, U);
+  for (int s = 0; s < 4; ++s) { free(k[s]); free(kg[s]); }
+  free(Y); free(YG);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* constraints                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Hamiltonian constraint H = R + 2/3 K^2 - A~_ij A~^ij and momentum
+   constraint M_i = g~^kl (d_k A~_li - 2 G~^m_l(i A~_k)m - 3 A~_ik P_l / phi)
+   - 2/3 d_i K (vacuum). R is the physical Ricci scalar, taken from the
+   Riemann relation of the appendix with the physical Christoffel symbols
+   and their derivatives (Z does not enter). M is computed with a lower
+   index, as printed on the right-hand side. */
+static void point_constraints(const double q[OG_NV], const double d1[OG_NV][3],
+                              const double d2[OG_NV][3][3], double out[4]) {
+  geom G;
+  build_geom(q, d1, d2, &G);
+  double (*g)[3] = G.g, (*ig)[3] = G.ig;
+  const double ph = G.ph;
+  /* D_k^{ml} = g~^ma g~^lb D_kab */
+  double Dup[3][3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int m = 0; m < 3; ++m)
+      for (int l = 0; l < 3; ++l) {
+        double s = 0.0;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) s += ig[m][a] * ig[l][b] * G.D[k][a][b];
+        Dup[k][m][l] = s;
+      }
+  /* dD[k][i][j][l] = d_k D_ijl = 1/2 d_k d_i g~_jl */
+  double dD[3][3][3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        for (int l = 0; l < 3; ++l) dD[k][i][j][l] = 0.5 * d2[GXX + SYM[j][l]][k][i];
+  /* d_k Gamma^m_ij, the appendix's closing relation for the physical
+     Christoffel symbols */
+  double dPG[3][3][3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int m = 0; m < 3; ++m)
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          double s = 0.0;
+          for (int l = 0; l < 3; ++l) {
+            s += -2.0 * Dup[k][m][l] * (G.D[i][j][l] + G.D[j][i][l] - G.D[l][i][j]);
+            s += ig[m][l] * (dD[k][i][j][l] + dD[k][j][i][l] - dD[k][l][i][j]);
+            s += 2.0 / ph * Dup[k][m][l] * (g[j][l] * G.P[i] + g[i][l] * G.P[j] - g[i][j] * G.P[l]);
+            s += -2.0 / ph * ig[m][l] * (G.D[k][j][l] * G.P[i] + G.D[k][i][l] * G.P[j] - G.D[k][i][j] * G.P[l]);
+            s += -1.0 / ph * ig[m][l] * (g[j][l] * G.ddph[k][i] + g[i][l] * G.ddph[k][j] - g[i][j] * G.ddph[k][l]);
+            s += 1.0 / (ph * ph) * ig[m][l] *
+                 (g[j][l] * G.P[i] * G.P[k] + g[i][l] * G.P[j] * G.P[k] - g[i][j] * G.P[k] * G.P[l]);
+          }
+          dPG[k][m][i][j] = s;
+        }
+  /* R_ij = R^m_imj with R^m_ikj = d_k Gamma^m_ij - d_j Gamma^m_ik
+     + Gamma^l_ij Gamma^m_lk - Gamma^l_ik Gamma^m_lj */
+  double R = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double Rij = 0.0;
+      for (int m = 0; m < 3; ++m) {
+        Rij += dPG[m][m][i][j] - dPG[j][m][i][m];
+        for (int l = 0; l < 3; ++l)
+          Rij += G.PGam[l][i][j] * G.PGam[m][l][m] - G.PGam[l][i][m] * G.PGam[m][l][j];
+      }
+      R += ph * ph * ig[i][j] * Rij;   /* gamma^ij = phi^2 g~^ij */
+    }
+  double At[3][3], Aup[3][3], AA = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) At[i][j] = q[AXX + SYM[i][j]];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) s += ig[i][k] * ig[j][l] * At[k][l];
+      Aup[i][j] = s;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) AA += At[i][j] * Aup[i][j];
+  const double Kt = q[KTR];
+  out[0] = R + 2.0 / 3.0 * Kt * Kt - AA;
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l) {
+        double dA = d1[AXX + SYM[l][i]][k];
+        double cs = 0.0;
+        for (int m = 0; m < 3; ++m) cs += G.Gam[m][l][i] * At[k][m] + G.Gam[m][l][k] * At[i][m];
+        s += ig[k][l] * (dA - cs - 3.0 * At[i][k] * G.P[l] / ph);
+      }
+    out[1 + i] = s - 2.0 / 3.0 * d1[KTR][i];
+  }
+}
+
+/* L2 norms over all interior points (Sec. "Gauge Wave":
+   L2 = sqrt(sum H^2 / n), n the number of grid points). out[0] = L2 of H,
+   out[1] = L2 of |M| (|M|^2 = sum_i M_i^2), out[2] = max |H|,
+   out[3] = max |M|, out[4] = number of non-finite H or M values. */
+int og_constraints(const og_grid *g, const double *U, const double *G, double *H, double *M,
+                   double out[5]) {
+  int p = g->p, T = g->T;
+  long pts = n_interior(g), T3 = (long)T * T * T;
+  double *tile = (double *)malloc(sizeof(double) * (size_t)T3 * OG_NV);
+  double d1[OG_NV][3], d2[OG_NV][3][3];
+  double sH = 0.0, sM = 0.0, mH = 0.0, mM = 0.0, bad = 0.0;
+  for (int n = 0; n < g->n_patches; ++n) {
+    build_tile(g, n, U, G, tile);
+    for (int z = 0; z < p; ++z)
+      for (int y = 0; y < p; ++y)
+        for (int x = 0; x < p; ++x) {
+          tview tv;
+          tv.tile = tile;
+          tv.c = ((long)(z + OG_HALO) * T + (y + OG_HALO)) * T + (x + OG_HALO);
+          tv.st[0] = 1; tv.st[1] = T; tv.st[2] = (long)T * T;
+          double q[OG_NV], c4[4];
+          for (int v = 0; v < OG_NV; ++v) q[v] = tq(&tv, 0, v);
+          point_derivs(&tv, g->dx, d1, d2);
+          point_constraints(q, d1, d2, c4);
+          long li = (long)n * p * p * p + ((long)z * p + y) * p + x;
+          if (H) H[li] = c4[0];
+          if (M)
+            for (int i = 0; i < 3; ++i) M[(long)i * pts + li] = c4[1 + i];
+          double m2 = c4[1] * c4[1] + c4[2] * c4[2] + c4[3] * c4[3];
+          if (!isfinite(c4[0]) || !isfinite(m2)) { bad += 1.0; continue; }
+          sH += c4[0] * c4[0];
+          sM += m2;
+          if (fabs(c4[0]) > mH) mH = fabs(c4[0]);
+          if (sqrt(m2) > mM) mM = sqrt(m2);
+        }
+  }
+  free(tile);
+  out[0] = sqrt(sH / (double)pts);
+  out[1] = sqrt(sM / (double)pts);
+  out[2] = mH;
+  out[3] = mM;
+  out[4] = bad;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* sampled points (for checks at sizes where a full oracle pass is too slow) */
+/* ------------------------------------------------------------------------ */
+
+/* Small halo'd neighbourhood (7^3 points) of interior point pt, in the same
+   working layout as a tile. */
+static void build_neigh(const og_grid *g, const double *U, const double *G, long pt, double *nb) {
+  int p = g->p;
+  long p3 = (long)p * p * p;
+  int n = (int)(pt / p3);
+  long r = pt % p3;
+  int lz = (int)(r / (p * p)), ly = (int)((r / p) % p), lx = (int)(r % p);
+  int gx = g->ijk[3 * n] * p + lx, gy = g->ijk[3 * n + 1] * p + ly, gz = g->ijk[3 * n + 2] * p + lz;
+  const int W = 2 * OG_HALO + 1;
+  for (int c = 0; c < W; ++c)
+    for (int b = 0; b < W; ++b)
+      for (int a = 0; a < W; ++a)
+        for (int v = 0; v < OG_NV; ++v)
+          nb[(((long)c * W + b) * W + a) * OG_NV + v] =
+              value_at(g, U, G, v, gx + a - OG_HALO, gy + b - OG_HALO, gz + c - OG_HALO);
+}
+
+static int sample_view(const og_grid *g, const double *U, const double *G, long pt, double *nb, tview *tv) {
+  if (pt < 0 || pt >= n_interior(g)) return 1;
+  const int W = 2 * OG_HALO + 1;
+  build_neigh(g, U, G, pt, nb);
+  tv->tile = nb;
+  tv->c = ((long)OG_HALO * W + OG_HALO) * W + OG_HALO;
+  tv->st[0] = 1; tv->st[1] = W; tv->st[2] = (long)W * W;
+  return 0;
+}
+
+int og_rhs_points(const og_grid *g, const og_params *P, const double *U, const double *G,
+                  long n, const long *pts, double *out) {
+  double nb[7 * 7 * 7 * OG_NV];
+  double d1[OG_NV][3], d2[OG_NV][3][3];
+  for (long s = 0; s < n; ++s) {
+    tview tv;
+    if (sample_view(g, U, G, pts[s], nb, &tv)) return 1;
+    double q[OG_NV], r[OG_NV];
+    for (int v = 0; v < OG_NV; ++v) q[v] = tq(&tv, 0, v);
+    point_derivs(&tv, g->dx, d1, d2);
+    ccz4_point_rhs(P, q, d1, d2, r);
+    for (int v = 0; v < OG_NV; ++v) out[s * OG_NV + v] = r[v] + ko_sum(&tv, v, P->ko_eps, g->dx);
+  }
+  return 0;
+}
+
+int og_constraints_points(const og_grid *g, const double *U, const double *G, long n,
+                          const long *pts, double *out) {
+  double nb[7 * 7 * 7 * OG_NV];
+  double d1[OG_NV][3], d2[OG_NV][3][3];
+  for (long s = 0; s < n; ++s) {
+    tview tv;
+    if (sample_view(g, U, G, pts[s], nb, &tv)) return 1;
+    double q[OG_NV];
+    for (int v = 0; v < OG_NV; ++v) q[v] = tq(&tv, 0, v);
+    point_derivs(&tv, g->dx, d1, d2);
+    point_constraints(q, d1, d2, out + 4 * s);
+  }
+  return 0;
+}
+
+int og_point_derivs(const og_grid *g, const double *U, const double *G, long pt, double ko_eps,
+                    double *d1o, double *d2o, double *koo) {
+  double nb[7 * 7 * 7 * OG_NV];
+  double d1[OG_NV][3], d2[OG_NV][3][3];
+  tview tv;
+  if (sample_view(g, U, G, pt, nb, &tv)) return 1;
+  point_derivs(&tv, g->dx, d1, d2);
+  for (int v = 0; v < OG_NV; ++v) {
+    for (int k = 0; k < 3; ++k) {
+      d1o[v * 3 + k] = d1[v][k];
+      for (int l = 0; l < 3; ++l) d2o[(v * 3 + k) * 3 + l] = d2[v][k][l];
+    }
+    koo[v] = ko_sum(&tv, v, ko_eps, g->dx);
+  }
+  return 0;
+}

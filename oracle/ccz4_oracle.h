@@ -1,0 +1,74 @@
+/*
+ * CCZ4 oracle: plain, slow, FP64 CPU restatement of the fourth-order
+ * finite-difference CCZ4 method of the ExaGRyPE paper (arXiv 2406.11626).
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check of the
+ * package entry point and the CPU-baseline leg of bench.py may load this
+ * library. The CUDA path never calls it, includes it or links it: the two
+ * share no code, and no product code path falls back to it.
+ *
+ * Layout of the arrays this API exchanges (the "canonical" layout; the
+ * oracle's internal working layout is its own):
+ *   U     [25][n_patches][p][p][p]   interior points, x fastest, fields in the
+ *                                    order listed below, patches in the
+ *                                    order of the ijk array
+ *   G     [25][n_ghost]              ghost-shell points (Sommerfeld only),
+ *                                    ghost cells in lexicographic order of
+ *                                    their global (z, y, x) coordinates
+ *   tiles [25][n_patches][p+6]^3     each patch with its halo of width 3
+ *
+ * Field order (the primary variables of the second-order formulation, Eq.
+ * second-order-variables, 25 of them):
+ *   0..5 conformal metric g~ (xx,xy,xz,yy,yz,zz), 6 lapse alpha,
+ *   7..9 shift beta^i, 10 conformal factor phi, 11..16 A~ (xx..zz), 17 K,
+ *   18 Theta, 19..21 Gamma-hat^i, 22..24 b^i.
+ */
+#ifndef CCZ4_ORACLE_H
+#define CCZ4_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OG_NV 25
+#define OG_HALO 3
+
+enum { OG_BC_PERIODIC = 0, OG_BC_COPY = 1, OG_BC_SOMMERFELD = 2 };
+enum { OG_SLICING_HARMONIC = 0, OG_SLICING_ONE_PLUS_LOG = 1 };
+enum { OG_SHIFT_ZERO = 0, OG_SHIFT_GAMMA_DRIVER = 1 };
+
+typedef struct {
+  double kappa1, kappa2, kappa3, e, c, tau, mu, f, eta, s, K0, ko_eps;
+  int slicing; /* OG_SLICING_* */
+  int shift;   /* OG_SHIFT_* */
+  double somm_speed[OG_NV];
+} og_params;
+
+typedef struct og_grid og_grid;
+
+og_grid *og_grid_new(int p, int np0, int np1, int np2, int n_patches, const int *ijk,
+                     double ox, double oy, double oz, double dx, int bc);
+void og_grid_free(og_grid *g);
+long og_n_ghost(const og_grid *g);
+void og_ghost_coords(const og_grid *g, int *out /* [n_ghost][3] (x,y,z) */);
+
+int og_fill_tiles(const og_grid *g, const double *U, const double *G, double *tiles);
+int og_rhs(const og_grid *g, const og_params *P, const double *U, const double *G,
+           const double *Gini, double *rU, double *rG);
+int og_rk4_step(const og_grid *g, const og_params *P, double dt, double *U, double *G,
+                const double *Gini);
+int og_enforce(const og_grid *g, double *U);
+int og_constraints(const og_grid *g, const double *U, const double *G, double *H,
+                   double *M, double out[5]);
+int og_rhs_points(const og_grid *g, const og_params *P, const double *U, const double *G,
+                  long n, const long *pts, double *out /* [n][25] */);
+int og_constraints_points(const og_grid *g, const double *U, const double *G, long n,
+                          const long *pts, double *out /* [n][4] = H, M_x, M_y, M_z */);
+int og_point_derivs(const og_grid *g, const double *U, const double *G, long pt,
+                    double ko_eps, double *d1 /* [25][3] */, double *d2 /* [25][3][3] */,
+                    double *ko /* [25] */);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
