@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the CCZ4 FD4 hot path on GB300.
+
+Workload: the single static puncture of mass M = 1 at the origin (Brill-
+Lindquist data, 1+log slicing, Gamma-driver shift with eta = 2, Kreiss-Oliger
+0.1, Sommerfeld boundary), [-8, 8]^3 as 16^3 patches of 9^3 points
+(144^3 = 2,985,984 points, dx = 1/9), classic RK4 with dt = 0.1 dx.
+A step is one RK4 step over the whole grid: for each of the four stages the
+halo fill and the fused right-hand-side + stage-update kernel (plus the
+Sommerfeld ghost-cell kernel). Metric: point-stages per second
+(interior points x 4 stages x steps / time).
+
+Prints one JSON line. --impl reference times the CPU oracle instead (the
+plain FP64 restatement of the paper used as the parity judge) on a bounded
+sample of the same physics.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CCZ4 RHS+RK point-stages/s at 1 GB300, mixed vs FP64 at stated error; % roofline"
+UNIT = "point-stages/s"
+# FP64 pipe of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops at the 2070 MHz
+# maximum SM clock (the nominal 1.25 TFLOP/s FP64 rate).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+KERNEL_SOURCES = ("paper_2406_11626_gb300/csrc/rhs.cu", "paper_2406_11626_gb300/csrc/ccz4_algebra.cuh",
+                  "paper_2406_11626_gb300/csrc/ccz4_internal.cuh")
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.5)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [r for r in rows if r[2] > 200.0] or rows
+        sm = sorted(r[0] for r in load)
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in load for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(load), "power_w_max": max(r[2] for r in rows)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample_config():
+    """Same physics and grid spacing as the 144^3 workload on a 36^3-point
+    sub-box (4^3 patches of 9^3 around the puncture, [-2, 2]^3)."""
+    from paper_2406_11626_gb300 import inputs as I
+    return I.single_puncture_config(n_side=4, half_width=2.0)
+
+
+def time_oracle(n_steps, n_warm=0):
+    import oracle as O
+    from paper_2406_11626_gb300 import inputs as I
+    cfg = oracle_sample_config()
+    og = O.Grid(cfg.p, cfg.np, cfg.ijk(), cfg.origin, cfg.dx, cfg.bc)
+    U, G = I.initial_state(cfg)
+    P = O.make_params(**cfg.params)
+    for _ in range(n_warm):
+        U, G = og.rk4_step(P, cfg.dt, U, G, G)
+    t0 = time.perf_counter()
+    Gini = G
+    for _ in range(n_steps):
+        U, G = og.rk4_step(P, cfg.dt, U, G, Gini)
+    dt = time.perf_counter() - t0
+    return cfg, dt
+
+
+def cpu_baseline(target_s=12.0):
+    cfg, t1 = time_oracle(1)
+    n = max(1, int(target_s / max(t1, 1e-3)))
+    cfg, t = time_oracle(n)
+    v = cfg.n_points * 4 * n / t
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d RK4 steps of the same puncture physics and dx on %d^3 points "
+                      "(4^3 patches of 9^3, [-2,2]^3), single-threaded plain C FP64" % (n, cfg.N[0])}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfg, _ = time_oracle(args.warmup) if args.warmup > 0 else (oracle_sample_config(), 0.0)
+    cfg, t = time_oracle(max(args.steps, 1))
+    v = cfg.n_points * 4 * max(args.steps, 1) / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / max(args.steps, 1) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(None),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "each step: one RK4 step of the puncture physics at dx = 1/9 on "
+                                   "%d^3 points (4^3 patches of 9^3)" % cfg.N[0]},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(g, precision="fp64", K=None):
+    from paper_2406_11626_gb300 import inputs as I
+    cfg = I.single_puncture_config()
+    c = {"workload": "single puncture M=1, [-8,8]^3, 16^3 patches of 9^3 (144^3 points), "
+                     "1+log, Gamma-driver eta=2, KO 0.1, Sommerfeld, RK4 dt=0.1dx",
+         "patches": cfg.n_patches, "p": cfg.p, "points": cfg.n_points, "dx": cfg.dx,
+         "precision": precision,
+         "l2": "inputs larger than L2: each state buffer is 25 x 3.38M doubles = 675 MB"}
+    if g is not None:
+        c["ghost_cells"] = g.n_ghost
+    return c
+
+
+# ----------------------------------------------------------------------------
+# GB300 arm
+# ----------------------------------------------------------------------------
+def load_traffic():
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    return d.get("bytes_per_launch")
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2406_11626_gb300 import ccz4 as C
+    from paper_2406_11626_gb300 import inputs as I
+    cfg = I.single_puncture_config()
+    g = C.Grid.from_config(cfg)
+    U0, G0 = I.initial_state(cfg)
+    g.upload(U0, G0)
+    g.upload(U0, G0, buf="INI")
+    P = C.make_params(**cfg.params, precision=args.precision)
+    stream = torch.cuda.current_stream()
+    bufs = [C.stage_buffers(s) for s in range(4)]
+
+    def step(ev=None):
+        for s in range(4):
+            g.fill_halos(bufs[s][0], stream)
+            if ev is not None:
+                ev[s][0].record(stream)
+            g.rk_stage(P, s, cfg.dt, stream, fill=False)
+            if ev is not None:
+                ev[s][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    K = args.steps
+    kev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(4)] for _ in range(K)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(local)
+    clk.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(K):
+        step(kev[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    stage_ms = [kev[k][s][0].elapsed_time(kev[k][s][1]) for k in range(K) for s in range(4)]
+    ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = world * cfg.n_points * 4 * K / (ms * 1e-3)
+    out = g.constraints("U", raise_nonfinite=False)
+
+    # end to end through the C ABI from pinned host memory, one step per call
+    n_state = g.n_points + g.n_ghost
+    Uh = torch.empty((I.NV, g.n_points), dtype=torch.float64, pin_memory=True).numpy()
+    Gh = torch.empty((I.NV, max(g.n_ghost, 1)), dtype=torch.float64, pin_memory=True).numpy()[:, :g.n_ghost]
+    Ud, Gd = g.download("U")
+    Uh[...] = Ud.reshape(I.NV, -1)
+    Gh[...] = Gd
+    E = max(1, args.e2e_steps)
+    g.evolve_host(P, cfg.dt, 1, Uh, Gh, Uh, Gh, stream)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(E):
+        g.evolve_host(P, cfg.dt, 1, Uh, Gh, Uh, Gh, stream)
+    t_e2e = time.perf_counter() - t0
+    te = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * cfg.n_points * 4 * E / float(te.item())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    fl = C.flops_per_point_stage(args.precision)
+    t_stage = sum(stage_ms) / len(stage_ms) * 1e-3
+    f64 = fl["fp64"] * cfg.n_points
+    f32 = fl["fp32"] * cfg.n_points
+    if args.precision == "fp64" or f32 == 0:
+        roof = {"bound": "alu", "achieved": f64 / t_stage / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": f64 / t_stage / 1e12 / FP64_PEAK_TFLOPS, "traffic": load_traffic(),
+                "kernel": "interior_kernel (fused RHS + RK stage) with the ghost-cell kernel of the same stage",
+                "flops_per_point_stage": fl["fp64"],
+                "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz"}
+    else:
+        t_roof = max(f64 / (FP64_PEAK_TFLOPS * 1e12), f32 / (FP32_PEAK_TFLOPS * 1e12))
+        roof = {"bound": "alu", "achieved": t_roof / t_stage, "peak": 1.0, "unit": "fraction of max(F64/P64, F32/P32)",
+                "frac": t_roof / t_stage, "traffic": load_traffic(),
+                "fp64_flops_per_point_stage": fl["fp64"], "fp32_flops_per_point_stage": fl["fp32"],
+                "fp64_tflops": f64 / t_stage / 1e12, "fp32_tflops": f32 / t_stage / 1e12}
+    launches_per_stage = 2 + (1 if g.n_ghost > 0 else 0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64 state + f32 algebra",
+        "data": "synthetic (Brill-Lindquist puncture data generated in closed form)",
+        "config": workload_config(g, args.precision, K),
+        "stage_kernel_ms": sum(stage_ms) / len(stage_ms),
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * I.NV * n_state,
+                "d2h_bytes_per_step": 8 * I.NV * n_state,
+                "how": "ccz4_evolve_host per step: pinned host state -> device, one RK4 step, device -> host"},
+        "gpu_launches": launches_per_stage * 4 * K,
+        "constraints_after": {"L2_H": out[0], "L2_M": out[1], "max_H": out[2], "nonfinite": out[4]},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,219 @@
+/*
+ * ccz4.h -- C ABI of the GB300 CCZ4 finite-difference hot path.
+ *
+ * The library evolves the second-order CCZ4 formulation of the Einstein
+ * equations (ExaGRyPE paper, arXiv 2406.11626, appendix "Spacetime
+ * foliation": the nine primary evolution equations with the red terms
+ * removed) on one uniform level of p^3 Cartesian patches with a halo of
+ * width 3, discretised by fourth-order central finite differences with
+ * Kreiss-Oliger dissipation (appendix "Formulation for the kernel FD4
+ * Solver") and classic RK4 in time (Sec. "Finite Differences"). All work
+ * runs in CUDA kernels on the current device; there is no CPU fallback.
+ *
+ * Conventions for every call
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream). Every call is asynchronous on that stream unless its
+ *    comment says it synchronises.
+ *  - Errors: a call returns CCZ4_OK or an error code and never aborts or
+ *    traps. Argument errors are caught on the host before any launch
+ *    (CCZ4_ERR_INVALID). Device-side faults of the data (for example a
+ *    non-finite constraint value) are reported by the synchronising calls.
+ *    ccz4_last_error() returns a message for the last failing call of the
+ *    calling thread.
+ *  - Ownership: a ccz4_grid owns every device buffer it allocates; host
+ *    arrays passed in are read (or written) during the call only and stay
+ *    owned by the caller.
+ *  - Fields (25, the primary variables of Eq. second-order-variables), in
+ *    this order: conformal metric g~_xx, g~_xy, g~_xz, g~_yy, g~_yz, g~_zz;
+ *    lapse alpha; shift beta^x, beta^y, beta^z; conformal factor phi;
+ *    A~_xx, A~_xy, A~_xz, A~_yy, A~_yz, A~_zz; K; Theta; Gamma-hat^x,y,z;
+ *    b^x, b^y, b^z.
+ *  - Points: cell-centred, x = origin + (i + 1/2) dx (Sec. "Finite
+ *    Differences": samples at the centres of the patch volumes).
+ *  - Device state layout ("SoA"): a state buffer holds 25 fields of
+ *    `field_stride` doubles each. Within a field, the interior points come
+ *    first, patch after patch in the order of the descriptor's ijk array,
+ *    each patch as [z][y][x] with x fastest (n_points = n_patches * p^3);
+ *    then, for Sommerfeld boundaries, the n_ghost evolved ghost cells: every
+ *    cell within 3 points of the domain and outside it, in lexicographic
+ *    (z, y, x) order of its global integer coordinates. Host arrays use the
+ *    same order without padding: U[25][n_points] and G[25][n_ghost].
+ *  - Halo tiles (CCZ4_BUF_TILE): [25][n_patches][(p+6)^3], each patch with
+ *    its width-3 halo, [z][y][x] with x fastest, local index l = patch
+ *    point index + 3.
+ */
+#ifndef CCZ4_H
+#define CCZ4_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CCZ4_NV 25
+#define CCZ4_HALO 3
+
+typedef enum {
+  CCZ4_OK = 0,
+  CCZ4_ERR_INVALID = 1,   /* bad argument; nothing was launched */
+  CCZ4_ERR_NOMEM = 2,     /* a device or host allocation failed */
+  CCZ4_ERR_CUDA = 3,      /* a CUDA call failed (message in ccz4_last_error) */
+  CCZ4_ERR_NONFINITE = 4, /* non-finite values found by ccz4_constraints */
+  CCZ4_ERR_TIMEOUT = 5,   /* a bounded device wait gave up */
+  CCZ4_ERR_BOUNDS = 6     /* a kernel met an index outside its buffers */
+} ccz4_status;
+
+/* Boundary kinds (Sec. "Boundary Treatment"). PERIODIC wraps the domain.
+   COPY is the homogeneous Neumann condition Q_out = Q_in filled layer by
+   layer outward, so every ghost point equals the nearest interior point.
+   SOMMERFELD keeps the ghost cells as evolved state and advances them with
+   the radiative condition of Eq. SommerfeldBC_v1, discretised as in Eq.
+   exa_sommerfeld_inter (a ghost cell outside in several directions belongs
+   to its highest outside axis, z before y before x). */
+enum { CCZ4_BC_PERIODIC = 0, CCZ4_BC_COPY = 1, CCZ4_BC_SOMMERFELD = 2 };
+
+/* Slicing function g(alpha) of Eq. NR_foccz4_lapse_gauge: 1 (harmonic) or
+   2/alpha ("1+log"). */
+enum { CCZ4_SLICING_HARMONIC = 0, CCZ4_SLICING_ONE_PLUS_LOG = 1 };
+
+/* Shift condition: zero (static) shift, or the Gamma-driver of Eqs.
+   NR_foccz4_shift_gauge and NR_foccz4_b^i. */
+enum { CCZ4_SHIFT_ZERO = 0, CCZ4_SHIFT_GAMMA_DRIVER = 1 };
+
+/* Arithmetic of the pointwise CCZ4 algebra. FP64: everything in double.
+   MIXED: state, RK accumulation, finite differences and the terms with
+   1/phi in double; the rest of the pointwise algebra in single. */
+enum { CCZ4_PREC_FP64 = 0, CCZ4_PREC_MIXED = 1 };
+
+/* Device buffers of a grid. U: the state U_n. Y0, Y1: RK stage states.
+   ACC: RK accumulator. RHS: output of ccz4_rhs. INI: Q_ini of the
+   Sommerfeld condition (ghost part only is used). TILE: halo tiles. The
+   state-shaped buffers (U, Y0, Y1, ACC, RHS, INI) share one layout. */
+enum {
+  CCZ4_BUF_U = 0, CCZ4_BUF_Y0 = 1, CCZ4_BUF_Y1 = 2, CCZ4_BUF_ACC = 3,
+  CCZ4_BUF_RHS = 4, CCZ4_BUF_INI = 5, CCZ4_BUF_TILE = 6
+};
+
+typedef struct {
+  int p;              /* points per patch edge, >= 1 */
+  int np[3];          /* patch slots per axis; the domain has np[d]*p points along d */
+  int n_patches;      /* must equal np[0]*np[1]*np[2]: the patches cover the domain */
+  const int *ijk;     /* host [n_patches][3] integer patch coordinates, each slot once */
+  double origin[3];   /* lower corner of the domain */
+  double dx;          /* grid spacing, > 0, the same along every axis */
+  int bc;             /* CCZ4_BC_* for the whole outer boundary */
+} ccz4_grid_desc;
+
+/* Physical and numerical parameters (appendix "Spacetime foliation":
+   kappa1, kappa2, kappa3, e, c, tau, mu, f, eta, s, K0; Eq. exa_fd4_ko:
+   the dissipation strength epsilon). mu enters only the first-order
+   formulation and is unused here. somm_speed is the wave speed c of the
+   Sommerfeld condition per field. */
+typedef struct {
+  double kappa1, kappa2, kappa3, e, c, tau, mu, f, eta, s, K0, ko_eps;
+  int slicing;        /* CCZ4_SLICING_* */
+  int shift;          /* CCZ4_SHIFT_* */
+  double somm_speed[CCZ4_NV];
+  int precision;      /* CCZ4_PREC_* */
+} ccz4_params;
+
+typedef struct ccz4_grid ccz4_grid;
+
+/* Creates a grid on the current device and allocates its buffers (Sec.
+   "Spatial Discretisation": p^3 patches with K = 3 halo layers). The
+   descriptor and its ijk array are copied. Buffers start zeroed. On error
+   *out is set to NULL. */
+ccz4_status ccz4_alloc_patches(const ccz4_grid_desc *desc, ccz4_grid **out);
+
+/* Releases every buffer of the grid (synchronises the device). NULL is a no-op. */
+ccz4_status ccz4_free_patches(ccz4_grid *g);
+
+/* Sizes: interior points (n_patches * p^3), ghost cells (0 unless
+   Sommerfeld) and the field stride of the state buffers, in doubles. */
+ccz4_status ccz4_grid_info(const ccz4_grid *g, long long *n_points, long long *n_ghost,
+                           long long *field_stride);
+
+/* Device address of buffer `buf` (CCZ4_BUF_*) and its size in doubles.
+   The grid keeps ownership. */
+ccz4_status ccz4_field_ptr(ccz4_grid *g, int buf, double **dev, long long *n_doubles);
+
+/* Copies host arrays U[25][n_points] and (Sommerfeld only, may be NULL
+   otherwise) G[25][n_ghost] into a state-shaped buffer, or back. Both
+   synchronise the stream before returning (the host arrays may be reused
+   at once). */
+ccz4_status ccz4_upload(ccz4_grid *g, int buf, const double *U, const double *G, void *stream);
+ccz4_status ccz4_download(ccz4_grid *g, int buf, double *U, double *G, void *stream);
+
+/* Halo fill (Sec. "Spatial Discretisation", Fig. patch-face-reconstruction:
+   each patch is glued with the data of its neighbours into a
+   (p+2K)^3 tile). Writes CCZ4_BUF_TILE from the state-shaped buffer `buf`:
+   interior points from their owning patch, points outside the domain by
+   the boundary kind (periodic wrap, copy of the nearest interior point,
+   or the Sommerfeld ghost cell). Faces, edges and corners are all filled. */
+ccz4_status ccz4_fill_halos(ccz4_grid *g, int buf, void *stream);
+
+/* Right-hand side d_t Q of the second-order CCZ4 system (appendix
+   "Spacetime foliation", Eqs. NR_foccz4_gamma_ij ... NR_foccz4_b^i, closed
+   by the listed relations and Eq. NR_foccz4_modified_ricci) plus the
+   Kreiss-Oliger term of Eq. exa_fd4_ko summed over x, y, z, at every
+   interior point, and the Sommerfeld right-hand side at every ghost cell.
+   Fills the halos of `in_buf` first (the TILE buffer is overwritten) and
+   writes `out_buf`. in_buf and out_buf must differ. */
+ccz4_status ccz4_rhs(ccz4_grid *g, const ccz4_params *P, int in_buf, int out_buf, void *stream);
+
+/* One stage s = 0..3 of classic RK4 (weights 1/6, 1/3, 1/3, 1/6; nodes
+   0, 1/2, 1/2, 1), the paper's compute kernel applied to every patch. The
+   halo fill is a separate step (the paper merges patch and halo before the
+   kernel runs): CCZ4_BUF_TILE must hold the halo'd stage input, i.e.
+   ccz4_fill_halos must have been called on the buffer that
+   ccz4_stage_buffers names as the input of stage s (U, Y0, Y1, Y0 for
+   s = 0, 1, 2, 3). The kernel evaluates the right-hand side k_s and applies
+   the update in the same pass:
+     s = 0: ACC = k0,        Y0 = U + dt/2 k0
+     s = 1: ACC += 2 k1,     Y1 = U + dt/2 k1
+     s = 2: ACC += 2 k2,     Y0 = U + dt k2
+     s = 3: U = U + dt/6 (ACC + k3), then the algebraic constraints are
+            enforced at every interior point (Sec. "Evolution equations":
+            g~ rescaled to unit determinant, then the trace of A~ removed).
+   Sommerfeld ghost cells are advanced by the same stage formulas. The four
+   stages in order, each after its halo fill, make one time step of size dt. */
+ccz4_status ccz4_rk_stage(ccz4_grid *g, const ccz4_params *P, int stage, double dt, void *stream);
+
+/* Input and output buffers (CCZ4_BUF_*) of RK stage s = 0..3. */
+ccz4_status ccz4_stage_buffers(int stage, int *in_buf, int *out_buf);
+
+/* n_steps full RK4 steps on U: for each stage, ccz4_fill_halos of the
+   stage input followed by ccz4_rk_stage. */
+ccz4_status ccz4_step(ccz4_grid *g, const ccz4_params *P, double dt, int n_steps, void *stream);
+
+/* End-to-end call from host memory: uploads U (and G) into CCZ4_BUF_U,
+   runs n_steps RK4 steps, downloads the result into U_out (and G_out),
+   and synchronises. In and out arrays may alias. */
+ccz4_status ccz4_evolve_host(ccz4_grid *g, const ccz4_params *P, double dt, int n_steps,
+                             const double *U_in, const double *G_in, double *U_out,
+                             double *G_out, void *stream);
+
+/* Algebraic constraint enforcement alone, in place on a state buffer
+   (interior points). */
+ccz4_status ccz4_enforce(ccz4_grid *g, int buf, void *stream);
+
+/* Constraint monitors of the state in `buf` (Eqs. hamilton_constraints and
+   momentum_constraints, vacuum): fills its halos, evaluates H and the
+   covariant M_i at every interior point, writes them to dev_H[n_points] and
+   dev_M[3][n_points] when those device pointers are not NULL, and reduces
+   (Sec. "Gauge Wave": L2 = sqrt(sum H^2 / n) over the n interior points):
+     out[0] = L2 of H, out[1] = L2 of |M| with |M|^2 = sum_i M_i^2,
+     out[2] = max |H|, out[3] = max |M|, out[4] = number of points where H
+     or M is not finite (those points are left out of the sums).
+   The reduction runs in a fixed order, so repeated calls give identical
+   results. Synchronises the stream; returns CCZ4_ERR_NONFINITE when
+   out[4] > 0 (out is still filled). */
+ccz4_status ccz4_constraints(ccz4_grid *g, int buf, double out[5], double *dev_H, double *dev_M,
+                             void *stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *ccz4_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCZ4_H */

@@ -65,6 +65,7 @@ def lib():
         L.og_ghost_coords.argtypes = [ctypes.c_void_p, _int_p]
         L.og_fill_tiles.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, _dbl_p]
         L.og_rhs.argtypes = [ctypes.c_void_p, ctypes.POINTER(Params), _dbl_p, _dbl_p, _dbl_p, _dbl_p, _dbl_p]
+        L.og_ghost_rhs.argtypes = [ctypes.c_void_p, ctypes.POINTER(Params), _dbl_p, _dbl_p, _dbl_p, _dbl_p]
         L.og_rk4_step.argtypes = [ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_double, _dbl_p, _dbl_p, _dbl_p]
         L.og_enforce.argtypes = [ctypes.c_void_p, _dbl_p]
         L.og_constraints.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, _dbl_p, _dbl_p, _dbl_p]
@@ -146,6 +147,15 @@ class Grid:
         rG = np.empty((NV, max(self.n_ghost, 1)))
         lib().og_rhs(self._h, ctypes.byref(P), _d(U), _d(G), _d(Gini), _d(rU), _d(rG))
         return rU, rG[:, :self.n_ghost]
+
+    def ghost_rhs(self, P, U, G, Gini):
+        """Right-hand side of the Sommerfeld ghost shell only, (25, n_ghost)."""
+        U = _f64(U, self.ushape)
+        G = self._g(G)
+        Gini = self._g(Gini)
+        rG = np.empty((NV, max(self.n_ghost, 1)))
+        lib().og_ghost_rhs(self._h, ctypes.byref(P), _d(U), _d(G), _d(Gini), _d(rG))
+        return rG[:, :self.n_ghost]
 
     def rk4_step(self, P, dt, U, G=None, Gini=None):
         """One RK4 step; returns new (U, G) (inputs are not modified)."""

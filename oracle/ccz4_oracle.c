@@ -656,6 +656,17 @@ int og_rhs(const og_grid *g, const og_params *P, const double *U, const double *
   return 0;
 }
 
+/* Right-hand side of the ghost shell alone (the interior is not evaluated). */
+int og_ghost_rhs(const og_grid *g, const og_params *P, const double *U, const double *G,
+                 const double *Gini, double *rG) {
+  for (long id = 0; id < g->n_ghost; ++id) {
+    double r[OG_NV];
+    ghost_rhs(g, P, U, G, Gini, id, r);
+    for (int v = 0; v < OG_NV; ++v) rG[(long)v * g->n_ghost + id] = r[v];
+  }
+  return 0;
+}
+
 /* Algebraic constraints: det g~ = 1 by rescaling every component with
    det^(-1/3), then tr A~ = 0 by removing g~_ij / 3 times the trace taken with
    the rescaled metric. */

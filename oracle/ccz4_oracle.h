@@ -55,6 +55,8 @@ void og_ghost_coords(const og_grid *g, int *out /* [n_ghost][3] (x,y,z) */);
 int og_fill_tiles(const og_grid *g, const double *U, const double *G, double *tiles);
 int og_rhs(const og_grid *g, const og_params *P, const double *U, const double *G,
            const double *Gini, double *rU, double *rG);
+int og_ghost_rhs(const og_grid *g, const og_params *P, const double *U, const double *G,
+                 const double *Gini, double *rG);
 int og_rk4_step(const og_grid *g, const og_params *P, double dt, double *U, double *G,
                 const double *Gini);
 int og_enforce(const og_grid *g, double *U);

@@ -1,0 +1,252 @@
+"""Python binding of the CCZ4 C ABI (include/ccz4.h): argument marshalling only.
+
+Every step of the hot path runs in the CUDA kernels of lib/libccz4_gb300.so.
+If that library is missing, every call raises: there is no CPU fallback.
+PyTorch is used only to pick up the current CUDA stream and, optionally, to
+view device buffers as tensors.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .inputs import NV
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libccz4_gb300.so")
+
+OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_BOUNDS = range(7)
+BC = {"periodic": 0, "copy": 1, "sommerfeld": 2}
+SLICING = {"harmonic": 0, "1+log": 1}
+SHIFT = {"zero": 0, "gamma-driver": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
+BUF = {"U": 0, "Y0": 1, "Y1": 2, "ACC": 3, "RHS": 4, "INI": 5, "TILE": 6}
+
+_dbl_p = ctypes.POINTER(ctypes.c_double)
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("np", ctypes.c_int * 3), ("n_patches", ctypes.c_int),
+                ("ijk", ctypes.POINTER(ctypes.c_int)), ("origin", ctypes.c_double * 3),
+                ("dx", ctypes.c_double), ("bc", ctypes.c_int)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("kappa1", "kappa2", "kappa3", "e", "c", "tau", "mu", "f", "eta", "s", "K0", "ko_eps")] + [
+        ("slicing", ctypes.c_int), ("shift", ctypes.c_int), ("somm_speed", ctypes.c_double * NV),
+        ("precision", ctypes.c_int)]
+
+
+class CCZ4Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("ccz4 error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Loads the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("CCZ4 CUDA library not found at %s; run __graft_entry__.build() "
+                          "(paper_2406_11626_gb300.build.build()) first" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ll_p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)
+    sig = {
+        "ccz4_alloc_patches": [ctypes.POINTER(GridDesc), ctypes.POINTER(vp)],
+        "ccz4_free_patches": [vp],
+        "ccz4_grid_info": [vp, ll_p, ll_p, ll_p],
+        "ccz4_field_ptr": [vp, ctypes.c_int, ctypes.POINTER(_dbl_p), ll_p],
+        "ccz4_upload": [vp, ctypes.c_int, _dbl_p, _dbl_p, vp],
+        "ccz4_download": [vp, ctypes.c_int, _dbl_p, _dbl_p, vp],
+        "ccz4_fill_halos": [vp, ctypes.c_int, vp],
+        "ccz4_rhs": [vp, ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int, vp],
+        "ccz4_rk_stage": [vp, ctypes.POINTER(Params), ctypes.c_int, ctypes.c_double, vp],
+        "ccz4_stage_buffers": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+        "ccz4_step": [vp, ctypes.POINTER(Params), ctypes.c_double, ctypes.c_int, vp],
+        "ccz4_evolve_host": [vp, ctypes.POINTER(Params), ctypes.c_double, ctypes.c_int,
+                             _dbl_p, _dbl_p, _dbl_p, _dbl_p, vp],
+        "ccz4_enforce": [vp, ctypes.c_int, vp],
+        "ccz4_constraints": [vp, ctypes.c_int, _dbl_p, _dbl_p, _dbl_p, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.ccz4_last_error.restype = ctypes.c_char_p
+    L.ccz4_last_error.argtypes = []
+    _lib = L
+    return L
+
+
+def _check(code):
+    if code != OK:
+        raise CCZ4Error(code, lib().ccz4_last_error().decode())
+
+
+def make_params(kappa1=1.0, kappa2=0.0, kappa3=0.0, e=1.0, c=1.0, tau=1.0, mu=0.2, f=0.75,
+                eta=2.0, s=1.0, K0=0.0, ko_eps=0.1, slicing="harmonic", shift="zero",
+                somm_speed=1.0, precision="fp64"):
+    P = Params()
+    for k, v in dict(kappa1=kappa1, kappa2=kappa2, kappa3=kappa3, e=e, c=c, tau=tau, mu=mu, f=f,
+                     eta=eta, s=s, K0=K0, ko_eps=ko_eps).items():
+        setattr(P, k, float(v))
+    P.slicing = SLICING[slicing] if isinstance(slicing, str) else int(slicing)
+    P.shift = SHIFT[shift] if isinstance(shift, str) else int(shift)
+    P.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    sp = np.broadcast_to(np.asarray(somm_speed, dtype=np.float64), (NV,))
+    for i in range(NV):
+        P.somm_speed[i] = float(sp[i])
+    return P
+
+
+def stage_buffers(stage):
+    """(input, output) buffer ids of RK stage s."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(lib().ccz4_stage_buffers(int(stage), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _buf(b):
+    return BUF[b] if isinstance(b, str) else int(b)
+
+
+def _d(a):
+    return a.ctypes.data_as(_dbl_p) if a is not None else None
+
+
+class Grid:
+    """One uniform level of p^3 patches on the current CUDA device."""
+
+    def __init__(self, p, np_, ijk, origin, dx, bc="periodic"):
+        L = lib()
+        self.p = int(p)
+        self.np = tuple(int(v) for v in np_)
+        self.ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+        self.n_patches = len(self.ijk)
+        d = GridDesc()
+        d.p = self.p
+        for q in range(3):
+            d.np[q] = self.np[q]
+            d.origin[q] = float(origin[q])
+        d.n_patches = self.n_patches
+        d.ijk = self.ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        d.dx = float(dx)
+        d.bc = BC[bc] if isinstance(bc, str) else int(bc)
+        h = ctypes.c_void_p()
+        _check(L.ccz4_alloc_patches(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        n, g, s = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(L.ccz4_grid_info(h, ctypes.byref(n), ctypes.byref(g), ctypes.byref(s)))
+        self.n_points, self.n_ghost, self.field_stride = n.value, g.value, s.value
+        self.origin = tuple(float(v) for v in origin)
+        self.dx = float(dx)
+
+    @classmethod
+    def from_config(cls, cfg):
+        return cls(cfg.p, cfg.np, cfg.ijk(), cfg.origin, cfg.dx, cfg.bc)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ccz4_free_patches(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- data movement ------------------------------------------------------
+    def upload(self, U, G=None, buf="U", stream=None):
+        U = np.ascontiguousarray(U, dtype=np.float64).reshape(NV, self.n_points)
+        Gc = None
+        if self.n_ghost:
+            Gc = np.ascontiguousarray(G, dtype=np.float64).reshape(NV, self.n_ghost)
+        _check(lib().ccz4_upload(self._h, _buf(buf), _d(U), _d(Gc), _stream(stream)))
+
+    def download(self, buf="U", stream=None):
+        if _buf(buf) == BUF["TILE"]:
+            T = self.p + 6
+            out = np.empty((NV, self.n_patches, T, T, T))
+            _check(lib().ccz4_download(self._h, BUF["TILE"], _d(out), None, _stream(stream)))
+            return out
+        U = np.empty((NV, self.n_patches, self.p, self.p, self.p))
+        G = np.empty((NV, self.n_ghost))
+        _check(lib().ccz4_download(self._h, _buf(buf), _d(U), _d(G) if self.n_ghost else None,
+                                   _stream(stream)))
+        return U, G
+
+    def device_ptr(self, buf):
+        p, n = _dbl_p(), ctypes.c_longlong()
+        _check(lib().ccz4_field_ptr(self._h, _buf(buf), ctypes.byref(p), ctypes.byref(n)))
+        return ctypes.cast(p, ctypes.c_void_p).value, n.value
+
+    def as_tensor(self, buf):
+        """Zero-copy torch view (1-D, float64) of a device buffer."""
+        import torch
+        ptr, n = self.device_ptr(buf)
+
+        class _CAI:
+            __cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (ptr, False),
+                                        "version": 3, "strides": None}
+        return torch.as_tensor(_CAI(), device="cuda")
+
+    # -- the hot path -----------------------------------------------------------
+    def fill_halos(self, buf="U", stream=None):
+        _check(lib().ccz4_fill_halos(self._h, _buf(buf), _stream(stream)))
+
+    def rhs(self, P, in_buf="U", out_buf="RHS", stream=None):
+        _check(lib().ccz4_rhs(self._h, ctypes.byref(P), _buf(in_buf), _buf(out_buf), _stream(stream)))
+
+    def rk_stage(self, P, stage, dt, stream=None, fill=True):
+        """RK4 stage s; with fill=True the halo of the stage input is filled first."""
+        if fill:
+            self.fill_halos(stage_buffers(stage)[0], stream)
+        _check(lib().ccz4_rk_stage(self._h, ctypes.byref(P), int(stage), float(dt), _stream(stream)))
+
+    def step(self, P, dt, n_steps=1, stream=None):
+        _check(lib().ccz4_step(self._h, ctypes.byref(P), float(dt), int(n_steps), _stream(stream)))
+
+    def evolve_host(self, P, dt, n_steps, U, G=None, U_out=None, G_out=None, stream=None):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        U_out = np.empty_like(U) if U_out is None else U_out
+        Gc = G_o = None
+        if self.n_ghost:
+            Gc = np.ascontiguousarray(G, dtype=np.float64)
+            G_o = np.empty_like(Gc) if G_out is None else G_out
+        _check(lib().ccz4_evolve_host(self._h, ctypes.byref(P), float(dt), int(n_steps), _d(U), _d(Gc),
+                                      _d(U_out), _d(G_o), _stream(stream)))
+        return U_out, G_o
+
+    def enforce(self, buf="U", stream=None):
+        _check(lib().ccz4_enforce(self._h, _buf(buf), _stream(stream)))
+
+    def constraints(self, buf="U", dev_H=None, dev_M=None, stream=None, raise_nonfinite=True):
+        out = np.empty(5)
+        code = lib().ccz4_constraints(self._h, _buf(buf), _d(out),
+                                      ctypes.cast(dev_H, _dbl_p) if dev_H else None,
+                                      ctypes.cast(dev_M, _dbl_p) if dev_M else None, _stream(stream))
+        if code == ERR_NONFINITE and not raise_nonfinite:
+            return out
+        _check(code)
+        return out

@@ -1,0 +1,421 @@
+// Host side of the C ABI declared in include/ccz4.h: grid allocation and
+// validation, host <-> device copies, and the orchestration of halo fill,
+// right-hand side, RK4 stages and constraint monitors. Every compute step
+// runs in the kernels of halo.cu, rhs.cu and constraints.cu.
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "ccz4_internal.cuh"
+
+namespace ccz4 {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int constraint_blocks(long long n_points);
+
+}  // namespace ccz4
+
+using namespace ccz4;
+
+#define CUDA_TRY(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return CCZ4_ERR_CUDA;                                                              \
+    }                                                                                    \
+  } while (0)
+
+static bool state_buffer(int buf) { return buf >= CCZ4_BUF_U && buf <= CCZ4_BUF_INI; }
+
+static ccz4_status check_grid(const ccz4_grid *g) {
+  if (!g) {
+    set_error("grid is NULL");
+    return CCZ4_ERR_INVALID;
+  }
+  return CCZ4_OK;
+}
+
+static ccz4_status check_params(const ccz4_params *P) {
+  if (!P) {
+    set_error("params is NULL");
+    return CCZ4_ERR_INVALID;
+  }
+  if (P->slicing != CCZ4_SLICING_HARMONIC && P->slicing != CCZ4_SLICING_ONE_PLUS_LOG) {
+    set_error("unknown slicing %d", P->slicing);
+    return CCZ4_ERR_INVALID;
+  }
+  if (P->shift != CCZ4_SHIFT_ZERO && P->shift != CCZ4_SHIFT_GAMMA_DRIVER) {
+    set_error("unknown shift condition %d", P->shift);
+    return CCZ4_ERR_INVALID;
+  }
+  if (P->precision != CCZ4_PREC_FP64) {
+    set_error("precision %d is not available in this build", P->precision);
+    return CCZ4_ERR_INVALID;
+  }
+  if (!(P->tau != 0.0)) {
+    set_error("tau must be non-zero");
+    return CCZ4_ERR_INVALID;
+  }
+  return CCZ4_OK;
+}
+
+static void free_all(ccz4_grid *g) {
+  for (int b = 0; b < 7; ++b) cudaFree(g->buf[b]);
+  cudaFree(g->d_ijk);
+  cudaFree(g->d_owner);
+  cudaFree(g->d_gcoord);
+  cudaFree(g->d_status);
+  cudaFree(g->red_partial);
+  cudaFree(g->red_out);
+  cudaFreeHost(g->host_out);
+  free(g);
+}
+
+extern "C" ccz4_status ccz4_alloc_patches(const ccz4_grid_desc *d, ccz4_grid **out) {
+  if (!out) {
+    set_error("out is NULL");
+    return CCZ4_ERR_INVALID;
+  }
+  *out = nullptr;
+  if (!d) {
+    set_error("descriptor is NULL");
+    return CCZ4_ERR_INVALID;
+  }
+  if (d->p < 1 || d->np[0] < 1 || d->np[1] < 1 || d->np[2] < 1 || !(d->dx > 0.0)) {
+    set_error("invalid sizes: p=%d np=(%d,%d,%d) dx=%g", d->p, d->np[0], d->np[1], d->np[2], d->dx);
+    return CCZ4_ERR_INVALID;
+  }
+  if (d->bc != CCZ4_BC_PERIODIC && d->bc != CCZ4_BC_COPY && d->bc != CCZ4_BC_SOMMERFELD) {
+    set_error("unknown boundary kind %d", d->bc);
+    return CCZ4_ERR_INVALID;
+  }
+  const long long slots = (long long)d->np[0] * d->np[1] * d->np[2];
+  if (slots != d->n_patches || !d->ijk) {
+    set_error("n_patches (%d) must equal np0*np1*np2 (%lld) and ijk must be given", d->n_patches, slots);
+    return CCZ4_ERR_INVALID;
+  }
+  const long long Nx = (long long)d->np[0] * d->p, Ny = (long long)d->np[1] * d->p, Nz = (long long)d->np[2] * d->p;
+  if (Nx + 2 * HALO > (1 << 30) || Ny + 2 * HALO > (1 << 30) || Nz + 2 * HALO > (1 << 30)) {
+    set_error("domain too large for 32-bit point coordinates");
+    return CCZ4_ERR_INVALID;
+  }
+  std::vector<int> owner((size_t)slots, -1);
+  for (int n = 0; n < d->n_patches; ++n) {
+    const int a = d->ijk[3 * n], b = d->ijk[3 * n + 1], c = d->ijk[3 * n + 2];
+    if (a < 0 || a >= d->np[0] || b < 0 || b >= d->np[1] || c < 0 || c >= d->np[2]) {
+      set_error("patch %d has coordinates (%d,%d,%d) outside the %dx%dx%d block", n, a, b, c, d->np[0],
+                d->np[1], d->np[2]);
+      return CCZ4_ERR_INVALID;
+    }
+    const long long cell = ((long long)c * d->np[1] + b) * d->np[0] + a;
+    if (owner[cell] >= 0) {
+      set_error("patch slot (%d,%d,%d) is listed twice", a, b, c);
+      return CCZ4_ERR_INVALID;
+    }
+    owner[cell] = n;
+  }
+  ccz4_grid *g = (ccz4_grid *)calloc(1, sizeof(ccz4_grid));
+  if (!g) {
+    set_error("host allocation failed");
+    return CCZ4_ERR_NOMEM;
+  }
+  GridView &v = g->v;
+  v.p = d->p;
+  v.T = d->p + 2 * HALO;
+  for (int q = 0; q < 3; ++q) {
+    v.np[q] = d->np[q];
+    v.origin[q] = d->origin[q];
+  }
+  v.N[0] = (int)Nx;
+  v.N[1] = (int)Ny;
+  v.N[2] = (int)Nz;
+  v.n_patches = d->n_patches;
+  v.bc = d->bc;
+  v.dx = d->dx;
+  v.n_points = (long long)d->n_patches * d->p * d->p * d->p;
+  v.T3 = (long long)v.T * v.T * v.T;
+  std::vector<int> gcoord;
+  if (d->bc == CCZ4_BC_SOMMERFELD) {
+    v.n_ghost = (Nx + 6) * (Ny + 6) * (Nz + 6) - Nx * Ny * Nz;
+    gcoord.reserve((size_t)(3 * v.n_ghost));
+    for (int z = -HALO; z < Nz + HALO; ++z)
+      for (int y = -HALO; y < Ny + HALO; ++y)
+        for (int x = -HALO; x < Nx + HALO; ++x) {
+          if (x >= 0 && x < Nx && y >= 0 && y < Ny && z >= 0 && z < Nz) {
+            x = (int)Nx - 1;  // jump over the interior of this row
+            continue;
+          }
+          gcoord.push_back(x);
+          gcoord.push_back(y);
+          gcoord.push_back(z);
+        }
+  } else {
+    v.n_ghost = 0;
+  }
+  v.S = ((v.n_points + v.n_ghost + 31) / 32) * 32;
+  if (v.S == 0) v.S = 32;
+  cudaGetDevice(&g->device);
+  const long long state_len = (long long)NV * v.S;
+  const long long lens[7] = {state_len, state_len, state_len, state_len, state_len,
+                             d->bc == CCZ4_BC_SOMMERFELD ? state_len : 0,
+                             (long long)NV * v.n_patches * v.T3};
+  for (int b = 0; b < 7; ++b) {
+    g->buf_len[b] = lens[b];
+    if (lens[b] == 0) continue;
+    cudaError_t e = cudaMalloc(&g->buf[b], sizeof(double) * (size_t)lens[b]);
+    if (e != cudaSuccess) {
+      set_error("cudaMalloc of %lld doubles failed: %s", lens[b], cudaGetErrorString(e));
+      cudaGetLastError();
+      free_all(g);
+      return CCZ4_ERR_NOMEM;
+    }
+    cudaMemset(g->buf[b], 0, sizeof(double) * (size_t)lens[b]);
+  }
+  g->red_blocks = constraint_blocks(v.n_points);
+  bool ok = cudaMalloc(&g->d_ijk, sizeof(int) * 3 * (size_t)d->n_patches) == cudaSuccess &&
+            cudaMalloc(&g->d_owner, sizeof(int) * (size_t)slots) == cudaSuccess &&
+            cudaMalloc(&g->d_gcoord, sizeof(int) * (gcoord.size() > 0 ? gcoord.size() : 3)) == cudaSuccess &&
+            cudaMalloc(&g->d_status, sizeof(unsigned)) == cudaSuccess &&
+            cudaMalloc(&g->red_partial, sizeof(double) * 5 * (size_t)(g->red_blocks > 0 ? g->red_blocks : 1)) ==
+                cudaSuccess &&
+            cudaMalloc(&g->red_out, sizeof(double) * 5) == cudaSuccess &&
+            cudaMallocHost(&g->host_out, sizeof(double) * 5) == cudaSuccess;
+  if (!ok) {
+    set_error("device allocation of grid tables failed: %s", cudaGetErrorString(cudaGetLastError()));
+    free_all(g);
+    return CCZ4_ERR_NOMEM;
+  }
+  cudaMemcpy(g->d_ijk, d->ijk, sizeof(int) * 3 * (size_t)d->n_patches, cudaMemcpyHostToDevice);
+  cudaMemcpy(g->d_owner, owner.data(), sizeof(int) * (size_t)slots, cudaMemcpyHostToDevice);
+  if (!gcoord.empty())
+    cudaMemcpy(g->d_gcoord, gcoord.data(), sizeof(int) * gcoord.size(), cudaMemcpyHostToDevice);
+  cudaMemset(g->d_status, 0, sizeof(unsigned));
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    set_error("grid set-up failed: %s", cudaGetErrorString(e));
+    free_all(g);
+    return CCZ4_ERR_CUDA;
+  }
+  v.ijk = g->d_ijk;
+  v.owner = g->d_owner;
+  v.gcoord = g->d_gcoord;
+  v.status = g->d_status;
+  *out = g;
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_free_patches(ccz4_grid *g) {
+  if (!g) return CCZ4_OK;
+  cudaDeviceSynchronize();
+  free_all(g);
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_grid_info(const ccz4_grid *g, long long *n_points, long long *n_ghost,
+                                      long long *field_stride) {
+  if (check_grid(g)) return CCZ4_ERR_INVALID;
+  if (n_points) *n_points = g->v.n_points;
+  if (n_ghost) *n_ghost = g->v.n_ghost;
+  if (field_stride) *field_stride = g->v.S;
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_field_ptr(ccz4_grid *g, int buf, double **dev, long long *n_doubles) {
+  if (check_grid(g)) return CCZ4_ERR_INVALID;
+  if (buf < 0 || buf > CCZ4_BUF_TILE || !g->buf[buf]) {
+    set_error("buffer %d does not exist on this grid", buf);
+    return CCZ4_ERR_INVALID;
+  }
+  if (dev) *dev = g->buf[buf];
+  if (n_doubles) *n_doubles = g->buf_len[buf];
+  return CCZ4_OK;
+}
+
+static ccz4_status copy_state(ccz4_grid *g, int buf, double *U, double *G, bool to_device, cudaStream_t s) {
+  const GridView &v = g->v;
+  double *d = g->buf[buf];
+  const cudaMemcpyKind kind = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+  if (v.n_points > 0) {
+    if (to_device)
+      CUDA_TRY(cudaMemcpy2DAsync(d, sizeof(double) * v.S, U, sizeof(double) * v.n_points,
+                                 sizeof(double) * v.n_points, NV, kind, s));
+    else
+      CUDA_TRY(cudaMemcpy2DAsync(U, sizeof(double) * v.n_points, d, sizeof(double) * v.S,
+                                 sizeof(double) * v.n_points, NV, kind, s));
+  }
+  if (v.n_ghost > 0 && G) {
+    if (to_device)
+      CUDA_TRY(cudaMemcpy2DAsync(d + v.n_points, sizeof(double) * v.S, G, sizeof(double) * v.n_ghost,
+                                 sizeof(double) * v.n_ghost, NV, kind, s));
+    else
+      CUDA_TRY(cudaMemcpy2DAsync(G, sizeof(double) * v.n_ghost, d + v.n_points, sizeof(double) * v.S,
+                                 sizeof(double) * v.n_ghost, NV, kind, s));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_upload(ccz4_grid *g, int buf, const double *U, const double *G, void *stream) {
+  if (check_grid(g)) return CCZ4_ERR_INVALID;
+  if (!state_buffer(buf) || !g->buf[buf] || (!U && g->v.n_points > 0)) {
+    set_error("upload: invalid buffer %d or NULL host array", buf);
+    return CCZ4_ERR_INVALID;
+  }
+  if (g->v.n_ghost > 0 && !G) {
+    set_error("upload: this grid has %lld Sommerfeld ghost cells; G must be given", g->v.n_ghost);
+    return CCZ4_ERR_INVALID;
+  }
+  return copy_state(g, buf, const_cast<double *>(U), const_cast<double *>(G), true, (cudaStream_t)stream);
+}
+
+extern "C" ccz4_status ccz4_download(ccz4_grid *g, int buf, double *U, double *G, void *stream) {
+  if (check_grid(g)) return CCZ4_ERR_INVALID;
+  if (buf == CCZ4_BUF_TILE) {
+    if (!U) {
+      set_error("download: NULL host array");
+      return CCZ4_ERR_INVALID;
+    }
+    CUDA_TRY(cudaMemcpyAsync(U, g->buf[buf], sizeof(double) * (size_t)g->buf_len[buf], cudaMemcpyDeviceToHost,
+                             (cudaStream_t)stream));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return CCZ4_OK;
+  }
+  if (!state_buffer(buf) || !g->buf[buf] || (!U && g->v.n_points > 0)) {
+    set_error("download: invalid buffer %d or NULL host array", buf);
+    return CCZ4_ERR_INVALID;
+  }
+  return copy_state(g, buf, U, G, false, (cudaStream_t)stream);
+}
+
+extern "C" ccz4_status ccz4_fill_halos(ccz4_grid *g, int buf, void *stream) {
+  if (check_grid(g)) return CCZ4_ERR_INVALID;
+  if (!state_buffer(buf) || !g->buf[buf]) {
+    set_error("fill_halos: buffer %d is not a state buffer of this grid", buf);
+    return CCZ4_ERR_INVALID;
+  }
+  CUDA_TRY(launch_fill_halos(g->v, g->buf[buf], g->buf[CCZ4_BUF_TILE], (cudaStream_t)stream));
+  return CCZ4_OK;
+}
+
+static const double *ini_ptr(ccz4_grid *g) {
+  return g->buf[CCZ4_BUF_INI] ? g->buf[CCZ4_BUF_INI] : g->buf[CCZ4_BUF_U];
+}
+
+extern "C" ccz4_status ccz4_rhs(ccz4_grid *g, const ccz4_params *P, int in_buf, int out_buf, void *stream) {
+  if (check_grid(g) || check_params(P)) return CCZ4_ERR_INVALID;
+  if (!state_buffer(in_buf) || !state_buffer(out_buf) || in_buf == out_buf || !g->buf[in_buf] ||
+      !g->buf[out_buf] || out_buf == CCZ4_BUF_INI) {
+    set_error("rhs: invalid buffers in=%d out=%d", in_buf, out_buf);
+    return CCZ4_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(launch_fill_halos(g->v, g->buf[in_buf], g->buf[CCZ4_BUF_TILE], s));
+  CUDA_TRY(launch_rhs(g->v, *P, g->buf[CCZ4_BUF_TILE], g->buf[in_buf], ini_ptr(g), g->buf[out_buf], s));
+  return CCZ4_OK;
+}
+
+static const int kStageIn[4] = {CCZ4_BUF_U, CCZ4_BUF_Y0, CCZ4_BUF_Y1, CCZ4_BUF_Y0};
+static const int kStageOut[4] = {CCZ4_BUF_Y0, CCZ4_BUF_Y1, CCZ4_BUF_Y0, CCZ4_BUF_U};
+
+static ccz4_status stage_kernel(ccz4_grid *g, const ccz4_params *P, int stage, double dt, cudaStream_t s) {
+  double *in = g->buf[kStageIn[stage]];
+  CUDA_TRY(launch_rk_stage(g->v, *P, stage, dt, g->buf[CCZ4_BUF_TILE], in, ini_ptr(g), g->buf[CCZ4_BUF_U],
+                           g->buf[CCZ4_BUF_ACC], g->buf[kStageOut[stage]], s));
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_stage_buffers(int stage, int *in_buf, int *out_buf) {
+  if (stage < 0 || stage > 3) {
+    set_error("stage must be 0..3 (got %d)", stage);
+    return CCZ4_ERR_INVALID;
+  }
+  if (in_buf) *in_buf = kStageIn[stage];
+  if (out_buf) *out_buf = kStageOut[stage];
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_rk_stage(ccz4_grid *g, const ccz4_params *P, int stage, double dt, void *stream) {
+  if (check_grid(g) || check_params(P)) return CCZ4_ERR_INVALID;
+  if (stage < 0 || stage > 3 || !(dt == dt)) {
+    set_error("rk_stage: stage must be 0..3 (got %d) and dt finite", stage);
+    return CCZ4_ERR_INVALID;
+  }
+  return stage_kernel(g, P, stage, dt, (cudaStream_t)stream);
+}
+
+extern "C" ccz4_status ccz4_step(ccz4_grid *g, const ccz4_params *P, double dt, int n_steps, void *stream) {
+  if (check_grid(g) || check_params(P)) return CCZ4_ERR_INVALID;
+  if (n_steps < 0 || !(dt == dt)) {
+    set_error("step: n_steps must be >= 0 and dt finite");
+    return CCZ4_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int n = 0; n < n_steps; ++n)
+    for (int st = 0; st < 4; ++st) {
+      CUDA_TRY(launch_fill_halos(g->v, g->buf[kStageIn[st]], g->buf[CCZ4_BUF_TILE], s));
+      ccz4_status r = stage_kernel(g, P, st, dt, s);
+      if (r != CCZ4_OK) return r;
+    }
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_evolve_host(ccz4_grid *g, const ccz4_params *P, double dt, int n_steps,
+                                        const double *U_in, const double *G_in, double *U_out, double *G_out,
+                                        void *stream) {
+  ccz4_status st = ccz4_upload(g, CCZ4_BUF_U, U_in, G_in, stream);
+  if (st != CCZ4_OK) return st;
+  st = ccz4_step(g, P, dt, n_steps, stream);
+  if (st != CCZ4_OK) return st;
+  return ccz4_download(g, CCZ4_BUF_U, U_out, G_out, stream);
+}
+
+extern "C" ccz4_status ccz4_enforce(ccz4_grid *g, int buf, void *stream) {
+  if (check_grid(g)) return CCZ4_ERR_INVALID;
+  if (!state_buffer(buf) || !g->buf[buf]) {
+    set_error("enforce: buffer %d is not a state buffer of this grid", buf);
+    return CCZ4_ERR_INVALID;
+  }
+  CUDA_TRY(launch_enforce(g->v, g->buf[buf], (cudaStream_t)stream));
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_constraints(ccz4_grid *g, int buf, double out[5], double *dev_H, double *dev_M,
+                                        void *stream) {
+  if (check_grid(g)) return CCZ4_ERR_INVALID;
+  if (!state_buffer(buf) || !g->buf[buf] || !out) {
+    set_error("constraints: invalid buffer %d or NULL out", buf);
+    return CCZ4_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(launch_fill_halos(g->v, g->buf[buf], g->buf[CCZ4_BUF_TILE], s));
+  CUDA_TRY(launch_constraints(g->v, g->buf[CCZ4_BUF_TILE], dev_H, dev_M, g->red_partial, g->red_blocks,
+                              g->red_out, s));
+  CUDA_TRY(cudaMemcpyAsync(g->host_out, g->red_out, sizeof(double) * 5, cudaMemcpyDeviceToHost, s));
+  unsigned status = 0;
+  CUDA_TRY(cudaMemcpyAsync(&status, g->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  memcpy(out, g->host_out, sizeof(double) * 5);
+  if (status & STATUS_BOUNDS) {
+    set_error("a kernel met a point outside the grid (device status %u)", status);
+    return CCZ4_ERR_BOUNDS;
+  }
+  if (out[4] > 0.0) {
+    set_error("%.0f points have non-finite constraint values", out[4]);
+    return CCZ4_ERR_NONFINITE;
+  }
+  return CCZ4_OK;
+}
+
+extern "C" const char *ccz4_last_error(void) { return g_err; }

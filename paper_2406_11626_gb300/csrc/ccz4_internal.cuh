@@ -1,0 +1,126 @@
+// Internal definitions shared by the CUDA translation units of the CCZ4
+// library: the device view of a grid, point lookup across patches and the
+// boundary, and host-side error plumbing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ccz4.h"
+
+namespace ccz4 {
+
+constexpr int NV = CCZ4_NV;
+constexpr int HALO = CCZ4_HALO;
+
+// Device-side status bits (OR-ed by kernels, read at synchronising calls).
+constexpr unsigned STATUS_BOUNDS = 1u;
+
+// Field indices in the order of the C ABI.
+enum : int {
+  GXX = 0, GXY, GXZ, GYY, GYZ, GZZ, ALPHA, BETAX, BETAY, BETAZ, PHI,
+  AXX, AXY, AXZ, AYY, AYZ, AZZ, KTR, THETA, GHX, GHY, GHZ, BBX, BBY, BBZ
+};
+
+// Plain-data view of a grid, passed by value to every kernel.
+struct GridView {
+  int p, T;                    // points per patch edge; tile edge p + 2*HALO
+  int np[3], N[3];             // patches and points per axis
+  int n_patches;
+  int bc;
+  long long n_points;          // n_patches * p^3
+  long long n_ghost;           // Sommerfeld ghost cells (0 otherwise)
+  long long S;                 // field stride of state-shaped buffers
+  long long T3;                // T^3
+  double origin[3], dx;
+  const int *ijk;              // [n_patches][3]
+  const int *owner;            // [np2][np1][np0] -> patch id
+  const int *gcoord;           // [n_ghost][3] global coordinates of the ghost cells
+  unsigned *status;            // device status word
+};
+
+__host__ __device__ __forceinline__ int wrap(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+__host__ __device__ __forceinline__ int clampi(int a, int lo, int hi) {
+  return a < lo ? lo : (a > hi ? hi : a);
+}
+
+// Rank of an outside cell (x, y, z) within the ghost shell of width HALO,
+// cells counted in lexicographic (z, y, x) order. Closed form: whole planes
+// (z outside) contribute Mx*My cells, planes with z inside contribute
+// Mx*My - Nx*Ny; within a plane with z inside, rows with y outside
+// contribute Mx cells and rows with y inside 2*HALO cells.
+__host__ __device__ __forceinline__ long long ghost_rank(const GridView &g, int x, int y, int z) {
+  const long long Mx = g.N[0] + 2 * HALO, My = g.N[1] + 2 * HALO;
+  const int zz = z + HALO, yy = y + HALO, xx = x + HALO;
+  const long long full_planes = (zz < HALO ? zz : HALO) + (zz > g.N[2] + HALO ? zz - (g.N[2] + HALO) : 0);
+  const long long inner_planes = clampi(zz - HALO, 0, g.N[2]);
+  long long r = full_planes * Mx * My + inner_planes * (Mx * My - (long long)g.N[0] * g.N[1]);
+  if (z < 0 || z >= g.N[2]) return r + (long long)yy * Mx + xx;
+  const long long full_rows = (yy < HALO ? yy : HALO) + (yy > g.N[1] + HALO ? yy - (g.N[1] + HALO) : 0);
+  const long long inner_rows = clampi(yy - HALO, 0, g.N[1]);
+  r += full_rows * Mx + inner_rows * (2 * HALO);
+  if (y < 0 || y >= g.N[1]) return r + xx;
+  return r + (x < 0 ? xx : HALO + (x - g.N[0]));
+}
+
+// Index, within a field of a state-shaped buffer, of the value at global
+// point (x, y, z), which may lie up to HALO points outside the domain.
+// Returns -1 if the point cannot be resolved (sets the bounds status bit).
+__device__ __forceinline__ long long locate(const GridView &g, int x, int y, int z) {
+  const bool inside = x >= 0 && x < g.N[0] && y >= 0 && y < g.N[1] && z >= 0 && z < g.N[2];
+  if (!inside) {
+    if (g.bc == CCZ4_BC_PERIODIC) {
+      x = wrap(x, g.N[0]); y = wrap(y, g.N[1]); z = wrap(z, g.N[2]);
+    } else if (g.bc == CCZ4_BC_COPY) {
+      x = clampi(x, 0, g.N[0] - 1); y = clampi(y, 0, g.N[1] - 1); z = clampi(z, 0, g.N[2] - 1);
+    } else {
+      if (x < -HALO || x >= g.N[0] + HALO || y < -HALO || y >= g.N[1] + HALO ||
+          z < -HALO || z >= g.N[2] + HALO) {
+        atomicOr(g.status, STATUS_BOUNDS);
+        return -1;
+      }
+      return g.n_points + ghost_rank(g, x, y, z);
+    }
+  }
+  const int p = g.p;
+  const int px = x / p, py = y / p, pz = z / p;
+  const int n = __ldg(g.owner + ((long long)pz * g.np[1] + py) * g.np[0] + px);
+  return (long long)n * p * p * p + ((long long)(z - pz * p) * p + (y - py * p)) * p + (x - px * p);
+}
+
+}  // namespace ccz4
+
+// Host-side helpers implemented in ccz4_capi.cu.
+namespace ccz4 {
+void set_error(const char *fmt, ...);
+}
+
+struct ccz4_grid {
+  ccz4::GridView v;
+  int device;
+  double *buf[7];            // U, Y0, Y1, ACC, RHS, INI, TILE
+  long long buf_len[7];      // doubles
+  int *d_ijk, *d_owner, *d_gcoord;
+  unsigned *d_status;
+  double *red_partial;       // per-block partial sums of the constraint reduction
+  int red_blocks;
+  double *red_out;           // device [5]
+  double *host_out;          // pinned [5]
+};
+
+// Kernel launchers (one translation unit each).
+namespace ccz4 {
+cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile, cudaStream_t s);
+cudaError_t launch_rhs(const GridView &g, const ccz4_params &P, const double *tile, const double *in,
+                       const double *ini, double *out, cudaStream_t s);
+cudaError_t launch_rk_stage(const GridView &g, const ccz4_params &P, int stage, double dt,
+                            const double *tile, const double *in, const double *ini, const double *U,
+                            double *acc, double *out, cudaStream_t s);
+cudaError_t launch_enforce(const GridView &g, double *U, cudaStream_t s);
+cudaError_t launch_constraints(const GridView &g, const double *tile, double *H, double *M,
+                               double *partial, int blocks, double *out5, cudaStream_t s);
+}  // namespace ccz4

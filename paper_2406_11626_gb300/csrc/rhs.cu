@@ -1,0 +1,159 @@
+// Right-hand side and fused RK4 stage kernels.
+//
+// interior_kernel: one thread per interior point reads its halo'd
+// neighbourhood from the tile buffer, evaluates the CCZ4 right-hand side
+// plus Kreiss-Oliger dissipation, and either stores it (plain RHS) or
+// applies the RK4 stage update in the same pass, so the right-hand side
+// never travels through HBM. The last stage also enforces the algebraic
+// constraints on the new state.
+// ghost_kernel: one thread per evolved Sommerfeld ghost cell (Eq.
+// exa_sommerfeld_inter), same stage update, no enforcement.
+#include "ccz4_algebra.cuh"
+
+namespace ccz4 {
+namespace {
+
+struct StageArgs {
+  const double *U;  // U_n
+  double *acc;      // RK accumulator
+  double *out;      // plain RHS (MODE < 0), next stage state, or U_{n+1}
+  double dt;
+};
+
+// MODE < 0: store k. MODE = s in 0..3: RK4 stage s.
+template <int MODE>
+__device__ __forceinline__ void finish_point(const GridView &g, long long i, double k[NV],
+                                             const StageArgs &a, bool interior) {
+  const long long S = g.S;
+  if (MODE < 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) a.out[v * S + i] = k[v];
+    return;
+  }
+  if (MODE == 0 || MODE == 1 || MODE == 2) {
+    const double c = (MODE == 2) ? a.dt : 0.5 * a.dt;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double u = a.U[v * S + i];
+      if (MODE == 0) a.acc[v * S + i] = k[v];
+      else a.acc[v * S + i] = fma(2.0, k[v], a.acc[v * S + i]);
+      a.out[v * S + i] = fma(c, k[v], u);
+    }
+    return;
+  }
+  // MODE == 3: U_{n+1} = U_n + dt/6 (k0 + 2 k1 + 2 k2 + k3)
+  const double c6 = a.dt * (1.0 / 6.0);
+  double un[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) un[v] = fma(c6, a.acc[v * S + i] + k[v], a.U[v * S + i]);
+  if (interior) enforce_point(un + GXX, un + AXX);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) a.out[v * S + i] = un[v];
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) interior_kernel(GridView g, ccz4_params P, StencilCoef C,
+                                                       const double *__restrict__ tile, StageArgs a) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n_points) return;
+  const int p = g.p, T = g.T;
+  const long long p3 = (long long)p * p * p;
+  const int n = (int)(i / p3);
+  const int r = (int)(i - n * p3);
+  const int z = r / (p * p), y = (r / p) % p, x = r % p;
+  Nbhd N;
+  N.c = tile + n * g.T3 + ((long long)(z + HALO) * T + (y + HALO)) * T + (x + HALO);
+  N.fs = (long long)g.n_patches * g.T3;
+  N.st[0] = 1;
+  N.st[1] = T;
+  N.st[2] = T * T;
+  double k[NV];
+  ccz4_rhs_point(P, N, C, k);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) k[v] += ko_sum(N, v, C.cko);
+  finish_point<MODE>(g, i, k, a, true);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) ghost_kernel(GridView g, ccz4_params P, const double *__restrict__ in,
+                                                    const double *__restrict__ ini, StageArgs a) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= g.n_ghost) return;
+  int c[3] = {__ldg(g.gcoord + 3 * id), __ldg(g.gcoord + 3 * id + 1), __ldg(g.gcoord + 3 * id + 2)};
+  // the face a ghost cell belongs to: its highest outside axis
+  int d = 0, side = 0;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (c[q] < 0) { d = q; side = -1; }
+    if (c[q] >= g.N[q]) { d = q; side = 1; }
+  }
+  int nb[3] = {c[0], c[1], c[2]};
+  nb[d] -= side;
+  const long long sn = locate(g, nb[0], nb[1], nb[2]);
+  if (sn < 0 || side == 0) return;
+  double xs[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) xs[q] = g.origin[q] + (c[q] + 0.5) * g.dx;
+  const double rr = sqrt(xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2]);
+  const double ir = 1.0 / rr;
+  const double geo = rr / xs[d] * (side > 0 ? 1.0 : -1.0) / g.dx;  // (r / x_d) * sign / dx
+  const long long self = g.n_points + id;
+  double k[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double qg = __ldg(in + v * g.S + self);
+    const double qn = __ldg(in + v * g.S + sn);
+    const double cv = P.somm_speed[v];
+    k[v] = -cv * geo * (qg - qn) - cv * ir * (qg - __ldg(ini + v * g.S + self));
+  }
+  finish_point<MODE>(g, self, k, a, false);
+}
+
+StencilCoef coefs(const GridView &g, const ccz4_params &P) {
+  StencilCoef C;
+  C.c1 = 1.0 / (12.0 * g.dx);
+  C.c2 = 1.0 / (12.0 * g.dx * g.dx);
+  C.c3 = 1.0 / (144.0 * g.dx * g.dx);
+  C.cko = P.ko_eps / (64.0 * g.dx);
+  return C;
+}
+
+template <int MODE>
+cudaError_t launch_mode(const GridView &g, const ccz4_params &P, const double *tile, const double *in,
+                        const double *ini, const StageArgs &a, cudaStream_t s) {
+  if (g.n_points > 0) {
+    const long long blocks = (g.n_points + 127) / 128;
+    interior_kernel<MODE><<<(unsigned)blocks, 128, 0, s>>>(g, P, coefs(g, P), tile, a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (g.n_ghost > 0) {
+    const long long blocks = (g.n_ghost + 127) / 128;
+    ghost_kernel<MODE><<<(unsigned)blocks, 128, 0, s>>>(g, P, in, ini, a);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_rhs(const GridView &g, const ccz4_params &P, const double *tile, const double *in,
+                       const double *ini, double *out, cudaStream_t s) {
+  StageArgs a{nullptr, nullptr, out, 0.0};
+  return launch_mode<-1>(g, P, tile, in, ini, a, s);
+}
+
+cudaError_t launch_rk_stage(const GridView &g, const ccz4_params &P, int stage, double dt,
+                            const double *tile, const double *in, const double *ini, const double *U,
+                            double *acc, double *out, cudaStream_t s) {
+  StageArgs a{U, acc, out, dt};
+  switch (stage) {
+    case 0: return launch_mode<0>(g, P, tile, in, ini, a, s);
+    case 1: return launch_mode<1>(g, P, tile, in, ini, a, s);
+    case 2: return launch_mode<2>(g, P, tile, in, ini, a, s);
+    case 3: return launch_mode<3>(g, P, tile, in, ini, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ccz4

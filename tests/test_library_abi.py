@@ -1,0 +1,32 @@
+"""The CUDA library loads on a machine without a GPU and exports every
+function that include/ccz4.h declares (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ccz4.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ccz4_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_hot_path_calls():
+    names = _declared()
+    for n in ("ccz4_alloc_patches", "ccz4_fill_halos", "ccz4_rhs", "ccz4_rk_stage", "ccz4_constraints"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2406_11626_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_library_is_built_for_sm_103a():
+    from paper_2406_11626_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.NVCC_FLAGS)
