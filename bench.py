@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--workload", default="puncture144", choices=["puncture144", "small"],
+                    help="small: the same physics on 54^3 points (6^3 patches), for profiler captures")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     return ap.parse_args()
 
 
@@ -166,14 +169,21 @@ def run_reference(args):
     return 0
 
 
-def workload_config(g, precision="fp64", K=None):
+def workload_config(g, precision="fp64", K=None, workload="puncture144"):
     from paper_2406_11626_gb300 import inputs as I
-    cfg = I.single_puncture_config()
-    c = {"workload": "single puncture M=1, [-8,8]^3, 16^3 patches of 9^3 (144^3 points), "
-                     "1+log, Gamma-driver eta=2, KO 0.1, Sommerfeld, RK4 dt=0.1dx",
+    if workload == "small":
+        cfg = I.single_puncture_config(n_side=6, half_width=3.0)
+        name = "single puncture M=1, [-3,3]^3, 6^3 patches of 9^3 (54^3 points), profiling case"
+    else:
+        cfg = I.single_puncture_config()
+        name = ("single puncture M=1, [-8,8]^3, 16^3 patches of 9^3 (144^3 points), "
+                "1+log, Gamma-driver eta=2, KO 0.1, Sommerfeld, RK4 dt=0.1dx")
+    c = {"workload": name,
          "patches": cfg.n_patches, "p": cfg.p, "points": cfg.n_points, "dx": cfg.dx,
          "precision": precision,
-         "l2": "inputs larger than L2: each state buffer is 25 x 3.38M doubles = 675 MB"}
+         "l2": "inputs larger than L2 (129 MB): each state buffer is 25 x %.2fM doubles = %.0f MB, "
+               "the halo tiles %.0f MB" % ((cfg.n_points + 0) / 1e6, 8 * 25 * cfg.n_points / 1e6,
+                                         8 * 25 * cfg.n_patches * (cfg.p + 6) ** 3 / 1e6)}
     if g is not None:
         c["ghost_cells"] = g.n_ghost
     return c
@@ -193,6 +203,57 @@ def load_traffic():
     return d.get("bytes_per_launch")
 
 
+def bench_config(args):
+    from paper_2406_11626_gb300 import inputs as I
+    if args.workload == "small":
+        return I.single_puncture_config(n_side=6, half_width=3.0)
+    return I.single_puncture_config()
+
+
+def time_path(C, I, cfg, precision, K, W, stream, dist, clocks_index=None):
+    """Builds a grid, runs W warm-up and K timed RK4 steps; returns the grid,
+    the time of the K steps and the per-stage kernel times (ms)."""
+    import torch
+    g = C.Grid.from_config(cfg)
+    U0, G0 = I.initial_state(cfg)
+    g.upload(U0, G0)
+    g.upload(U0, G0, buf="INI")
+    P = C.make_params(**cfg.params, precision=precision)
+    bufs = [C.stage_buffers(s) for s in range(4)]
+
+    def step(ev=None):
+        for s in range(4):
+            g.fill_halos(bufs[s][0], stream)
+            if ev is not None:
+                ev[s][0].record(stream)
+            g.rk_stage(P, s, cfg.dt, stream, fill=False)
+            if ev is not None:
+                ev[s][1].record(stream)
+
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize()
+    kev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(4)] for _ in range(K)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(clocks_index) if clocks_index is not None else None
+    if clk:
+        clk.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(K):
+        step(kev[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop() if clk else None
+    ms = e0.elapsed_time(e1)
+    stage_ms = [kev[k][s][0].elapsed_time(kev[k][s][1]) for k in range(K) for s in range(4)]
+    return g, P, ms, stage_ms, clocks
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -206,45 +267,10 @@ def run_gb300(args):
         dist.init_process_group("nccl")
     from paper_2406_11626_gb300 import ccz4 as C
     from paper_2406_11626_gb300 import inputs as I
-    cfg = I.single_puncture_config()
-    g = C.Grid.from_config(cfg)
-    U0, G0 = I.initial_state(cfg)
-    g.upload(U0, G0)
-    g.upload(U0, G0, buf="INI")
-    P = C.make_params(**cfg.params, precision=args.precision)
+    cfg = bench_config(args)
     stream = torch.cuda.current_stream()
-    bufs = [C.stage_buffers(s) for s in range(4)]
-
-    def step(ev=None):
-        for s in range(4):
-            g.fill_halos(bufs[s][0], stream)
-            if ev is not None:
-                ev[s][0].record(stream)
-            g.rk_stage(P, s, cfg.dt, stream, fill=False)
-            if ev is not None:
-                ev[s][1].record(stream)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
     K = args.steps
-    kev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(4)] for _ in range(K)]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clk = ClockSampler(local)
-    clk.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for k in range(K):
-        step(kev[k])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    stage_ms = [kev[k][s][0].elapsed_time(kev[k][s][1]) for k in range(K) for s in range(4)]
+    g, P, ms, stage_ms, clocks = time_path(C, I, cfg, args.precision, K, args.warmup, stream, dist, local)
     ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
     if dist:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
@@ -272,6 +298,34 @@ def run_gb300(args):
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = world * cfg.n_points * 4 * E / float(te.item())
 
+    mixed = None
+    if not args.no_mixed and args.precision == "fp64":
+        # the mixed path on the same workload, same steps; its state is
+        # compared with the FP64 state after the same W + K steps
+        g64, _, _, _, _ = time_path(C, I, cfg, "fp64", K, args.warmup, stream, None)
+        gmx, _, ms_mx, stage_mx, _ = time_path(C, I, cfg, "mixed", K, args.warmup, stream, None)
+        a, _ = g64.download("U")
+        b, _ = gmx.download("U")
+        a = a.reshape(I.NV, -1)
+        b = b.reshape(I.NV, -1)
+        err = np.abs(b - a).max(axis=1) / np.maximum(np.abs(a).max(axis=1), 1.0)
+        c64 = g64.constraints("U", raise_nonfinite=False)
+        cmx = gmx.constraints("U", raise_nonfinite=False)
+        flm = C.flops_per_point_stage("mixed")
+        t_stage_mx = sum(stage_mx) / len(stage_mx) * 1e-3
+        t_roof_mx = max(flm["fp64"] * cfg.n_points / (FP64_PEAK_TFLOPS * 1e12),
+                        flm["fp32"] * cfg.n_points / (FP32_PEAK_TFLOPS * 1e12))
+        mixed = {"value": world * cfg.n_points * 4 * K / (ms_mx * 1e-3), "unit": UNIT,
+                 "speedup_vs_fp64": ms / ms_mx, "ms_per_step": ms_mx / K,
+                 "dtype": "f64 state/differences/1-over-phi terms/update + f32 algebra",
+                 "max_rel_state_error_vs_fp64": float(err.max()),
+                 "worst_field": I.FIELDS[int(err.argmax())],
+                 "after_steps": K + args.warmup,
+                 "L2_H": cmx[0], "L2_H_fp64": c64[0], "L2_M": cmx[1], "L2_M_fp64": c64[1],
+                 "roofline_frac": t_roof_mx / t_stage_mx,
+                 "fp64_flops_per_point_stage": flm["fp64"], "fp32_flops_per_point_stage": flm["fp32"]}
+        del g64, gmx
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -284,21 +338,22 @@ def run_gb300(args):
         roof = {"bound": "alu", "achieved": f64 / t_stage / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": f64 / t_stage / 1e12 / FP64_PEAK_TFLOPS, "traffic": load_traffic(),
                 "kernel": "interior_kernel (fused RHS + RK stage) with the ghost-cell kernel of the same stage",
-                "flops_per_point_stage": fl["fp64"],
+                "flops_per_point_stage": fl["fp64"], "units_per_launch": cfg.n_points,
                 "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz"}
     else:
         t_roof = max(f64 / (FP64_PEAK_TFLOPS * 1e12), f32 / (FP32_PEAK_TFLOPS * 1e12))
-        roof = {"bound": "alu", "achieved": t_roof / t_stage, "peak": 1.0, "unit": "fraction of max(F64/P64, F32/P32)",
+        roof = {"bound": "alu", "achieved": f64 / t_stage / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": t_roof / t_stage, "traffic": load_traffic(),
                 "fp64_flops_per_point_stage": fl["fp64"], "fp32_flops_per_point_stage": fl["fp32"],
-                "fp64_tflops": f64 / t_stage / 1e12, "fp32_tflops": f32 / t_stage / 1e12}
+                "fp32_tflops": f32 / t_stage / 1e12,
+                "note": "frac = max(F64/P64, F32/P32) / kernel time"}
     launches_per_stage = 2 + (1 if g.n_ghost > 0 else 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f64 state + f32 algebra",
         "data": "synthetic (Brill-Lindquist puncture data generated in closed form)",
-        "config": workload_config(g, args.precision, K),
+        "config": workload_config(g, args.precision, K, args.workload),
         "stage_kernel_ms": sum(stage_ms) / len(stage_ms),
         "roofline": roof,
         "clocks": clocks,
@@ -308,6 +363,8 @@ def run_gb300(args):
         "gpu_launches": launches_per_stage * 4 * K,
         "constraints_after": {"L2_H": out[0], "L2_M": out[1], "max_H": out[2], "nonfinite": out[4]},
     }
+    if mixed is not None:
+        line["mixed"] = mixed
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

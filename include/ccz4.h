@@ -210,6 +210,17 @@ ccz4_status ccz4_enforce(ccz4_grid *g, int buf, void *stream);
 ccz4_status ccz4_constraints(ccz4_grid *g, int buf, double out[5], double *dev_H, double *dev_M,
                              void *stream);
 
+/* Arithmetic of one interior point-stage of the fused stage kernel for the
+   given parameters and precision: the right-hand side, the dissipation, the
+   RK4 update (the mean over the four stages) and a quarter of the
+   enforcement, counted on the host by running the kernel's own templates
+   with operation-counting scalars (add, sub, mul = 1 flop; FMA = 2;
+   division = 1). Needs no GPU. out[0] = FP64 flops, out[1] = FP32 flops,
+   out[2] = FP64 divisions and roots, out[3] = precision conversions,
+   out[4] = FP64 FMAs, out[5] = FP64 adds and multiplies. These are the
+   algorithmic flops behind the roofline of the stage kernel. */
+ccz4_status ccz4_flops_per_point_stage(const ccz4_params *P, double out[6]);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *ccz4_last_error(void);
 

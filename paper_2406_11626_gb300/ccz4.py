@@ -78,6 +78,8 @@ def lib():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    L.ccz4_flops_per_point_stage.argtypes = [ctypes.POINTER(Params), _dbl_p]
+    L.ccz4_flops_per_point_stage.restype = ctypes.c_int
     L.ccz4_last_error.restype = ctypes.c_char_p
     L.ccz4_last_error.argtypes = []
     _lib = L
@@ -103,6 +105,18 @@ def make_params(kappa1=1.0, kappa2=0.0, kappa3=0.0, e=1.0, c=1.0, tau=1.0, mu=0.
     for i in range(NV):
         P.somm_speed[i] = float(sp[i])
     return P
+
+
+def flops_per_point_stage(precision="fp64", P=None):
+    """Algorithmic flops of one interior point-stage of the stage kernel
+    (counted on the host from the kernel's own templates)."""
+    if P is None:
+        from .inputs import PUNCTURE_PARAMS
+        P = make_params(**PUNCTURE_PARAMS, precision=precision)
+    out = (ctypes.c_double * 6)()
+    _check(lib().ccz4_flops_per_point_stage(ctypes.byref(P), out))
+    return {"fp64": out[0], "fp32": out[1], "fp64_div_root": out[2], "conversions": out[3],
+            "fp64_fma": out[4], "fp64_add_mul": out[5]}
 
 
 def stage_buffers(stage):

@@ -60,8 +60,8 @@ static ccz4_status check_params(const ccz4_params *P) {
     set_error("unknown shift condition %d", P->shift);
     return CCZ4_ERR_INVALID;
   }
-  if (P->precision != CCZ4_PREC_FP64) {
-    set_error("precision %d is not available in this build", P->precision);
+  if (P->precision != CCZ4_PREC_FP64 && P->precision != CCZ4_PREC_MIXED) {
+    set_error("unknown precision %d", P->precision);
     return CCZ4_ERR_INVALID;
   }
   if (!(P->tau != 0.0)) {

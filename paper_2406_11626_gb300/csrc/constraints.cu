@@ -14,7 +14,7 @@ namespace {
 
 constexpr int RED_THREADS = 256;
 
-__device__ void constraints_point(const Nbhd &N, const StencilCoef &C, double &H, double M[3]) {
+__device__ void constraints_point(const Nbhd &N, const StencilCoef<double> &C, double &H, double M[3]) {
   double g[6], A[6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
@@ -28,11 +28,11 @@ __device__ void constraints_point(const Nbhd &N, const StencilCoef &C, double &H
     const int s = N.st[k];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      dg[k][c] = fd1(N, GXX + c, s, C.c1);
-      dA[k][c] = fd1(N, AXX + c, s, C.c1);
+      dg[k][c] = fd1<double>(N, GXX + c, s, C.c1);
+      dA[k][c] = fd1<double>(N, AXX + c, s, C.c1);
     }
-    dP[k] = fd1(N, PHI, s, C.c1);
-    dK[k] = fd1(N, KTR, s, C.c1);
+    dP[k] = fd1<double>(N, PHI, s, C.c1);
+    dK[k] = fd1<double>(N, KTR, s, C.c1);
   }
   double ig[6];
   ig[0] = g[3] * g[5] - g[4] * g[4];
@@ -74,7 +74,7 @@ __device__ void constraints_point(const Nbhd &N, const StencilCoef &C, double &H
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int l = k; l < 3; ++l) dd[c][S6(k, l)] = fdkl(N, GXX + c, k, l, C);
+      for (int l = k; l < 3; ++l) dd[c][S6(k, l)] = fdkl<double>(N, GXX + c, k, l, C);
   // dIg[j][ml] = g~^ma g~^lb d_j g~_ab  (= -d_j g~^ml)
   double dIg[3][6];
 #pragma unroll
@@ -128,7 +128,7 @@ __device__ void constraints_point(const Nbhd &N, const StencilCoef &C, double &H
 #pragma unroll
     for (int j = i; j < 3; ++j) {
       const int c = S6(i, j);
-      cdph[c] = fdkl(N, PHI, i, j, C) - (Gu[0][c] * dP[0] + Gu[1][c] * dP[1] + Gu[2][c] * dP[2]);
+      cdph[c] = fdkl<double>(N, PHI, i, j, C) - (Gu[0][c] * dP[0] + Gu[1][c] * dP[1] + Gu[2][c] * dP[2]);
     }
   double trcdph = 0.0;
 #pragma unroll
@@ -199,7 +199,7 @@ __device__ void constraints_point(const Nbhd &N, const StencilCoef &C, double &H
   }
 }
 
-__global__ void __launch_bounds__(RED_THREADS) constraints_kernel(GridView g, StencilCoef C,
+__global__ void __launch_bounds__(RED_THREADS) constraints_kernel(GridView g, StencilCoef<double> C,
                                                                   const double *__restrict__ tile,
                                                                   double *H, double *M, double *partial) {
   __shared__ double sh[5][RED_THREADS];
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(256) enforce_kernel(GridView g, double *U) {
     gm[c] = U[(GXX + c) * g.S + i];
     A[c] = U[(AXX + c) * g.S + i];
   }
-  enforce_point(gm, A);
+  enforce_point<double>(gm, A);
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
     U[(GXX + c) * g.S + i] = gm[c];
@@ -308,7 +308,7 @@ int constraint_blocks(long long n_points) { return (int)((n_points + RED_THREADS
 
 cudaError_t launch_constraints(const GridView &g, const double *tile, double *H, double *M, double *partial,
                                int blocks, double *out5, cudaStream_t s) {
-  StencilCoef C;
+  StencilCoef<double> C;
   C.c1 = 1.0 / (12.0 * g.dx);
   C.c2 = 1.0 / (12.0 * g.dx * g.dx);
   C.c3 = 1.0 / (144.0 * g.dx * g.dx);

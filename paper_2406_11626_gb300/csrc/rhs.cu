@@ -5,9 +5,10 @@
 // plus Kreiss-Oliger dissipation, and either stores it (plain RHS) or
 // applies the RK4 stage update in the same pass, so the right-hand side
 // never travels through HBM. The last stage also enforces the algebraic
-// constraints on the new state.
+// constraints on the new state. R is the type of the pointwise algebra
+// (double: FP64 path; float: mixed path).
 // ghost_kernel: one thread per evolved Sommerfeld ghost cell (Eq.
-// exa_sommerfeld_inter), same stage update, no enforcement.
+// exa_sommerfeld_inter), same stage update, no enforcement, FP64.
 #include "ccz4_algebra.cuh"
 
 namespace ccz4 {
@@ -30,29 +31,20 @@ __device__ __forceinline__ void finish_point(const GridView &g, long long i, dou
     for (int v = 0; v < NV; ++v) a.out[v * S + i] = k[v];
     return;
   }
-  if (MODE == 0 || MODE == 1 || MODE == 2) {
-    const double c = (MODE == 2) ? a.dt : 0.5 * a.dt;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const double u = a.U[v * S + i];
-      if (MODE == 0) a.acc[v * S + i] = k[v];
-      else a.acc[v * S + i] = fma(2.0, k[v], a.acc[v * S + i]);
-      a.out[v * S + i] = fma(c, k[v], u);
-    }
-    return;
-  }
-  // MODE == 3: U_{n+1} = U_n + dt/6 (k0 + 2 k1 + 2 k2 + k3)
-  const double c6 = a.dt * (1.0 / 6.0);
   double un[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) un[v] = fma(c6, a.acc[v * S + i] + k[v], a.U[v * S + i]);
-  if (interior) enforce_point(un + GXX, un + AXX);
+  for (int v = 0; v < NV; ++v) {
+    double acc = MODE == 0 ? 0.0 : a.acc[v * S + i];
+    un[v] = rk_combine<(MODE < 0 ? 0 : MODE), double>(a.U[v * S + i], acc, k[v], a.dt);
+    if (MODE < 3) a.acc[v * S + i] = acc;
+  }
+  if (MODE == 3 && interior) enforce_point<double>(un + GXX, un + AXX);
 #pragma unroll
   for (int v = 0; v < NV; ++v) a.out[v * S + i] = un[v];
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(128) interior_kernel(GridView g, ccz4_params P, StencilCoef C,
+template <int MODE, class R>
+__global__ void __launch_bounds__(128, 1) interior_kernel(GridView g, Phys<R> P, StencilCoef<double> C,
                                                        const double *__restrict__ tile, StageArgs a) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n_points) return;
@@ -68,9 +60,9 @@ __global__ void __launch_bounds__(128) interior_kernel(GridView g, ccz4_params P
   N.st[1] = T;
   N.st[2] = T * T;
   double k[NV];
-  ccz4_rhs_point(P, N, C, k);
+  ccz4_rhs_point<double, R>(P, N, C, k);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) k[v] += ko_sum(N, v, C.cko);
+  for (int v = 0; v < NV; ++v) k[v] += ko_sum<double>(N, v, C.cko);
   finish_point<MODE>(g, i, k, a, true);
 }
 
@@ -109,8 +101,8 @@ __global__ void __launch_bounds__(128) ghost_kernel(GridView g, ccz4_params P, c
   finish_point<MODE>(g, self, k, a, false);
 }
 
-StencilCoef coefs(const GridView &g, const ccz4_params &P) {
-  StencilCoef C;
+StencilCoef<double> coefs(const GridView &g, const ccz4_params &P) {
+  StencilCoef<double> C;
   C.c1 = 1.0 / (12.0 * g.dx);
   C.c2 = 1.0 / (12.0 * g.dx * g.dx);
   C.c3 = 1.0 / (144.0 * g.dx * g.dx);
@@ -118,12 +110,12 @@ StencilCoef coefs(const GridView &g, const ccz4_params &P) {
   return C;
 }
 
-template <int MODE>
+template <int MODE, class R>
 cudaError_t launch_mode(const GridView &g, const ccz4_params &P, const double *tile, const double *in,
                         const double *ini, const StageArgs &a, cudaStream_t s) {
   if (g.n_points > 0) {
     const long long blocks = (g.n_points + 127) / 128;
-    interior_kernel<MODE><<<(unsigned)blocks, 128, 0, s>>>(g, P, coefs(g, P), tile, a);
+    interior_kernel<MODE, R><<<(unsigned)blocks, 128, 0, s>>>(g, make_phys<R>(P), coefs(g, P), tile, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -135,12 +127,19 @@ cudaError_t launch_mode(const GridView &g, const ccz4_params &P, const double *t
   return cudaSuccess;
 }
 
+template <int MODE>
+cudaError_t launch_prec(const GridView &g, const ccz4_params &P, const double *tile, const double *in,
+                        const double *ini, const StageArgs &a, cudaStream_t s) {
+  if (P.precision == CCZ4_PREC_MIXED) return launch_mode<MODE, float>(g, P, tile, in, ini, a, s);
+  return launch_mode<MODE, double>(g, P, tile, in, ini, a, s);
+}
+
 }  // namespace
 
 cudaError_t launch_rhs(const GridView &g, const ccz4_params &P, const double *tile, const double *in,
                        const double *ini, double *out, cudaStream_t s) {
   StageArgs a{nullptr, nullptr, out, 0.0};
-  return launch_mode<-1>(g, P, tile, in, ini, a, s);
+  return launch_prec<-1>(g, P, tile, in, ini, a, s);
 }
 
 cudaError_t launch_rk_stage(const GridView &g, const ccz4_params &P, int stage, double dt,
@@ -148,10 +147,10 @@ cudaError_t launch_rk_stage(const GridView &g, const ccz4_params &P, int stage, 
                             double *acc, double *out, cudaStream_t s) {
   StageArgs a{U, acc, out, dt};
   switch (stage) {
-    case 0: return launch_mode<0>(g, P, tile, in, ini, a, s);
-    case 1: return launch_mode<1>(g, P, tile, in, ini, a, s);
-    case 2: return launch_mode<2>(g, P, tile, in, ini, a, s);
-    case 3: return launch_mode<3>(g, P, tile, in, ini, a, s);
+    case 0: return launch_prec<0>(g, P, tile, in, ini, a, s);
+    case 1: return launch_prec<1>(g, P, tile, in, ini, a, s);
+    case 2: return launch_prec<2>(g, P, tile, in, ini, a, s);
+    case 3: return launch_prec<3>(g, P, tile, in, ini, a, s);
     default: return cudaErrorInvalidValue;
   }
 }

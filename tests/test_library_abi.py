@@ -30,3 +30,14 @@ def test_library_exports_every_declared_symbol():
 def test_library_is_built_for_sm_103a():
     from paper_2406_11626_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.NVCC_FLAGS)
+
+
+def test_flop_count_is_available_without_a_gpu():
+    """The algorithmic flop count of the stage kernel comes from the host
+    instantiation of the kernel templates with counting scalars."""
+    from paper_2406_11626_gb300 import build, ccz4
+    build.build()
+    f64 = ccz4.flops_per_point_stage("fp64")
+    fmx = ccz4.flops_per_point_stage("mixed")
+    assert f64["fp32"] == 0 and f64["fp64"] > 3000 and f64["conversions"] == 0
+    assert fmx["fp32"] > 1000 and fmx["fp64"] < f64["fp64"] and fmx["conversions"] > 0
