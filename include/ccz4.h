@@ -210,6 +210,30 @@ ccz4_status ccz4_enforce(ccz4_grid *g, int buf, void *stream);
 ccz4_status ccz4_constraints(ccz4_grid *g, int buf, double out[5], double *dev_H, double *dev_M,
                              void *stream);
 
+/* Constraint monitors for callers that cannot allocate device memory (a
+   host framework that owns all device memory and forbids other
+   allocations, or a time loop that must not allocate once running). The
+   paper has no counterpart; this is a service of this library.
+   Computes what ccz4_constraints computes, but from halo tiles the caller
+   already holds, and allocates nothing: it calls no cudaMalloc, cudaFree
+   or allocating library routine.
+     tiles    device, [25][n_patches][(p+6)^3] halo tiles in the layout of
+              CCZ4_BUF_TILE (for instance that buffer after ccz4_fill_halos)
+     dev_H    device [n_points] or NULL; dev_M device [3][n_points] or NULL
+     dev_out  device [5]: L2 of H, L2 of |M|, max |H|, max |M|, count of
+              non-finite points (not copied to the host; no synchronisation)
+   n_points = n_patches * p^3 must not exceed 4,194,304: the per-block
+   partial sums of the reduction live in one fixed device array of
+   640 KiB that every GPU loading this library holds until the process
+   exits. The first call on a device looks up that array's address on
+   the current device; make that first call before any stream capture.
+   Every call shares the array and leaves its partial sums in it (each
+   call overwrites all the entries it reads), so calls that overlap on
+   the GPU race: serialise them, e.g. on one stream. Sizes beyond the
+   maximum return CCZ4_ERR_INVALID with a message. */
+ccz4_status ccz4_constraints_noalloc(const double *tiles, int p, int n_patches, double dx,
+                                     double *dev_H, double *dev_M, double *dev_out, void *stream);
+
 /* Arithmetic of one interior point-stage of the fused stage kernel for the
    given parameters and precision: the right-hand side, the dissipation, the
    RK4 update (the mean over the four stages) and a quarter of the

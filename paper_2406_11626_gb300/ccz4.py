@@ -264,3 +264,17 @@ class Grid:
             return out
         _check(code)
         return out
+
+
+def constraints_noalloc(tiles_ptr, p, n_patches, dx, H_ptr, M_ptr, out_ptr, stream=None):
+    """Constraint monitors from caller-held halo tiles, allocating nothing
+    (ccz4_constraints_noalloc in include/ccz4.h): for callers that cannot
+    allocate device memory. All pointers are device addresses; H_ptr and
+    M_ptr may be None; out_ptr receives the 5 reduced values on the device."""
+    f = lib().ccz4_constraints_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    _check(f(ctypes.c_void_p(tiles_ptr), int(p), int(n_patches), float(dx),
+             ctypes.c_void_p(H_ptr) if H_ptr else None, ctypes.c_void_p(M_ptr) if M_ptr else None,
+             ctypes.c_void_p(out_ptr), _stream(stream)))
