@@ -87,14 +87,19 @@ enum { CCZ4_PREC_FP64 = 0, CCZ4_PREC_MIXED = 1 };
 /* Device buffers of a grid. U: the state U_n. Y0, Y1: RK stage states.
    ACC: RK accumulator. RHS: output of ccz4_rhs. INI: Q_ini of the
    Sommerfeld condition (ghost part only is used). TILE: halo tiles. The
-   state-shaped buffers (U, Y0, Y1, ACC, RHS, INI) share one layout. */
+   state-shaped buffers (U, Y0, Y1, ACC, RHS, INI) share one layout.
+   MIX: [33][n_points] mixed second derivatives written by ccz4_fill_halos
+   with the tiles: for g~_xx..g~_zz (slots 0..17), alpha (18..20),
+   beta^x..beta^z (21..29) and phi (30..32), three slots each in the order
+   d_x d_y, d_x d_z, d_y d_z. */
 enum {
   CCZ4_BUF_U = 0, CCZ4_BUF_Y0 = 1, CCZ4_BUF_Y1 = 2, CCZ4_BUF_ACC = 3,
-  CCZ4_BUF_RHS = 4, CCZ4_BUF_INI = 5, CCZ4_BUF_TILE = 6
+  CCZ4_BUF_RHS = 4, CCZ4_BUF_INI = 5, CCZ4_BUF_TILE = 6, CCZ4_BUF_MIX = 7
 };
 
 typedef struct {
-  int p;              /* points per patch edge, >= 1 */
+  int p;              /* points per patch edge, 1..18 (the halo'd tile of one
+                         field, (p+6)^3 doubles, is staged in shared memory) */
   int np[3];          /* patch slots per axis; the domain has np[d]*p points along d */
   int n_patches;      /* must equal np[0]*np[1]*np[2]: the patches cover the domain */
   const int *ijk;     /* host [n_patches][3] integer patch coordinates, each slot once */
@@ -148,7 +153,10 @@ ccz4_status ccz4_download(ccz4_grid *g, int buf, double *U, double *G, void *str
    (p+2K)^3 tile). Writes CCZ4_BUF_TILE from the state-shaped buffer `buf`:
    interior points from their owning patch, points outside the domain by
    the boundary kind (periodic wrap, copy of the nearest interior point,
-   or the Sommerfeld ghost cell). Faces, edges and corners are all filled. */
+   or the Sommerfeld ghost cell). Faces, edges and corners are all filled.
+   While a field's tile is at hand it also writes the FD4 mixed second
+   derivatives of g~, alpha, beta and phi (the tensor product of two
+   first-derivative stencils) into CCZ4_BUF_MIX. */
 ccz4_status ccz4_fill_halos(ccz4_grid *g, int buf, void *stream);
 
 /* Right-hand side d_t Q of the second-order CCZ4 system (appendix
@@ -163,7 +171,8 @@ ccz4_status ccz4_rhs(ccz4_grid *g, const ccz4_params *P, int in_buf, int out_buf
 /* One stage s = 0..3 of classic RK4 (weights 1/6, 1/3, 1/3, 1/6; nodes
    0, 1/2, 1/2, 1), the paper's compute kernel applied to every patch. The
    halo fill is a separate step (the paper merges patch and halo before the
-   kernel runs): CCZ4_BUF_TILE must hold the halo'd stage input, i.e.
+   kernel runs): CCZ4_BUF_TILE and CCZ4_BUF_MIX must hold the halo'd stage
+   input and its mixed derivatives, i.e.
    ccz4_fill_halos must have been called on the buffer that
    ccz4_stage_buffers names as the input of stage s (U, Y0, Y1, Y0 for
    s = 0, 1, 2, 3). The kernel evaluates the right-hand side k_s and applies
@@ -184,6 +193,13 @@ ccz4_status ccz4_stage_buffers(int stage, int *in_buf, int *out_buf);
 /* n_steps full RK4 steps on U: for each stage, ccz4_fill_halos of the
    stage input followed by ccz4_rk_stage. */
 ccz4_status ccz4_step(ccz4_grid *g, const ccz4_params *P, double dt, int n_steps, void *stream);
+
+/* n_steps RK4 steps on U, like ccz4_step, replayed from a CUDA graph of one
+   step. The graph is captured on a private stream the first time, and again
+   whenever the parameters or dt differ from the captured ones; capturing
+   synchronises `stream` first. The graph then runs on `stream`. Results are
+   bit-identical to ccz4_step. */
+ccz4_status ccz4_step_graph(ccz4_grid *g, const ccz4_params *P, double dt, int n_steps, void *stream);
 
 /* End-to-end call from host memory: uploads U (and G) into CCZ4_BUF_U,
    runs n_steps RK4 steps, downloads the result into U_out (and G_out),

@@ -20,7 +20,10 @@ BC = {"periodic": 0, "copy": 1, "sommerfeld": 2}
 SLICING = {"harmonic": 0, "1+log": 1}
 SHIFT = {"zero": 0, "gamma-driver": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
-BUF = {"U": 0, "Y0": 1, "Y1": 2, "ACC": 3, "RHS": 4, "INI": 5, "TILE": 6}
+BUF = {"U": 0, "Y0": 1, "Y1": 2, "ACC": 3, "RHS": 4, "INI": 5, "TILE": 6, "MIX": 7}
+# mixed second derivatives d_x d_y, d_x d_z, d_y d_z of g~ (slots 0..17),
+# alpha (18..20), beta (21..29) and phi (30..32), written by the halo fill
+NMIX = 33
 
 _dbl_p = ctypes.POINTER(ctypes.c_double)
 
@@ -69,6 +72,7 @@ def lib():
         "ccz4_rk_stage": [vp, ctypes.POINTER(Params), ctypes.c_int, ctypes.c_double, vp],
         "ccz4_stage_buffers": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "ccz4_step": [vp, ctypes.POINTER(Params), ctypes.c_double, ctypes.c_int, vp],
+        "ccz4_step_graph": [vp, ctypes.POINTER(Params), ctypes.c_double, ctypes.c_int, vp],
         "ccz4_evolve_host": [vp, ctypes.POINTER(Params), ctypes.c_double, ctypes.c_int,
                              _dbl_p, _dbl_p, _dbl_p, _dbl_p, vp],
         "ccz4_enforce": [vp, ctypes.c_int, vp],
@@ -204,6 +208,10 @@ class Grid:
             out = np.empty((NV, self.n_patches, T, T, T))
             _check(lib().ccz4_download(self._h, BUF["TILE"], _d(out), None, _stream(stream)))
             return out
+        if _buf(buf) == BUF["MIX"]:
+            out = np.empty((NMIX, self.n_points))
+            _check(lib().ccz4_download(self._h, BUF["MIX"], _d(out), None, _stream(stream)))
+            return out
         U = np.empty((NV, self.n_patches, self.p, self.p, self.p))
         G = np.empty((NV, self.n_ghost))
         _check(lib().ccz4_download(self._h, _buf(buf), _d(U), _d(G) if self.n_ghost else None,
@@ -240,6 +248,9 @@ class Grid:
 
     def step(self, P, dt, n_steps=1, stream=None):
         _check(lib().ccz4_step(self._h, ctypes.byref(P), float(dt), int(n_steps), _stream(stream)))
+
+    def step_graph(self, P, dt, n_steps=1, stream=None):
+        _check(lib().ccz4_step_graph(self._h, ctypes.byref(P), float(dt), int(n_steps), _stream(stream)))
 
     def evolve_host(self, P, dt, n_steps, U, G=None, U_out=None, G_out=None, stream=None):
         U = np.ascontiguousarray(U, dtype=np.float64)

@@ -51,6 +51,50 @@ __host__ __device__ __forceinline__ double rcbrtT(double a) {
 #endif
 }
 
+// Precision conversions. GB300 executes the F2F double <-> float conversion
+// instructions on its narrow FP64 pipe, the bottleneck of this kernel, so on
+// the device they are done with integer operations on the bit patterns:
+// double -> float rounds to nearest (ties away from zero), flushes values
+// below the single-precision normal range to signed zero and maps values
+// beyond it to infinity (NaN if mantissa bits survive); float -> double is
+// exact for normal numbers and flushes subnormals to zero.
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sgn = hi & 0x80000000u, e = (hi >> 20) & 0x7FFu;
+  const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  unsigned f = (sgn | ((e - 896u) << 23) | m) + ((lo >> 28) & 1u);
+  f = e < 897u ? sgn : f;
+  f = e > 1150u ? (sgn | 0x7F800000u | (m ? 0x400000u : 0u)) : f;
+  return __uint_as_float(f);
+}
+__device__ __forceinline__ double f2d_bits(float v) {
+  const unsigned u = __float_as_uint(v), sgn = u & 0x80000000u, e = (u >> 23) & 0xFFu;
+  unsigned hi = sgn | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  unsigned lo = u << 29;
+  hi = e == 0u ? sgn : hi;
+  lo = e == 0u ? 0u : lo;
+  hi = e == 255u ? (sgn | 0x7FF00000u | ((u & 0x7FFFFFu) >> 3)) : hi;
+  return __hiloint2double((int)hi, (int)lo);
+}
+template <class To, class From>
+__host__ __device__ __forceinline__ To cvt(const From &x) { return To(x); }
+template <>
+__host__ __device__ __forceinline__ float cvt<float, double>(const double &x) {
+#ifdef __CUDA_ARCH__
+  return d2f_bits(x);
+#else
+  return (float)x;
+#endif
+}
+template <>
+__host__ __device__ __forceinline__ double cvt<double, float>(const float &x) {
+#ifdef __CUDA_ARCH__
+  return f2d_bits(x);
+#else
+  return (double)x;
+#endif
+}
+
 // index of the symmetric pair (i, j) among xx, xy, xz, yy, yz, zz
 __host__ __device__ constexpr int S6(int i, int j) {
   return i > j ? S6(j, i) : (i == 0 ? j : (i == 1 ? 2 + j : 5));
@@ -58,14 +102,23 @@ __host__ __device__ constexpr int S6(int i, int j) {
 
 // Read-only view of the halo'd neighbourhood of one point.
 struct Nbhd {
-  const double *__restrict__ c;  // field 0 at the centre point
-  long long fs;                  // distance between fields
-  int st[3];                     // distance between neighbours along x, y, z
+  const double *__restrict__ c;    // field 0 at the centre point
+  long long fs;                    // distance between fields
+  int st[3];                       // distance between neighbours along x, y, z
+  const double *__restrict__ mix;  // mixed second derivatives of this point, slot 0
+  long long ms;                    // distance between slots
   __host__ __device__ __forceinline__ double at(int v, int off) const {
 #ifdef __CUDA_ARCH__
     return __ldg(c + v * fs + off);
 #else
     return c[v * fs + off];
+#endif
+  }
+  __host__ __device__ __forceinline__ double mixed(int slot) const {
+#ifdef __CUDA_ARCH__
+    return __ldg(mix + slot * ms);
+#else
+    return mix[slot * ms];
 #endif
   }
 };
@@ -90,6 +143,15 @@ __host__ __device__ __forceinline__ D fd1(const Nbhd &N, int v, int s, const D &
   return fmaT(D(8.0), a, -b) * c1;
 }
 
+// First derivative whose neighbour differences are taken in D and whose
+// stencil weights are applied in O (O = D: identical to fd1).
+template <class D, class O>
+__host__ __device__ __forceinline__ O fd1o(const Nbhd &N, int v, int s, const O &c1) {
+  const D a = ld<D>(N, v, s) - ld<D>(N, v, -s);
+  const D b = ld<D>(N, v, 2 * s) - ld<D>(N, v, -2 * s);
+  return fmaT(O(8.0), cvt<O>(a), -cvt<O>(b)) * c1;
+}
+
 template <class D>
 __host__ __device__ __forceinline__ D fd2(const Nbhd &N, int v, int s, const D &c2) {
   const D s1 = ld<D>(N, v, s) + ld<D>(N, v, -s);
@@ -103,32 +165,80 @@ __host__ __device__ __forceinline__ D quad(const Nbhd &N, int v, int oa, int ob)
   return (ld<D>(N, v, oa + ob) - ld<D>(N, v, -oa + ob)) - (ld<D>(N, v, oa - ob) - ld<D>(N, v, -oa - ob));
 }
 
-template <class D>
-__host__ __device__ __forceinline__ D fd11(const Nbhd &N, int v, int sa, int sb, const D &c3) {
+template <class D, class O>
+__host__ __device__ __forceinline__ O fd11(const Nbhd &N, int v, int sa, int sb, const O &c3) {
   const D s11 = quad<D>(N, v, sa, sb);
   const D s12 = quad<D>(N, v, sa, 2 * sb);
   const D s21 = quad<D>(N, v, 2 * sa, sb);
   const D s22 = quad<D>(N, v, 2 * sa, 2 * sb);
-  return fmaT(D(64.0), s11, fmaT(D(-8.0), s12 + s21, s22)) * c3;
+  return fmaT(O(64.0), cvt<O>(s11), fmaT(O(-8.0), cvt<O>(s12) + cvt<O>(s21), cvt<O>(s22))) * c3;
 }
 
 // second derivative d_k d_l of field v (k, l known at compile time after unrolling)
 template <class D>
 __host__ __device__ __forceinline__ D fdkl(const Nbhd &N, int v, int k, int l, const StencilCoef<D> &C) {
-  return k == l ? fd2<D>(N, v, N.st[k], C.c2) : fd11<D>(N, v, N.st[k], N.st[l], C.c3);
+  return k == l ? fd2<D>(N, v, N.st[k], C.c2) : fd11<D, D>(N, v, N.st[k], N.st[l], C.c3);
 }
 
 template <class D>
 __host__ __device__ __forceinline__ D ko_sum(const Nbhd &N, int v, const D &cko) {
-  D p1 = D(0.0), p2 = D(0.0), p3 = D(0.0);
+  const int s0 = N.st[0], s1 = N.st[1], s2 = N.st[2];
+  const D p1 = (ld<D>(N, v, s0) + ld<D>(N, v, -s0)) + (ld<D>(N, v, s1) + ld<D>(N, v, -s1)) +
+               (ld<D>(N, v, s2) + ld<D>(N, v, -s2));
+  const D p2 = (ld<D>(N, v, 2 * s0) + ld<D>(N, v, -2 * s0)) + (ld<D>(N, v, 2 * s1) + ld<D>(N, v, -2 * s1)) +
+               (ld<D>(N, v, 2 * s2) + ld<D>(N, v, -2 * s2));
+  const D p3 = (ld<D>(N, v, 3 * s0) + ld<D>(N, v, -3 * s0)) + (ld<D>(N, v, 3 * s1) + ld<D>(N, v, -3 * s1)) +
+               (ld<D>(N, v, 3 * s2) + ld<D>(N, v, -3 * s2));
+  return fmaT(D(-60.0), ld<D>(N, v, 0), fmaT(D(15.0), p1, fmaT(D(-6.0), p2, p3))) * cko;
+}
+
+// Pure second derivatives d_x d_x, d_y d_y, d_z d_z of field v and its
+// Kreiss-Oliger sum, computed together: both use the same neighbour pair
+// sums Q+ + Q- and Q++ + Q--. The second derivatives come out in O: for
+// O != D the second differences Q+ + Q- - 2Q and Q++ + Q-- - 2Q are taken
+// in D and only their weighted combination is done in O.
+template <class D, class O>
+__host__ __device__ __forceinline__ void pure2_ko(const Nbhd &N, int v, const StencilCoef<D> &C, const O &c2o,
+                                                  O d2[3], D &ko) {
+  const D q0 = ld<D>(N, v, 0);
+  D s1[3], s2[3], s3[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const int s = N.st[k];
-    p1 += ld<D>(N, v, s) + ld<D>(N, v, -s);
-    p2 += ld<D>(N, v, 2 * s) + ld<D>(N, v, -2 * s);
-    p3 += ld<D>(N, v, 3 * s) + ld<D>(N, v, -3 * s);
+    s1[k] = ld<D>(N, v, s) + ld<D>(N, v, -s);
+    s2[k] = ld<D>(N, v, 2 * s) + ld<D>(N, v, -2 * s);
+    s3[k] = ld<D>(N, v, 3 * s) + ld<D>(N, v, -3 * s);
   }
-  return fmaT(D(-60.0), ld<D>(N, v, 0), fmaT(D(15.0), p1, fmaT(D(-6.0), p2, p3))) * cko;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if constexpr (std::is_same<D, O>::value) {
+      d2[k] = fmaT(D(-30.0), q0, fmaT(D(16.0), s1[k], -s2[k])) * C.c2;
+    } else {
+      const D t1 = fmaT(D(-2.0), q0, s1[k]), t2 = fmaT(D(-2.0), q0, s2[k]);
+      d2[k] = fmaT(O(16.0), cvt<O>(t1), -cvt<O>(t2)) * c2o;
+    }
+  }
+  const D p1 = s1[0] + s1[1] + s1[2], p2 = s2[0] + s2[1] + s2[2], p3 = s3[0] + s3[1] + s3[2];
+  ko = fmaT(D(-60.0), q0, fmaT(D(15.0), p1, fmaT(D(-6.0), p2, p3))) * C.cko;
+}
+
+// All six second derivatives of field v, in the order xx, xy, xz, yy, yz, zz,
+// in O, and its Kreiss-Oliger sum in D. The pure ones are taken here; the
+// mixed ones were formed by the halo fill while the tile was in shared
+// memory, sharing first derivatives between neighbouring points.
+template <class D, class O>
+__host__ __device__ __forceinline__ void second_ko(const Nbhd &N, int v, const StencilCoef<D> &C,
+                                                   const StencilCoef<O> &CO, O dd[6], D &ko) {
+  O d2[3];
+  pure2_ko<D, O>(N, v, C, CO.c2, d2, ko);
+  dd[0] = d2[0];
+  dd[3] = d2[1];
+  dd[5] = d2[2];
+  // the mixed derivatives come from the halo fill (CCZ4_BUF_MIX)
+  const int m = mix_slot(v);
+  dd[1] = cvt<O>(D(N.mixed(m)));
+  dd[2] = cvt<O>(D(N.mixed(m + 1)));
+  dd[4] = cvt<O>(D(N.mixed(m + 2)));
 }
 
 // Parameters of the equations, combined on the host and stored in the
@@ -137,10 +247,11 @@ template <class R>
 struct Phys {
   R itau;   // 1 / tau
   R c;      // c
+  R c2;     // 2 c
   R K0;     // K0
   R k1a;    // 3 kappa1 (1 + kappa2)
   R k1b;    // kappa1 (2 + kappa2)
-  R e2;     // e^2
+  R e2h;    // e^2 / 2
   R s3;     // s / 3
   R k3x2;   // 2 kappa3
   R kappa1, f, eta;
@@ -152,10 +263,11 @@ inline Phys<R> make_phys(const ccz4_params &P) {
   Phys<R> q;
   q.itau = R(1.0 / P.tau);
   q.c = R(P.c);
+  q.c2 = R(2.0 * P.c);
   q.K0 = R(P.K0);
   q.k1a = R(3.0 * P.kappa1 * (1.0 + P.kappa2));
   q.k1b = R(P.kappa1 * (2.0 + P.kappa2));
-  q.e2 = R(P.e * P.e);
+  q.e2h = R(0.5 * P.e * P.e);
   q.s3 = R(P.s / 3.0);
   q.k3x2 = R(2.0 * P.kappa3);
   q.kappa1 = R(P.kappa1);
@@ -182,86 +294,83 @@ __host__ __device__ __forceinline__ T sym_inverse(const T g[6], T ig[6]) {
   return det;
 }
 
-// Right-hand side (without the dissipation term) at one interior point.
-template <class D, class R>
-__host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const Nbhd &N,
-                                                        const StencilCoef<D> &C, D r[NV]) {
+// Right-hand side, Kreiss-Oliger dissipation included, at one interior point.
+// Each field's value d_t Q_v is handed to sink(v, value) as soon as it is
+// known, in the order g~, A~, alpha, phi, K, Theta, Gamma-hat, beta, b; the
+// work is ordered so that every derivative is taken right before its first
+// use, which keeps the number of live values (and so register spills) low.
+template <class D, class R, class Sink>
+__host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const Nbhd &N, const StencilCoef<D> &C,
+                                                        const StencilCoef<R> &CR, Sink &sink) {
   constexpr bool SAME = std::is_same<D, R>::value;
-  // ---- state and first derivatives, in D ------------------------------------
+  // ---- conformal metric, its inverse and its first derivatives ----------------
   D gD[6];
-  R g[6], A[6];
+  R g[6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
     gD[c] = ld<D>(N, GXX + c, 0);
-    g[c] = R(gD[c]);
-    A[c] = R(ld<D>(N, AXX + c, 0));
+    g[c] = cvt<R>(gD[c]);
   }
-  const D phD = ld<D>(N, PHI, 0);
-  const R al = R(ld<D>(N, ALPHA, 0)), ph = R(phD), Kt = R(ld<D>(N, KTR, 0)), Th = R(ld<D>(N, THETA, 0));
-  R be[3], Gh[3], bb[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    be[i] = R(ld<D>(N, BETAX + i, 0));
-    Gh[i] = R(ld<D>(N, GHX + i, 0));
-    bb[i] = R(ld<D>(N, BBX + i, 0));
-  }
-  D daD[3], dPD[3];
-  R dg[3][6], dA[3][6], da[3], dB[3][3], dP[3], dK[3], dT[3], dG[3][3], db[3][3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const int s = N.st[k];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      dg[k][c] = R(fd1<D>(N, GXX + c, s, C.c1));
-      dA[k][c] = R(fd1<D>(N, AXX + c, s, C.c1));
-    }
-    daD[k] = fd1<D>(N, ALPHA, s, C.c1);
-    dPD[k] = fd1<D>(N, PHI, s, C.c1);
-    da[k] = R(daD[k]);
-    dP[k] = R(dPD[k]);
-    dK[k] = R(fd1<D>(N, KTR, s, C.c1));
-    dT[k] = R(fd1<D>(N, THETA, s, C.c1));
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      dB[k][i] = R(fd1<D>(N, BETAX + i, s, C.c1));  // B_k^i = d_k beta^i
-      dG[k][i] = R(fd1<D>(N, GHX + i, s, C.c1));    // d_k Gamma-hat^i
-      db[k][i] = R(fd1<D>(N, BBX + i, s, C.c1));    // d_k b^i
-    }
-  }
-
-  CCZ4_MARK("first derivatives");
-  // ---- inverse conformal metric ---------------------------------------------
+  // igw: the inverse with the off-diagonal entries doubled, for contractions
+  // with a symmetric pair stored as six components
   R ig[6];
   const R det = sym_inverse<R>(g, ig);
-  D igD[6];
+  const R igw[6] = {ig[0], ig[1] + ig[1], ig[2] + ig[2], ig[3], ig[4] + ig[4], ig[5]};
+  D igD[6], igwD[6];
   if constexpr (SAME) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) igD[c] = ig[c];
+    for (int c = 0; c < 6; ++c) {
+      igD[c] = ig[c];
+      igwD[c] = igw[c];
+    }
   } else {
     sym_inverse<D>(gD, igD);
+    igwD[0] = igD[0];
+    igwD[1] = igD[1] + igD[1];
+    igwD[2] = igD[2] + igD[2];
+    igwD[3] = igD[3];
+    igwD[4] = igD[4] + igD[4];
+    igwD[5] = igD[5];
   }
-  const R w6[6] = {R(1.0), R(2.0), R(2.0), R(1.0), R(2.0), R(1.0)};
-  const D w6D[6] = {D(1.0), D(2.0), D(2.0), D(1.0), D(2.0), D(1.0)};
-
+  R be[3], Gh[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    be[i] = cvt<R>(ld<D>(N, BETAX + i, 0));
+    Gh[i] = cvt<R>(ld<D>(N, GHX + i, 0));
+  }
   CCZ4_MARK("inverse metric");
+
   // ---- Christoffel symbols of g~ --------------------------------------------
   // Gd[k][ij] = G~_kij = (d_i g~_jk + d_j g~_ik - d_k g~_ij) / 2 ; Gu[k][ij] = G~^k_ij
   R Gd[3][6], Gu[3][6], Gc[3];
+  R advg[6], Ghdg[6];  // beta^k d_k g~_ij and Gamma-hat^k d_k g~_ij
+  {
+    R dg[3][6];
 #pragma unroll
-  for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 3; ++k)
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+      for (int c = 0; c < 6; ++c) dg[k][c] = fd1o<D, R>(N, GXX + c, N.st[k], CR.c1);
 #pragma unroll
-      for (int j = i; j < 3; ++j)
-        Gd[k][S6(i, j)] = R(0.5) * (dg[i][S6(j, k)] + dg[j][S6(i, k)] - dg[k][S6(i, j)]);
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j)
+          Gd[k][S6(i, j)] = R(0.5) * (dg[i][S6(j, k)] + dg[j][S6(i, k)] - dg[k][S6(i, j)]);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      advg[c] = fmaT(be[0], dg[0][c], fmaT(be[1], dg[1][c], be[2] * dg[2][c]));
+      Ghdg[c] = fmaT(Gh[0], dg[0][c], fmaT(Gh[1], dg[1][c], Gh[2] * dg[2][c]));
+    }
+  }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
 #pragma unroll
     for (int c = 0; c < 6; ++c)
       Gu[k][c] = fmaT(ig[S6(k, 0)], Gd[0][c], fmaT(ig[S6(k, 1)], Gd[1][c], ig[S6(k, 2)] * Gd[2][c]));
-    R s = R(0.0);
+    R s = igw[0] * Gu[k][0];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) s = fmaT(w6[c] * ig[c], Gu[k][c], s);
+    for (int c = 1; c < 6; ++c) s = fmaT(igw[c], Gu[k][c], s);
     Gc[k] = s;  // G~^k = g~^ij G~^k_ij
   }
   // Gamma-hat - G~ and Z_i = g~_ij (Gamma-hat^j - G~^j) / 2
@@ -271,267 +380,306 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
 #pragma unroll
   for (int i = 0; i < 3; ++i)
     Zd[i] = R(0.5) * fmaT(g[S6(i, 0)], dGam[0], fmaT(g[S6(i, 1)], dGam[1], g[S6(i, 2)] * dGam[2]));
-
   CCZ4_MARK("christoffel");
-  // ---- conformal-factor terms, in D -----------------------------------------
+
+  // ---- quadratic Christoffel part of the Ricci tensor -------------------------
+  // Cm[k][i][m] = g~^lm G~^k_li. With it, g~^lm G~^k_li G~_jkm = sum_km Cm[k][i][m] G~_jkm
+  // and g~^lm G~^k_im G~_klj = sum_kl Cm[k][i][l] G~_klj; Q6_ij collects the three terms.
+  R Q6[6];
+  {
+    R Cm[3][3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+          Cm[k][i][m] = fmaT(ig[S6(0, m)], Gu[k][S6(0, i)],
+                             fmaT(ig[S6(1, m)], Gu[k][S6(1, i)], ig[S6(2, m)] * Gu[k][S6(2, i)]));
+    R X[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        R s = Cm[0][i][0] * Gd[j][S6(0, 0)];
+#pragma unroll
+        for (int q = 1; q < 9; ++q) s = fmaT(Cm[q / 3][i][q % 3], Gd[j][S6(q / 3, q % 3)], s);
+        X[i][j] = s;
+      }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        R q3 = Cm[0][i][0] * Gd[0][S6(0, j)];
+#pragma unroll
+        for (int q = 1; q < 9; ++q) q3 = fmaT(Cm[q / 3][i][q % 3], Gd[q / 3][S6(q % 3, j)], q3);
+        Q6[S6(i, j)] = X[i][j] + X[j][i] + q3;
+      }
+  }
+  CCZ4_MARK("ricci quadratic");
+
+  // ---- conformal-factor terms and nabla nabla alpha, in D ---------------------
   // the parts of R_ij + 2 nabla_(i Z_j) and of nabla_i nabla_j alpha with
   // inverse powers of phi:
   //   (1/phi)(nabla~_i nabla~_j phi + g~_ij g~^kl nabla~_k nabla~_l phi)
   //   - (2/phi^2) g~_ij g~^kl P_k P_l + (2/phi^3) Z^k (g~_ik P_j + g~_jk P_i - g~_ij P_k)
   //   and (1/phi)(P_i A_j + P_j A_i - g~_ij g~^kl P_k A_l)
+  const D phD = ld<D>(N, PHI, 0);
+  const R ph = cvt<R>(phD), al = cvt<R>(ld<D>(N, ALPHA, 0));
+  D daD[3], dPD[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    daD[k] = fd1<D>(N, ALPHA, N.st[k], C.c1);
+    dPD[k] = fd1<D>(N, PHI, N.st[k], C.c1);
+  }
   const D iph = D(1.0) / phD;
-  D PuD[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-    PuD[k] = fmaT(igD[S6(k, 0)], dPD[0], fmaT(igD[S6(k, 1)], dPD[1], igD[S6(k, 2)] * dPD[2]));
-  const D PP = fmaT(PuD[0], dPD[0], fmaT(PuD[1], dPD[1], PuD[2] * dPD[2]));
-  const D PA = fmaT(PuD[0], daD[0], fmaT(PuD[1], daD[1], PuD[2] * daD[2]));
-  D dGamD[3], ZdD[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    dGamD[i] = D(dGam[i]);
-    ZdD[i] = D(Zd[i]);
-  }
-  const D dGP = fmaT(dGamD[0], dPD[0], fmaT(dGamD[1], dPD[1], dGamD[2] * dPD[2]));
-  D cdph[6];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = i; j < 3; ++j) {
-      const int c = S6(i, j);
-      const D Gp = fmaT(D(Gu[0][c]), dPD[0], fmaT(D(Gu[1][c]), dPD[1], D(Gu[2][c]) * dPD[2]));
-      cdph[c] = fdkl<D>(N, PHI, i, j, C) - Gp;  // nabla~_i nabla~_j phi
-    }
-  D trcdph = D(0.0);
-#pragma unroll
-  for (int c = 0; c < 6; ++c) trcdph = fmaT(w6D[c] * igD[c], cdph[c], trcdph);
-  const D two_iph2PP = D(2.0) * iph * iph * PP;
-  R phiRZ[6], phiDDa[6];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = i; j < 3; ++j) {
-      const int c = S6(i, j);
-      const D zt = D(2.0) * (ZdD[i] * dPD[j] + ZdD[j] * dPD[i]) - gD[c] * dGP;
-      phiRZ[c] = R(iph * (cdph[c] + fmaT(gD[c], trcdph, zt)) - two_iph2PP * gD[c]);
-      phiDDa[c] = R(iph * (dPD[i] * daD[j] + dPD[j] * daD[i] - gD[c] * PA));
-    }
-
-  CCZ4_MARK("phi terms");
-  // ---- second derivatives of alpha, g~ and beta, contracted in D ----------------
-  R DDa[6];  // nabla_i nabla_j alpha (physical Christoffel symbols)
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = i; j < 3; ++j) {
-      const int c = S6(i, j);
-      const R Ga = fmaT(Gu[0][c], da[0], fmaT(Gu[1][c], da[1], Gu[2][c] * da[2]));
-      DDa[c] = R(fdkl<D>(N, ALPHA, i, j, C)) - Ga + phiDDa[c];
-    }
-  R lapg[6];  // g~^kl d_k d_l g~_ij
-#pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    D s = D(0.0);
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int l = k; l < 3; ++l) s = fmaT(w6D[S6(k, l)] * igD[S6(k, l)], fdkl<D>(N, GXX + c, k, l, C), s);
-    lapg[c] = R(s);
-  }
-  R lapB[3], gdivB[3];  // g~^kl d_k d_l beta^i and d_k (d_l beta^l)
+  const R da[3] = {cvt<R>(daD[0]), cvt<R>(daD[1]), cvt<R>(daD[2])};
+  R phiRZ[6], DDa[6];
+  D koP, koA;
   {
-    D lb[3] = {D(0.0), D(0.0), D(0.0)}, gd[3] = {D(0.0), D(0.0), D(0.0)};
+    D PuD[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int l = k; l < 3; ++l) {
-        const D w = w6D[S6(k, l)] * igD[S6(k, l)];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const D u = fdkl<D>(N, BETAX + i, k, l, C);
-          lb[i] = fmaT(w, u, lb[i]);
-          if (i == l) gd[k] += u;
-          if (i == k && k != l) gd[l] += u;
-        }
-      }
+      PuD[k] = fmaT(igD[S6(k, 0)], dPD[0], fmaT(igD[S6(k, 1)], dPD[1], igD[S6(k, 2)] * dPD[2]));
+    const D PP = fmaT(PuD[0], dPD[0], fmaT(PuD[1], dPD[1], PuD[2] * dPD[2]));
+    const D PA = fmaT(PuD[0], daD[0], fmaT(PuD[1], daD[1], PuD[2] * daD[2]));
+    D dGamD[3], Z2D[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      lapB[i] = R(lb[i]);
-      gdivB[i] = R(gd[i]);
+      dGamD[i] = cvt<D>(dGam[i]);
+      const D z = cvt<D>(Zd[i]);
+      Z2D[i] = z + z;  // 2 Z_i
     }
-  }
-  R trDDa = R(0.0);
+    const D dGP = fmaT(dGamD[0], dPD[0], fmaT(dGamD[1], dPD[1], dGamD[2] * dPD[2]));
+    D cdph[6];  // nabla~_i nabla~_j phi
+    {
+      D ddP[6];
+      second_ko<D, D>(N, PHI, C, C, ddP, koP);
 #pragma unroll
-  for (int c = 0; c < 6; ++c) trDDa = fmaT(w6[c] * ig[c], DDa[c], trDDa);
-
-  CCZ4_MARK("second derivatives");
-  // ---- quadratic Christoffel part of the Ricci tensor ---------------------------
-  // Cm[k][i][m] = g~^lm G~^k_li ; Em[k][j][m] = g~^lm G~_klj ; X_ij = g~^lm G~^k_li G~_jkm
-  R Cm[3][3][3], Em[3][3][3];
+      for (int c = 0; c < 6; ++c)
+        cdph[c] = ddP[c] - fmaT(cvt<D>(Gu[0][c]), dPD[0], fmaT(cvt<D>(Gu[1][c]), dPD[1], cvt<D>(Gu[2][c]) * dPD[2]));
+    }
+    D trcdph = igwD[0] * cdph[0];
 #pragma unroll
-  for (int k = 0; k < 3; ++k)
+    for (int c = 1; c < 6; ++c) trcdph = fmaT(igwD[c], cdph[c], trcdph);
+    const D two_iph2PP = D(2.0) * (iph * iph) * PP;
+    D ddA[6];
+    second_ko<D, D>(N, ALPHA, C, C, ddA, koA);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        Cm[k][i][m] = fmaT(ig[S6(0, m)], Gu[k][S6(0, i)],
-                           fmaT(ig[S6(1, m)], Gu[k][S6(1, i)], ig[S6(2, m)] * Gu[k][S6(2, i)]));
-        Em[k][i][m] = fmaT(ig[S6(0, m)], Gd[k][S6(0, i)],
-                           fmaT(ig[S6(1, m)], Gd[k][S6(1, i)], ig[S6(2, m)] * Gd[k][S6(2, i)]));
+      for (int j = i; j < 3; ++j) {
+        const int c = S6(i, j);
+        const D zt = fmaT(Z2D[i], dPD[j], fmaT(Z2D[j], dPD[i], -gD[c] * dGP));
+        phiRZ[c] = cvt<R>(fmaT(iph, cdph[c] + fmaT(gD[c], trcdph, zt), -two_iph2PP * gD[c]));
+        const D phiDDa = iph * fmaT(dPD[i], daD[j], fmaT(dPD[j], daD[i], -gD[c] * PA));
+        // nabla_i nabla_j alpha with the physical Christoffel symbols
+        DDa[c] = cvt<R>(ddA[c] + phiDDa) - fmaT(Gu[0][c], da[0], fmaT(Gu[1][c], da[1], Gu[2][c] * da[2]));
       }
-  R X[3][3];
+  }
+  R trDDa = igw[0] * DDa[0];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      R s = R(0.0);
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int m = 0; m < 3; ++m) s = fmaT(Cm[k][i][m], Gd[j][S6(k, m)], s);
-      X[i][j] = s;
-    }
+  for (int c = 1; c < 6; ++c) trDDa = fmaT(igw[c], DDa[c], trDDa);
+  CCZ4_MARK("phi terms");
 
-  CCZ4_MARK("ricci quadratic");
-  // ---- R_ij + 2 nabla_(i Z_j) -------------------------------------------------------
-  R RZ[6];
+  // ---- R_ij + 2 nabla_(i Z_j) -----------------------------------------------------
+  // -1/2 g~^kl d_k d_l g~_ij + g~_k(i d_j) Gamma-hat^k + 1/2 Gamma-hat^k d_k g~_ij + Q6_ij + phi terms
+  R RZ[6], advGh[3];
+  D kog[6];
+  {
+    R dG[3][3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k)
 #pragma unroll
-    for (int j = i; j < 3; ++j) {
-      const int c = S6(i, j);
-      R t = R(-0.5) * lapg[c];
-      // g~_k(i d_j) Gamma-hat^k + 1/2 Gamma-hat^k d_k g~_ij
-      R u = R(0.0);
+      for (int i = 0; i < 3; ++i) dG[k][i] = fd1o<D, R>(N, GHX + i, N.st[k], CR.c1);  // d_k Gamma-hat^i
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
-        u += fmaT(g[S6(k, i)], dG[j][k], fmaT(g[S6(k, j)], dG[i][k], Gh[k] * dg[k][c]));
-      t = fmaT(R(0.5), u, t);
-      // g~^lm (G~^k_li G~_jkm + G~^k_lj G~_ikm + G~^k_im G~_klj)
-      R q3 = R(0.0);
+    for (int i = 0; i < 3; ++i) advGh[i] = fmaT(be[0], dG[0][i], fmaT(be[1], dG[1][i], be[2] * dG[2][i]));
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int m = 0; m < 3; ++m) q3 = fmaT(Gu[k][S6(i, m)], Em[k][j][m], q3);
-      RZ[c] = t + X[i][j] + X[j][i] + q3 + phiRZ[c];
-    }
-  R trRZ = R(0.0);
+      for (int j = i; j < 3; ++j) {
+        const int c = S6(i, j);
+        R dd[6];
+        second_ko<D, R>(N, GXX + c, C, CR, dd, kog[c]);
+        R lap = igw[0] * dd[0];
 #pragma unroll
-  for (int c = 0; c < 6; ++c) trRZ = fmaT(w6[c] * ig[c], RZ[c], trRZ);
+        for (int q = 1; q < 6; ++q) lap = fmaT(igw[q], dd[q], lap);
+        R u = Ghdg[c];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) u = fmaT(g[S6(k, i)], dG[j][k], fmaT(g[S6(k, j)], dG[i][k], u));
+        RZ[c] = fmaT(R(-0.5), lap, fmaT(R(0.5), u, Q6[c] + phiRZ[c]));
+      }
+  }
+  R trRZ = igw[0] * RZ[0];
+#pragma unroll
+  for (int c = 1; c < 6; ++c) trRZ = fmaT(igw[c], RZ[c], trRZ);
   const R ph2 = ph * ph;
-  const R RpZ = ph2 * trRZ;    // R + 2 nabla_k Z^k
+  const R RpZ = ph2 * trRZ;     // R + 2 nabla_k Z^k
   const R lapal = ph2 * trDDa;  // nabla^i nabla_i alpha
-
   CCZ4_MARK("ricci assembly");
+
   // ---- A~ contractions ---------------------------------------------------------------
-  R Am[3][3];  // A~_i^m = A~_il g~^lm
+  R A[6];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int m = 0; m < 3; ++m)
-      Am[i][m] = fmaT(A[S6(i, 0)], ig[S6(0, m)], fmaT(A[S6(i, 1)], ig[S6(1, m)], A[S6(i, 2)] * ig[S6(2, m)]));
-  const R trA = Am[0][0] + Am[1][1] + Am[2][2];
+  for (int c = 0; c < 6; ++c) A[c] = cvt<R>(ld<D>(N, AXX + c, 0));
   R Au[6], AgA[6];
+  {
+    R Am[3][3];  // A~_i^m = A~_il g~^lm
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = i; j < 3; ++j) {
-      Au[S6(i, j)] = fmaT(ig[S6(i, 0)], Am[0][j], fmaT(ig[S6(i, 1)], Am[1][j], ig[S6(i, 2)] * Am[2][j]));
-      AgA[S6(i, j)] = fmaT(Am[i][0], A[S6(0, j)], fmaT(Am[i][1], A[S6(1, j)], Am[i][2] * A[S6(2, j)]));
-    }
-  R AA = R(0.0);
+      for (int m = 0; m < 3; ++m)
+        Am[i][m] = fmaT(A[S6(i, 0)], ig[S6(0, m)], fmaT(A[S6(i, 1)], ig[S6(1, m)], A[S6(i, 2)] * ig[S6(2, m)]));
 #pragma unroll
-  for (int c = 0; c < 6; ++c) AA = fmaT(w6[c] * A[c], Au[c], AA);
-
-  const R trB = dB[0][0] + dB[1][1] + dB[2][2];
-  const R Kc = Kt - R(2.0) * P.c * Th;  // K - 2 Theta c
-  const R third = R(1.0 / 3.0), twothird = R(2.0 / 3.0);
-
-  CCZ4_MARK("A contractions");
-  // ---- d_t g~_ij, d_t A~_ij ---------------------------------------------------------------
-  const R trMx = al * trRZ - trDDa;  // g~^ij (-nabla_i nabla_j alpha + alpha RZ_ij)
-  R rr[NV];
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = i; j < 3; ++j) {
-      const int c = S6(i, j);
-      R advg = R(0.0), lieg = R(0.0), advA = R(0.0), lieA = R(0.0);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        advg = fmaT(be[k], dg[k][c], advg);
-        lieg += fmaT(g[S6(k, i)], dB[j][k], g[S6(k, j)] * dB[i][k]);
-        advA = fmaT(be[k], dA[k][c], advA);
-        lieA += fmaT(A[S6(k, i)], dB[j][k], A[S6(k, j)] * dB[i][k]);
+      for (int j = i; j < 3; ++j) {
+        Au[S6(i, j)] = fmaT(ig[S6(i, 0)], Am[0][j], fmaT(ig[S6(i, 1)], Am[1][j], ig[S6(i, 2)] * Am[2][j]));
+        AgA[S6(i, j)] = fmaT(Am[i][0], A[S6(0, j)], fmaT(Am[i][1], A[S6(1, j)], Am[i][2] * A[S6(2, j)]));
       }
-      rr[GXX + c] = advg + lieg - twothird * g[c] * trB - R(2.0) * al * (A[c] - third * g[c] * trA) -
-                    P.itau * (det - R(1.0)) * g[c];
-      const R Mij = al * RZ[c] - DDa[c];
-      rr[AXX + c] = advA + ph2 * (Mij - third * g[c] * trMx) + lieA - twothird * A[c] * trB +
-                    al * A[c] * Kc - R(2.0) * al * AgA[c];
-    }
-
-  CCZ4_MARK("rhs g A");
-  // ---- scalars ---------------------------------------------------------------------------------
-  const R advK = fmaT(be[0], dK[0], fmaT(be[1], dK[1], be[2] * dK[2]));
-  const R advT = fmaT(be[0], dT[0], fmaT(be[1], dT[1], be[2] * dT[2]));
-  const R gK = (P.slicing == CCZ4_SLICING_ONE_PLUS_LOG) ? R(2.0) * al : al * al;  // alpha^2 g(alpha)
-  rr[ALPHA] = fmaT(be[0], da[0], fmaT(be[1], da[1], be[2] * da[2])) - gK * (Kt - P.K0 - R(2.0) * P.c * Th);
-  rr[PHI] = fmaT(be[0], dP[0], fmaT(be[1], dP[1], be[2] * dP[2])) + third * ph * (al * Kt - trB);
-  rr[KTR] = advK - lapal + al * RpZ + al * Kt * Kc - al * P.k1a * Th;
-  const R ZA = R(0.5) * ph2 * fmaT(dGam[0], da[0], fmaT(dGam[1], da[1], dGam[2] * da[2]));  // Z^i A_i
-  const R e2 = P.e2;
-  rr[THETA] = advT + R(0.5) * al * e2 * (RpZ + twothird * Kt * Kt - AA) - al * Th * Kt * P.c - ZA -
-              al * P.k1b * Th;
-
-  CCZ4_MARK("rhs scalars");
-  // ---- d_t Gamma-hat^i, gauge --------------------------------------------------------------------
-  // the 3 A~^ij P_j / phi term of the Gamma-hat equation, in D
-  R AuPphi[3];
+  }
+  const R trA = fmaT(igw[0], A[0], fmaT(igw[1], A[1], fmaT(igw[2], A[2], fmaT(igw[3], A[3],
+                fmaT(igw[4], A[4], igw[5] * A[5])))));
+  const R Auw[6] = {Au[0], Au[1] + Au[1], Au[2] + Au[2], Au[3], Au[4] + Au[4], Au[5]};
+  R AA = A[0] * Auw[0];
+#pragma unroll
+  for (int c = 1; c < 6; ++c) AA = fmaT(A[c], Auw[c], AA);
+  R GA[3];  // G~^i_jk A~^jk
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const D s = fmaT(D(Au[S6(i, 0)]), dPD[0], fmaT(D(Au[S6(i, 1)]), dPD[1], D(Au[S6(i, 2)]) * dPD[2]));
-    AuPphi[i] = R(s * iph);
+    R s = Gu[i][0] * Auw[0];
+#pragma unroll
+    for (int c = 1; c < 6; ++c) s = fmaT(Gu[i][c], Auw[c], s);
+    GA[i] = s;
   }
-  const R s3 = P.s3;
+  CCZ4_MARK("A contractions");
+
+  // ---- d_t g~_ij, d_t A~_ij ---------------------------------------------------------------
+  R dB[3][3];  // B_k^i = d_k beta^i
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dB[k][i] = fd1o<D, R>(N, BETAX + i, N.st[k], CR.c1);
+  const R third = R(1.0 / 3.0), twothird = R(2.0 / 3.0);
+  const R trB = dB[0][0] + dB[1][1] + dB[2][2];
+  const R trB23 = twothird * trB;
+  const R Th = cvt<R>(ld<D>(N, THETA, 0)), Kt = cvt<R>(ld<D>(N, KTR, 0));
+  const R Kc = fmaT(-P.c2, Th, Kt);  // K - 2 c Theta
+  const R al2 = al + al;
+  {
+    // Lie-derivative parts: Xg_ij = g~_ki B_j^k, XA_ij = A~_ki B_j^k, used as X_ij + X_ji
+    R Xg[3][3], XA[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Xg[i][j] = fmaT(g[S6(0, i)], dB[j][0], fmaT(g[S6(1, i)], dB[j][1], g[S6(2, i)] * dB[j][2]));
+        XA[i][j] = fmaT(A[S6(0, i)], dB[j][0], fmaT(A[S6(1, i)], dB[j][1], A[S6(2, i)] * dB[j][2]));
+      }
+    const R trMx = fmaT(al, trRZ, -trDDa);  // g~^ij (-nabla_i nabla_j alpha + alpha RZ_ij)
+    const R sg = fmaT(twothird * al, trA, -trB23) - P.itau * (det - R(1.0));
+    const R ph2al = ph2 * al;
+    const R sA1 = -third * ph2 * trMx;
+    const R sA2 = fmaT(al, Kc, -trB23);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        const int c = S6(i, j);
+        sink(GXX + c, cvt<D>((advg[c] + (Xg[i][j] + Xg[j][i])) + fmaT(g[c], sg, -al2 * A[c])) + kog[c]);
+        R advA = R(0.0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) advA = fmaT(be[k], fd1o<D, R>(N, AXX + c, N.st[k], CR.c1), advA);
+        const R rA = (advA + (XA[i][j] + XA[j][i])) +
+                     fmaT(ph2al, RZ[c], fmaT(-ph2, DDa[c], fmaT(g[c], sA1, fmaT(A[c], sA2, -al2 * AgA[c]))));
+        sink(AXX + c, cvt<D>(rA) + ko_sum<D>(N, AXX + c, C.cko));
+      }
+  }
+  CCZ4_MARK("rhs g A");
+
+  // ---- scalars ---------------------------------------------------------------------------------
+  const R gK = (P.slicing == CCZ4_SLICING_ONE_PLUS_LOG) ? al2 : al * al;  // alpha^2 g(alpha)
+  const R dP[3] = {cvt<R>(dPD[0]), cvt<R>(dPD[1]), cvt<R>(dPD[2])};
+  sink(ALPHA, cvt<D>(fmaT(be[0], da[0], fmaT(be[1], da[1], be[2] * da[2])) - gK * (Kc - P.K0)) + koA);
+  sink(PHI, cvt<D>(fmaT(be[0], dP[0], fmaT(be[1], dP[1], be[2] * dP[2])) + third * ph * fmaT(al, Kt, -trB)) + koP);
+  R dK[3], dT[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dK[k] = fd1o<D, R>(N, KTR, N.st[k], CR.c1);
+    dT[k] = fd1o<D, R>(N, THETA, N.st[k], CR.c1);
+  }
+  const R advK = fmaT(be[0], dK[0], fmaT(be[1], dK[1], be[2] * dK[2]));
+  const R advT = fmaT(be[0], dT[0], fmaT(be[1], dT[1], be[2] * dT[2]));
+  sink(KTR, cvt<D>(advK - lapal + al * (RpZ + fmaT(Kt, Kc, -P.k1a * Th))) + ko_sum<D>(N, KTR, C.cko));
+  const R ZA = R(0.5) * ph2 * fmaT(dGam[0], da[0], fmaT(dGam[1], da[1], dGam[2] * da[2]));  // Z^i A_i
+  sink(THETA, cvt<D>(advT + al * fmaT(P.e2h, RpZ + fmaT(twothird * Kt, Kt, -AA), -Th * fmaT(Kt, P.c, P.k1b)) - ZA) +
+                  ko_sum<D>(N, THETA, C.cko));
+  CCZ4_MARK("rhs scalars");
+
+  // ---- d_t Gamma-hat^i, gauge --------------------------------------------------------------------
+  R lapB[3], gdivB[3];  // g~^kl d_k d_l beta^i and d_k (d_l beta^l)
+  D koB[3];
+  {
+    R ddB[3][6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      second_ko<D, R>(N, BETAX + i, C, CR, ddB[i], koB[i]);
+      R s = igw[0] * ddB[i][0];
+#pragma unroll
+      for (int q = 1; q < 6; ++q) s = fmaT(igw[q], ddB[i][q], s);
+      lapB[i] = s;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gdivB[k] = ddB[0][S6(k, 0)] + ddB[1][S6(k, 1)] + ddB[2][S6(k, 2)];
+  }
+  const R al43 = R(4.0 / 3.0) * al;
+  const R al6 = R(6.0) * al;
+  const R Th2 = Th + Th;
+  // coefficient of Gamma-hat^i - G~^i: (1/2)(-(4/3) alpha K - 2 alpha kappa1 + 2 kappa3 (2/3) tr B)
+  const R zc = R(0.5) * fmaT(-al43, Kt, fmaT(-al2, P.kappa1, P.k3x2 * trB23));
+  const R k3h = R(-0.5) * P.k3x2;
   R dbK[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    R adv = R(0.0), gT = R(0.0), gKk = R(0.0), gdv = R(0.0), gA = R(0.0), GB = R(0.0), AuA = R(0.0), ZB = R(0.0);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      adv = fmaT(be[k], dG[k][i], adv);
-      gT = fmaT(ig[S6(i, k)], dT[k], gT);
-      gKk = fmaT(ig[S6(i, k)], dK[k], gKk);
-      gdv = fmaT(ig[S6(i, k)], gdivB[k], gdv);
-      gA = fmaT(ig[S6(i, k)], da[k], gA);
-      GB = fmaT(Gc[k], dB[k][i], GB);
-      AuA = fmaT(Au[S6(i, k)], da[k], AuA);
-      ZB = fmaT(dGam[k], dB[k][i], ZB);
-    }
-    R GA = R(0.0);  // G~^i_jk A~^jk
-#pragma unroll
-    for (int c = 0; c < 6; ++c) GA = fmaT(w6[c] * Gu[i][c], Au[c], GA);
-    const R Zc = R(0.5) * dGam[i];  // g~^ij Z_j
-    const R rG = adv + R(2.0) * al * gT + lapB[i] + s3 * gdv - R(4.0 / 3.0) * al * gKk +
-                 twothird * Gc[i] * trB - GB + R(2.0) * al * (GA - R(3.0) * AuPphi[i]) - R(2.0) * Th * gA -
-                 R(4.0 / 3.0) * al * Kt * Zc - R(2.0) * AuA - R(2.0) * al * P.kappa1 * Zc +
-                 P.k3x2 * (twothird * Zc * trB - R(0.5) * ZB);
-    rr[GHX + i] = rG;
-    dbK[i] = rG - adv;
+    const R gT = fmaT(ig[S6(i, 0)], dT[0], fmaT(ig[S6(i, 1)], dT[1], ig[S6(i, 2)] * dT[2]));
+    const R gKk = fmaT(ig[S6(i, 0)], dK[0], fmaT(ig[S6(i, 1)], dK[1], ig[S6(i, 2)] * dK[2]));
+    const R gdv = fmaT(ig[S6(i, 0)], gdivB[0], fmaT(ig[S6(i, 1)], gdivB[1], ig[S6(i, 2)] * gdivB[2]));
+    const R gA = fmaT(ig[S6(i, 0)], da[0], fmaT(ig[S6(i, 1)], da[1], ig[S6(i, 2)] * da[2]));
+    const R GB = fmaT(Gc[0], dB[0][i], fmaT(Gc[1], dB[1][i], Gc[2] * dB[2][i]));
+    const R AuA = fmaT(Au[S6(i, 0)], da[0], fmaT(Au[S6(i, 1)], da[1], Au[S6(i, 2)] * da[2]));
+    const R ZB = fmaT(dGam[0], dB[0][i], fmaT(dGam[1], dB[1][i], dGam[2] * dB[2][i]));
+    // the 3 A~^ij P_j / phi term, in D
+    const D AuP = fmaT(cvt<D>(Au[S6(i, 0)]), dPD[0], fmaT(cvt<D>(Au[S6(i, 1)]), dPD[1], cvt<D>(Au[S6(i, 2)]) * dPD[2]));
+    const R AuPphi = cvt<R>(AuP * iph);
+    R t = fmaT(P.s3, gdv, lapB[i]);
+    t = fmaT(al2, gT + GA[i], t);
+    t = fmaT(-al43, gKk, t);
+    t = fmaT(trB23, Gc[i], t);
+    t = fmaT(-al6, AuPphi, t);
+    t = fmaT(-Th2, gA, t);
+    t = fmaT(R(-2.0), AuA, t);
+    t = fmaT(zc, dGam[i], t);
+    t = fmaT(k3h, ZB, t);
+    dbK[i] = t - GB;  // d_t Gamma-hat^i - beta^k d_k Gamma-hat^i
+    sink(GHX + i, cvt<D>(advGh[i] + dbK[i]) + ko_sum<D>(N, GHX + i, C.cko));
   }
+  if (P.shift == CCZ4_SHIFT_GAMMA_DRIVER) {
+    const R bb[3] = {cvt<R>(ld<D>(N, BBX, 0)), cvt<R>(ld<D>(N, BBY, 0)), cvt<R>(ld<D>(N, BBZ, 0))};
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    if (P.shift == CCZ4_SHIFT_GAMMA_DRIVER) {
-      rr[BETAX + i] = fmaT(be[0], dB[0][i], fmaT(be[1], dB[1][i], be[2] * dB[2][i])) + P.f * bb[i];
-      rr[BBX + i] = fmaT(be[0], db[0][i], fmaT(be[1], db[1][i], be[2] * db[2][i])) + dbK[i] - P.eta * bb[i];
-    } else {
-      rr[BETAX + i] = R(0.0);
-      rr[BBX + i] = R(0.0);
+    for (int i = 0; i < 3; ++i) {
+      sink(BETAX + i, cvt<D>(fmaT(be[0], dB[0][i], fmaT(be[1], dB[1][i], fmaT(be[2], dB[2][i], P.f * bb[i])))) + koB[i]);
+      R advb = fmaT(-P.eta, bb[i], dbK[i]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) advb = fmaT(be[k], fd1o<D, R>(N, BBX + i, N.st[k], CR.c1), advb);
+      sink(BBX + i, cvt<D>(advb) + ko_sum<D>(N, BBX + i, C.cko));
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      sink(BETAX + i, D(0.0) + koB[i]);
+      sink(BBX + i, D(0.0) + ko_sum<D>(N, BBX + i, C.cko));
     }
   }
-#pragma unroll
-  for (int v = 0; v < NV; ++v) r[v] = D(rr[v]);
   CCZ4_MARK("rhs gamma-hat gauge");
 }
 

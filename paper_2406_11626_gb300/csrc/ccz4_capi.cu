@@ -72,7 +72,9 @@ static ccz4_status check_params(const ccz4_params *P) {
 }
 
 static void free_all(ccz4_grid *g) {
-  for (int b = 0; b < 7; ++b) cudaFree(g->buf[b]);
+  if (g->step_exec) cudaGraphExecDestroy(g->step_exec);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+  for (int b = 0; b < 8; ++b) cudaFree(g->buf[b]);
   cudaFree(g->d_ijk);
   cudaFree(g->d_owner);
   cudaFree(g->d_gcoord);
@@ -95,6 +97,10 @@ extern "C" ccz4_status ccz4_alloc_patches(const ccz4_grid_desc *d, ccz4_grid **o
   }
   if (d->p < 1 || d->np[0] < 1 || d->np[1] < 1 || d->np[2] < 1 || !(d->dx > 0.0)) {
     set_error("invalid sizes: p=%d np=(%d,%d,%d) dx=%g", d->p, d->np[0], d->np[1], d->np[2], d->dx);
+    return CCZ4_ERR_INVALID;
+  }
+  if (d->p > MAX_P) {
+    set_error("patch edge p=%d exceeds %d: the halo'd tile of one field must fit in shared memory", d->p, MAX_P);
     return CCZ4_ERR_INVALID;
   }
   if (d->bc != CCZ4_BC_PERIODIC && d->bc != CCZ4_BC_COPY && d->bc != CCZ4_BC_SOMMERFELD) {
@@ -166,12 +172,17 @@ extern "C" ccz4_status ccz4_alloc_patches(const ccz4_grid_desc *d, ccz4_grid **o
   }
   v.S = ((v.n_points + v.n_ghost + 31) / 32) * 32;
   if (v.S == 0) v.S = 32;
+  if (v.S > 0x7FFFFFFFLL) {
+    set_error("grid too large: %lld points per field exceed 32-bit indexing", v.S);
+    free(g);
+    return CCZ4_ERR_INVALID;
+  }
   cudaGetDevice(&g->device);
   const long long state_len = (long long)NV * v.S;
-  const long long lens[7] = {state_len, state_len, state_len, state_len, state_len,
+  const long long lens[8] = {state_len, state_len, state_len, state_len, state_len,
                              d->bc == CCZ4_BC_SOMMERFELD ? state_len : 0,
-                             (long long)NV * v.n_patches * v.T3};
-  for (int b = 0; b < 7; ++b) {
+                             (long long)NV * v.n_patches * v.T3, (long long)NMIX * v.n_points};
+  for (int b = 0; b < 8; ++b) {
     g->buf_len[b] = lens[b];
     if (lens[b] == 0) continue;
     cudaError_t e = cudaMalloc(&g->buf[b], sizeof(double) * (size_t)lens[b]);
@@ -202,6 +213,7 @@ extern "C" ccz4_status ccz4_alloc_patches(const ccz4_grid_desc *d, ccz4_grid **o
   if (!gcoord.empty())
     cudaMemcpy(g->d_gcoord, gcoord.data(), sizeof(int) * gcoord.size(), cudaMemcpyHostToDevice);
   cudaMemset(g->d_status, 0, sizeof(unsigned));
+  prepare_fill_halos(v.p);
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     set_error("grid set-up failed: %s", cudaGetErrorString(e));
@@ -234,7 +246,7 @@ extern "C" ccz4_status ccz4_grid_info(const ccz4_grid *g, long long *n_points, l
 
 extern "C" ccz4_status ccz4_field_ptr(ccz4_grid *g, int buf, double **dev, long long *n_doubles) {
   if (check_grid(g)) return CCZ4_ERR_INVALID;
-  if (buf < 0 || buf > CCZ4_BUF_TILE || !g->buf[buf]) {
+  if (buf < 0 || buf > CCZ4_BUF_MIX || !g->buf[buf]) {
     set_error("buffer %d does not exist on this grid", buf);
     return CCZ4_ERR_INVALID;
   }
@@ -282,7 +294,7 @@ extern "C" ccz4_status ccz4_upload(ccz4_grid *g, int buf, const double *U, const
 
 extern "C" ccz4_status ccz4_download(ccz4_grid *g, int buf, double *U, double *G, void *stream) {
   if (check_grid(g)) return CCZ4_ERR_INVALID;
-  if (buf == CCZ4_BUF_TILE) {
+  if (buf == CCZ4_BUF_TILE || buf == CCZ4_BUF_MIX) {
     if (!U) {
       set_error("download: NULL host array");
       return CCZ4_ERR_INVALID;
@@ -305,7 +317,7 @@ extern "C" ccz4_status ccz4_fill_halos(ccz4_grid *g, int buf, void *stream) {
     set_error("fill_halos: buffer %d is not a state buffer of this grid", buf);
     return CCZ4_ERR_INVALID;
   }
-  CUDA_TRY(launch_fill_halos(g->v, g->buf[buf], g->buf[CCZ4_BUF_TILE], (cudaStream_t)stream));
+  CUDA_TRY(launch_fill_halos(g->v, g->buf[buf], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], (cudaStream_t)stream));
   return CCZ4_OK;
 }
 
@@ -321,8 +333,8 @@ extern "C" ccz4_status ccz4_rhs(ccz4_grid *g, const ccz4_params *P, int in_buf, 
     return CCZ4_ERR_INVALID;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  CUDA_TRY(launch_fill_halos(g->v, g->buf[in_buf], g->buf[CCZ4_BUF_TILE], s));
-  CUDA_TRY(launch_rhs(g->v, *P, g->buf[CCZ4_BUF_TILE], g->buf[in_buf], ini_ptr(g), g->buf[out_buf], s));
+  CUDA_TRY(launch_fill_halos(g->v, g->buf[in_buf], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], s));
+  CUDA_TRY(launch_rhs(g->v, *P, g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], g->buf[in_buf], ini_ptr(g), g->buf[out_buf], s));
   return CCZ4_OK;
 }
 
@@ -331,7 +343,7 @@ static const int kStageOut[4] = {CCZ4_BUF_Y0, CCZ4_BUF_Y1, CCZ4_BUF_Y0, CCZ4_BUF
 
 static ccz4_status stage_kernel(ccz4_grid *g, const ccz4_params *P, int stage, double dt, cudaStream_t s) {
   double *in = g->buf[kStageIn[stage]];
-  CUDA_TRY(launch_rk_stage(g->v, *P, stage, dt, g->buf[CCZ4_BUF_TILE], in, ini_ptr(g), g->buf[CCZ4_BUF_U],
+  CUDA_TRY(launch_rk_stage(g->v, *P, stage, dt, g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], in, ini_ptr(g), g->buf[CCZ4_BUF_U],
                            g->buf[CCZ4_BUF_ACC], g->buf[kStageOut[stage]], s));
   return CCZ4_OK;
 }
@@ -364,10 +376,69 @@ extern "C" ccz4_status ccz4_step(ccz4_grid *g, const ccz4_params *P, double dt, 
   cudaStream_t s = (cudaStream_t)stream;
   for (int n = 0; n < n_steps; ++n)
     for (int st = 0; st < 4; ++st) {
-      CUDA_TRY(launch_fill_halos(g->v, g->buf[kStageIn[st]], g->buf[CCZ4_BUF_TILE], s));
+      CUDA_TRY(launch_fill_halos(g->v, g->buf[kStageIn[st]], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], s));
       ccz4_status r = stage_kernel(g, P, st, dt, s);
       if (r != CCZ4_OK) return r;
     }
+  return CCZ4_OK;
+}
+
+// Captures one RK4 step (four halo fills and four stage launches) into a
+// CUDA graph on a private stream; kernel arguments, parameters and dt are
+// baked into the graph.
+static ccz4_status capture_step(ccz4_grid *g, const ccz4_params *P, double dt) {
+  if (g->step_exec) {
+    cudaGraphExecDestroy(g->step_exec);
+    g->step_exec = nullptr;
+  }
+  if (!g->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+  ccz4_status st = CCZ4_OK;
+  for (int s = 0; s < 4 && st == CCZ4_OK; ++s) {
+    cudaError_t e = launch_fill_halos(g->v, g->buf[kStageIn[s]], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], g->cap_stream);
+    if (e != cudaSuccess) {
+      set_error("capture: halo fill launch failed: %s", cudaGetErrorString(e));
+      st = CCZ4_ERR_CUDA;
+      break;
+    }
+    st = stage_kernel(g, P, s, dt, g->cap_stream);
+  }
+  cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+  if (st != CCZ4_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) {
+    set_error("cudaStreamEndCapture failed: %s", cudaGetErrorString(e));
+    return CCZ4_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(&g->step_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    g->step_exec = nullptr;
+    set_error("cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+    return CCZ4_ERR_CUDA;
+  }
+  g->step_P = *P;
+  g->step_dt = dt;
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_step_graph(ccz4_grid *g, const ccz4_params *P, double dt, int n_steps, void *stream) {
+  if (check_grid(g) || check_params(P)) return CCZ4_ERR_INVALID;
+  if (n_steps < 0 || !(dt == dt)) {
+    set_error("step_graph: n_steps must be >= 0 and dt finite");
+    return CCZ4_ERR_INVALID;
+  }
+  if (n_steps == 0) return CCZ4_OK;
+  if (!g->step_exec || memcmp(&g->step_P, P, sizeof(ccz4_params)) != 0 || g->step_dt != dt) {
+    // the graph's first kernel must not start before earlier work on `stream`
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    ccz4_status st = capture_step(g, P, dt);
+    if (st != CCZ4_OK) return st;
+  }
+  for (int n = 0; n < n_steps; ++n) CUDA_TRY(cudaGraphLaunch(g->step_exec, (cudaStream_t)stream));
   return CCZ4_OK;
 }
 
@@ -399,7 +470,7 @@ extern "C" ccz4_status ccz4_constraints(ccz4_grid *g, int buf, double out[5], do
     return CCZ4_ERR_INVALID;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  CUDA_TRY(launch_fill_halos(g->v, g->buf[buf], g->buf[CCZ4_BUF_TILE], s));
+  CUDA_TRY(launch_fill_halos(g->v, g->buf[buf], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], s));
   CUDA_TRY(launch_constraints(g->v, g->buf[CCZ4_BUF_TILE], dev_H, dev_M, g->red_partial, g->red_blocks,
                               g->red_out, s));
   CUDA_TRY(cudaMemcpyAsync(g->host_out, g->red_out, sizeof(double) * 5, cudaMemcpyDeviceToHost, s));

@@ -22,6 +22,16 @@ enum : int {
   AXX, AXY, AXZ, AYY, AYZ, AZZ, KTR, THETA, GHX, GHY, GHZ, BBX, BBY, BBZ
 };
 
+// First slot in the mixed-derivative buffer of field v (three slots: d_x d_y,
+// d_x d_z, d_y d_z), or -1 for fields without second derivatives.
+__host__ __device__ __forceinline__ constexpr int mix_slot(int v) {
+  return (v >= GXX && v <= GZZ) ? 3 * (v - GXX)
+         : v == ALPHA          ? 18
+         : (v >= BETAX && v <= BETAZ) ? 21 + 3 * (v - BETAX)
+         : v == PHI            ? 30
+                               : -1;
+}
+
 // Plain-data view of a grid, passed by value to every kernel.
 struct GridView {
   int p, T;                    // points per patch edge; tile edge p + 2*HALO
@@ -102,24 +112,33 @@ void set_error(const char *fmt, ...);
 struct ccz4_grid {
   ccz4::GridView v;
   int device;
-  double *buf[7];            // U, Y0, Y1, ACC, RHS, INI, TILE
-  long long buf_len[7];      // doubles
+  double *buf[8];            // U, Y0, Y1, ACC, RHS, INI, TILE, MIX
+  long long buf_len[8];      // doubles
   int *d_ijk, *d_owner, *d_gcoord;
   unsigned *d_status;
   double *red_partial;       // per-block partial sums of the constraint reduction
   int red_blocks;
   double *red_out;           // device [5]
   double *host_out;          // pinned [5]
+  cudaStream_t cap_stream;   // private stream for graph capture (created on first use)
+  cudaGraphExec_t step_exec; // one captured RK4 step, or NULL
+  ccz4_params step_P;        // parameters and dt baked into step_exec
+  double step_dt;
 };
 
 // Kernel launchers (one translation unit each).
 namespace ccz4 {
-cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile, cudaStream_t s);
-cudaError_t launch_rhs(const GridView &g, const ccz4_params &P, const double *tile, const double *in,
-                       const double *ini, double *out, cudaStream_t s);
+cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile, double *mix, cudaStream_t s);
+cudaError_t prepare_fill_halos(int p);
+// number of mixed second derivatives kept per point (d_xy, d_xz, d_yz of g~, alpha, beta, phi)
+constexpr int NMIX = 33;
+// largest patch edge whose halo'd tile of one field fits in the fill kernel's shared memory
+constexpr int MAX_P = 18;
+cudaError_t launch_rhs(const GridView &g, const ccz4_params &P, const double *tile, const double *mix,
+                       const double *in, const double *ini, double *out, cudaStream_t s);
 cudaError_t launch_rk_stage(const GridView &g, const ccz4_params &P, int stage, double dt,
-                            const double *tile, const double *in, const double *ini, const double *U,
-                            double *acc, double *out, cudaStream_t s);
+                            const double *tile, const double *mix, const double *in, const double *ini,
+                            const double *U, double *acc, double *out, cudaStream_t s);
 cudaError_t launch_enforce(const GridView &g, double *U, cudaStream_t s);
 cudaError_t launch_constraints(const GridView &g, const double *tile, double *H, double *M,
                                double *partial, int blocks, double *out5, cudaStream_t s);

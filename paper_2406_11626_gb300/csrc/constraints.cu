@@ -217,6 +217,8 @@ __global__ void __launch_bounds__(RED_THREADS) constraints_kernel(GridView g, St
     N.st[0] = 1;
     N.st[1] = T;
     N.st[2] = T * T;
+    N.mix = nullptr;
+    N.ms = 0;
     double h, m[3];
     constraints_point(N, C, h, m);
     if (H) H[i] = h;

@@ -31,31 +31,33 @@ void count_mark(const char *section) {
 
 namespace {
 
+template <int MODE>
+struct CountSink {
+  Cnt<double> dt{0.01};
+  void operator()(int, const Cnt<double> &k) {
+    Cnt<double> u(1.0), acc(0.5);
+    rk_combine<MODE, Cnt<double>>(u, acc, k, dt);
+  }
+};
+
 template <class R>
 void count_point_stage(const ccz4_params &P, const Nbhd &N) {
   using D = Cnt<double>;
   StencilCoef<D> C{D(1.0), D(1.0), D(1.0), D(P.ko_eps)};
+  StencilCoef<R> CR{R(1.0), R(1.0), R(1.0), R(P.ko_eps)};
   const Phys<R> ph = make_phys<R>(P);
-  D dt(0.01);
   // four stages: right-hand side + dissipation + update each
-  for (int s = 0; s < 4; ++s) {
-    D k[NV];
-    g_sections_on = (s == 0);
-    ccz4_rhs_point<D, R>(ph, N, C, k);
-    for (int v = 0; v < NV; ++v) k[v] += ko_sum<D>(N, v, C.cko);
-    count_mark("dissipation");
-    for (int v = 0; v < NV; ++v) {
-      D u(1.0), acc(0.5);
-      switch (s) {
-        case 0: rk_combine<0, D>(u, acc, k[v], dt); break;
-        case 1: rk_combine<1, D>(u, acc, k[v], dt); break;
-        case 2: rk_combine<2, D>(u, acc, k[v], dt); break;
-        default: rk_combine<3, D>(u, acc, k[v], dt); break;
-      }
-    }
-    count_mark("rk update");
-    g_sections_on = false;
-  }
+  g_sections_on = true;
+  CountSink<0> s0;
+  ccz4_rhs_point<D, R>(ph, N, C, CR, s0);
+  count_mark("rk update");
+  g_sections_on = false;
+  CountSink<1> s1;
+  ccz4_rhs_point<D, R>(ph, N, C, CR, s1);
+  CountSink<2> s2;
+  ccz4_rhs_point<D, R>(ph, N, C, CR, s2);
+  CountSink<3> s3;
+  ccz4_rhs_point<D, R>(ph, N, C, CR, s3);
   // enforcement after the last stage
   D g[6] = {D(1.0), D(0.01), D(0.0), D(1.0), D(0.0), D(1.0)};
   D A[6] = {D(0.1), D(0.0), D(0.0), D(-0.05), D(0.0), D(-0.05)};
@@ -77,7 +79,10 @@ extern "C" ccz4_status ccz4_flops_per_point_stage(const ccz4_params *P, double o
   std::vector<double> buf((size_t)NV * W * W * W, 0.0);
   for (int v : {GXX, GYY, GZZ, ALPHA, PHI})
     for (int t = 0; t < W * W * W; ++t) buf[(size_t)v * W * W * W + t] = 1.0;
+  std::vector<double> mixbuf(NMIX, 0.0);
   Nbhd N;
+  N.mix = mixbuf.data();
+  N.ms = 1;
   N.c = buf.data() + (3 * W * W + 3 * W + 3);
   N.fs = W * W * W;
   N.st[0] = 1;

@@ -1,41 +1,104 @@
 // Halo fill: glue every patch and the data around it into a (p+6)^3 tile
-// (Sec. "Spatial Discretisation", Fig. patch-face-reconstruction). One
-// thread per tile point resolves the global point once (neighbour patch,
-// periodic wrap, clamped copy or Sommerfeld ghost cell) and moves the 25
-// field values; consecutive threads write consecutive tile addresses.
+// (Sec. "Spatial Discretisation", Fig. patch-face-reconstruction), and take
+// the mixed second derivatives of the fields that need them while the tile
+// sits in shared memory.
+//
+// One CTA per patch. It resolves the source of every tile point once
+// (neighbour patch, periodic wrap, clamped copy or Sommerfeld ghost cell)
+// into an index table, then for each of the 25 fields gathers the field's
+// tile into shared memory and writes it out with coalesced stores. For g~,
+// alpha, beta and phi it also forms the mixed derivatives d_x d_y, d_x d_z,
+// d_y d_z as the first-derivative stencil applied to first derivatives
+// shared through shared memory: d_y Q is taken once on the patch widened by
+// two points along x and reused by the five neighbours that need it, which
+// costs about half the FP64 operations of evaluating each point's 16-point
+// tensor-product stencil on its own. The result is the same FD4 mixed
+// derivative (the tensor product of two first-derivative stencils).
 #include "ccz4_internal.cuh"
 
 namespace ccz4 {
 namespace {
 
-__global__ void __launch_bounds__(256) fill_halos_kernel(GridView g, const double *__restrict__ src,
-                                                         double *__restrict__ tile) {
-  const long long total = (long long)g.n_patches * g.T3;
-  const long long fs = total;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int n = (int)(t / g.T3);
-    const int r = (int)(t - (long long)n * g.T3);
-    const int T = g.T;
-    const int lz = r / (T * T), ly = (r / T) % T, lx = r % T;
-    const int gx = __ldg(g.ijk + 3 * n) * g.p + lx - HALO;
-    const int gy = __ldg(g.ijk + 3 * n + 1) * g.p + ly - HALO;
-    const int gz = __ldg(g.ijk + 3 * n + 2) * g.p + lz - HALO;
-    const long long s = locate(g, gx, gy, gz);
-    if (s < 0) continue;
-#pragma unroll 5
-    for (int v = 0; v < NV; ++v) tile[v * fs + t] = __ldg(src + v * g.S + s);
+constexpr int FILL_THREADS = 256;
+
+__global__ void __launch_bounds__(FILL_THREADS) fill_halos_kernel(GridView g, const double *__restrict__ src,
+                                                                  double *__restrict__ tile,
+                                                                  double *__restrict__ mix, double cmix) {
+  extern __shared__ double smem[];
+  const int n = blockIdx.x;
+  const int p = g.p, T = g.T;
+  const int T3 = (int)g.T3;
+  const int pe = p + 4;             // patch edge widened by two points on each side
+  const int next = pe * p * p;      // widened region of one first-derivative pass
+  double *ts = smem;                // [T3] tile of the current field
+  double *ext = smem + T3;          // [next] first derivatives on the widened region
+  int *idx = (int *)(ext + next);   // [T3] source index of each tile point
+  const int bx = __ldg(g.ijk + 3 * n) * p - HALO;
+  const int by = __ldg(g.ijk + 3 * n + 1) * p - HALO;
+  const int bz = __ldg(g.ijk + 3 * n + 2) * p - HALO;
+  for (int t = threadIdx.x; t < T3; t += blockDim.x) {
+    const int lz = t / (T * T), ly = (t / T) % T, lx = t % T;
+    const long long s = locate(g, bx + lx, by + ly, bz + lz);
+    idx[t] = (int)s;
+  }
+  __syncthreads();
+  const long long p3 = (long long)p * p * p;
+  const long long pbase = (long long)n * p3;
+  for (int v = 0; v < NV; ++v) {
+    const double *sv = src + v * g.S;
+    double *tv = tile + ((long long)v * g.n_patches + n) * g.T3;
+    for (int t = threadIdx.x; t < T3; t += blockDim.x) {
+      const int s = idx[t];
+      const double val = s >= 0 ? __ldg(sv + s) : 0.0;
+      ts[t] = val;
+      tv[t] = val;
+    }
+    const int slot = mix_slot(v);
+    if (slot < 0) continue;  // uniform across the block
+    __syncthreads();
+    // pass 0: d_y on the region widened along x, then d_x of it -> d_x d_y
+    // pass 1: d_z widened along x -> d_x d_z ; pass 2: d_z widened along y -> d_y d_z
+#pragma unroll 1
+    for (int pass = 0; pass < 3; ++pass) {
+      const int si = pass == 0 ? T : T * T;  // stride of the inner derivative in the tile
+      for (int e = threadIdx.x; e < next; e += blockDim.x) {
+        const int a = e % pe - 2, b = (e / pe) % p, c = e / (pe * p);
+        // a runs along the widened axis (x for passes 0, 1; y for pass 2)
+        const int x = pass == 2 ? b : a, y = pass == 2 ? a : b, z = c;
+        const int c0 = ((z + HALO) * T + (y + HALO)) * T + (x + HALO);
+        ext[e] = fma(8.0, ts[c0 + si] - ts[c0 - si], -(ts[c0 + 2 * si] - ts[c0 - 2 * si]));
+      }
+      __syncthreads();
+      double *mv = mix + (long long)(slot + pass) * g.n_points + pbase;
+      for (int q = threadIdx.x; q < p3; q += blockDim.x) {
+        const int x = q % p, y = (q / p) % p, z = q / (p * p);
+        const int a = pass == 2 ? y : x, b = pass == 2 ? x : y;
+        const int e = (z * p + b) * pe + (a + 2);
+        mv[q] = fma(8.0, ext[e + 1] - ext[e - 1], -(ext[e + 2] - ext[e - 2])) * cmix;
+      }
+      __syncthreads();
+    }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile, cudaStream_t s) {
-  const long long total = (long long)g.n_patches * g.T3;
-  if (total == 0) return cudaSuccess;
-  long long blocks = (total + 255) / 256;
-  if (blocks > 152LL * 64) blocks = 152LL * 64;
-  fill_halos_kernel<<<(unsigned)blocks, 256, 0, s>>>(g, src, tile);
+size_t fill_smem_bytes(int p) {
+  const size_t T = (size_t)p + 2 * HALO;
+  return sizeof(double) * (T * T * T + (size_t)(p + 4) * p * p) + sizeof(int) * T * T * T;
+}
+
+// Raises the kernel's dynamic shared-memory limit for patch edge p (once per
+// grid, outside any stream capture).
+cudaError_t prepare_fill_halos(int p) {
+  return cudaFuncSetAttribute(fill_halos_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)fill_smem_bytes(MAX_P > p ? MAX_P : p));
+}
+
+cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile, double *mix, cudaStream_t s) {
+  if (g.n_patches == 0) return cudaSuccess;
+  const size_t bytes = fill_smem_bytes(g.p);
+  fill_halos_kernel<<<g.n_patches, FILL_THREADS, bytes, s>>>(g, src, tile, mix, 1.0 / (144.0 * g.dx * g.dx));
   return cudaGetLastError();
 }
 

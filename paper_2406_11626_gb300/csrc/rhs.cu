@@ -11,6 +11,16 @@
 // exa_sommerfeld_inter), same stage update, no enforcement, FP64.
 #include "ccz4_algebra.cuh"
 
+// Minimum resident blocks of 128 threads per SM requested for the stage
+// kernel. 4 caps ptxas at 128 registers per thread (16 warps per SM): the
+// kernel spills more than at 255 registers (8 warps per SM), but the extra
+// warps hide the latency of the narrow FP64 pipe and of instruction fetch
+// (measured on GB300: 51.2 -> 42.5 ms per RK4 step for the mixed path at
+// 144^3, 62.7 -> 62.2 ms for the FP64 path).
+#ifndef CCZ4_INTERIOR_MIN_BLOCKS
+#define CCZ4_INTERIOR_MIN_BLOCKS 4
+#endif
+
 namespace ccz4 {
 namespace {
 
@@ -43,9 +53,49 @@ __device__ __forceinline__ void finish_point(const GridView &g, long long i, dou
   for (int v = 0; v < NV; ++v) a.out[v * S + i] = un[v];
 }
 
+// Receives d_t Q_v of one interior point field by field and applies the
+// stage update at once, so finished values leave the registers early. The
+// last stage holds g~ and A~ back for the algebraic enforcement.
+template <int MODE>
+struct StageSink {
+  const GridView &g;
+  long long i;
+  const StageArgs &a;
+  double ug[6], uA[6];
+  __device__ __forceinline__ void operator()(int v, double k) {
+    const long long o = v * g.S + i;
+    if (MODE < 0) {
+      a.out[o] = k;
+      return;
+    }
+    double acc = MODE == 0 ? 0.0 : a.acc[o];
+    const double un = rk_combine<(MODE < 0 ? 0 : MODE), double>(a.U[o], acc, k, a.dt);
+    if (MODE < 3) a.acc[o] = acc;
+    if (MODE == 3 && v >= GXX && v <= GZZ) {
+      ug[v - GXX] = un;
+      return;
+    }
+    if (MODE == 3 && v >= AXX && v <= AZZ) {
+      uA[v - AXX] = un;
+      return;
+    }
+    a.out[o] = un;
+  }
+  __device__ __forceinline__ void finish() {
+    if (MODE != 3) return;
+    enforce_point<double>(ug, uA);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      a.out[(GXX + c) * g.S + i] = ug[c];
+      a.out[(AXX + c) * g.S + i] = uA[c];
+    }
+  }
+};
+
 template <int MODE, class R>
-__global__ void __launch_bounds__(128, 1) interior_kernel(GridView g, Phys<R> P, StencilCoef<double> C,
-                                                       const double *__restrict__ tile, StageArgs a) {
+__global__ void __launch_bounds__(128, CCZ4_INTERIOR_MIN_BLOCKS) interior_kernel(GridView g, Phys<R> P, StencilCoef<double> C,
+                                                          StencilCoef<R> CR, const double *__restrict__ tile,
+                                                          const double *__restrict__ mix, StageArgs a) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n_points) return;
   const int p = g.p, T = g.T;
@@ -59,11 +109,11 @@ __global__ void __launch_bounds__(128, 1) interior_kernel(GridView g, Phys<R> P,
   N.st[0] = 1;
   N.st[1] = T;
   N.st[2] = T * T;
-  double k[NV];
-  ccz4_rhs_point<double, R>(P, N, C, k);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) k[v] += ko_sum<double>(N, v, C.cko);
-  finish_point<MODE>(g, i, k, a, true);
+  N.mix = mix + i;
+  N.ms = g.n_points;
+  StageSink<MODE> sink{g, i, a};
+  ccz4_rhs_point<double, R>(P, N, C, CR, sink);
+  sink.finish();
 }
 
 template <int MODE>
@@ -111,11 +161,13 @@ StencilCoef<double> coefs(const GridView &g, const ccz4_params &P) {
 }
 
 template <int MODE, class R>
-cudaError_t launch_mode(const GridView &g, const ccz4_params &P, const double *tile, const double *in,
-                        const double *ini, const StageArgs &a, cudaStream_t s) {
+cudaError_t launch_mode(const GridView &g, const ccz4_params &P, const double *tile, const double *mix,
+                        const double *in, const double *ini, const StageArgs &a, cudaStream_t s) {
   if (g.n_points > 0) {
     const long long blocks = (g.n_points + 127) / 128;
-    interior_kernel<MODE, R><<<(unsigned)blocks, 128, 0, s>>>(g, make_phys<R>(P), coefs(g, P), tile, a);
+    const StencilCoef<double> C = coefs(g, P);
+    const StencilCoef<R> CR{R(C.c1), R(C.c2), R(C.c3), R(C.cko)};
+    interior_kernel<MODE, R><<<(unsigned)blocks, 128, 0, s>>>(g, make_phys<R>(P), C, CR, tile, mix, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -128,29 +180,29 @@ cudaError_t launch_mode(const GridView &g, const ccz4_params &P, const double *t
 }
 
 template <int MODE>
-cudaError_t launch_prec(const GridView &g, const ccz4_params &P, const double *tile, const double *in,
-                        const double *ini, const StageArgs &a, cudaStream_t s) {
-  if (P.precision == CCZ4_PREC_MIXED) return launch_mode<MODE, float>(g, P, tile, in, ini, a, s);
-  return launch_mode<MODE, double>(g, P, tile, in, ini, a, s);
+cudaError_t launch_prec(const GridView &g, const ccz4_params &P, const double *tile, const double *mix,
+                        const double *in, const double *ini, const StageArgs &a, cudaStream_t s) {
+  if (P.precision == CCZ4_PREC_MIXED) return launch_mode<MODE, float>(g, P, tile, mix, in, ini, a, s);
+  return launch_mode<MODE, double>(g, P, tile, mix, in, ini, a, s);
 }
 
 }  // namespace
 
-cudaError_t launch_rhs(const GridView &g, const ccz4_params &P, const double *tile, const double *in,
-                       const double *ini, double *out, cudaStream_t s) {
+cudaError_t launch_rhs(const GridView &g, const ccz4_params &P, const double *tile, const double *mix,
+                       const double *in, const double *ini, double *out, cudaStream_t s) {
   StageArgs a{nullptr, nullptr, out, 0.0};
-  return launch_prec<-1>(g, P, tile, in, ini, a, s);
+  return launch_prec<-1>(g, P, tile, mix, in, ini, a, s);
 }
 
 cudaError_t launch_rk_stage(const GridView &g, const ccz4_params &P, int stage, double dt,
-                            const double *tile, const double *in, const double *ini, const double *U,
-                            double *acc, double *out, cudaStream_t s) {
+                            const double *tile, const double *mix, const double *in, const double *ini,
+                            const double *U, double *acc, double *out, cudaStream_t s) {
   StageArgs a{U, acc, out, dt};
   switch (stage) {
-    case 0: return launch_prec<0>(g, P, tile, in, ini, a, s);
-    case 1: return launch_prec<1>(g, P, tile, in, ini, a, s);
-    case 2: return launch_prec<2>(g, P, tile, in, ini, a, s);
-    case 3: return launch_prec<3>(g, P, tile, in, ini, a, s);
+    case 0: return launch_prec<0>(g, P, tile, mix, in, ini, a, s);
+    case 1: return launch_prec<1>(g, P, tile, mix, in, ini, a, s);
+    case 2: return launch_prec<2>(g, P, tile, mix, in, ini, a, s);
+    case 3: return launch_prec<3>(g, P, tile, mix, in, ini, a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -227,3 +227,54 @@ def test_single_puncture_full_size_sampled_parity():
     # every ghost cell of the Sommerfeld shell
     oG = og.ghost_rhs(O.make_params(**cfg.params), U, G, G)
     assert rel_err(accG, oG).max() < TOL
+
+
+def test_graph_steps_are_bit_identical_to_plain_steps():
+    """A time step captured as a CUDA graph and replayed gives exactly the
+    state of the same steps launched one by one; changing dt re-captures."""
+    from paper_2406_11626_gb300 import ccz4 as C
+    cfg = I.single_puncture_config(p=6, n_side=3, half_width=2.0)
+    U0, G0 = I.initial_state(cfg)
+    out = []
+    for use_graph in (False, True):
+        g = C.Grid.from_config(cfg)
+        g.upload(U0, G0)
+        g.upload(U0, G0, buf="INI")
+        P = C.make_params(**cfg.params)
+        for dt in (cfg.dt, 0.5 * cfg.dt):
+            if use_graph:
+                g.step_graph(P, dt, 3)
+            else:
+                g.step(P, dt, 3)
+        out.append(g.download("U"))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("bc,p,npv", [("sommerfeld", 9, (2, 2, 2)), ("periodic", 6, (3, 2, 2)), ("copy", 17, (1, 2, 1)),
+                                      ("periodic", 2, (3, 3, 2))])
+def test_mixed_derivatives_from_the_halo_fill_match_oracle(bc, p, npv):
+    """The halo fill forms d_x d_y, d_x d_z, d_y d_z of g~, alpha, beta and phi
+    from first derivatives shared in shared memory; they equal the oracle's
+    tensor-product stencil at every point (buffer CCZ4_BUF_MIX)."""
+    dx = 0.3
+    origin = (-0.5 * npv[0] * p * dx, -0.5 * npv[1] * p * dx - 0.011, -0.5 * npv[2] * p * dx + 0.017)
+    gg, og, ijk = make_pair(p, npv, origin, dx, bc, permute_seed=6)
+    U, G = random_state(p, npv, origin, dx, ijk, seed=2, bc=bc, base="puncture" if bc == "sommerfeld" else "flat")
+    gg.upload(U, G)
+    gg.fill_halos("U")
+    n = gg.n_points
+    tiles = gg.download("TILE")
+    mix = gg.download("MIX")
+    assert mix.shape == (33, n)
+    slots = [(I.IDX[f], 3 * k) for k, f in enumerate(["gxx", "gxy", "gxz", "gyy", "gyz", "gzz"])]
+    slots += [(I.IDX["alpha"], 18), (I.IDX["betax"], 21), (I.IDX["betay"], 24), (I.IDX["betaz"], 27), (I.IDX["phi"], 30)]
+    rng = np.random.default_rng(0)
+    pts = rng.choice(n, min(n, 200), replace=False)
+    for pt in pts:
+        _, d2, _ = og.point_derivs(U, G, int(pt))
+        for v, s in slots:
+            ref = np.array([d2[v, 0, 1], d2[v, 0, 2], d2[v, 1, 2]])
+            got = mix[s:s + 3, pt]
+            assert np.abs(got - ref).max() <= 1e-11 * max(np.abs(ref).max(), 1.0), (pt, v)
+    np.testing.assert_array_equal(tiles, og.fill_tiles(U, G))
