@@ -53,8 +53,8 @@ def parse_args():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--workload", default="puncture144", choices=["puncture144", "small"],
-                    help="small: the same physics on 54^3 points (6^3 patches), for profiler captures")
+    ap.add_argument("--workload", default="puncture144", choices=["puncture144", "mid", "small"],
+                    help="the same physics on fewer points, for profiler captures: mid = 90^3 (10^3 patches), small = 54^3 (6^3 patches)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     return ap.parse_args()
 
@@ -207,6 +207,8 @@ def bench_config(args):
     from paper_2406_11626_gb300 import inputs as I
     if args.workload == "small":
         return I.single_puncture_config(n_side=6, half_width=3.0)
+    if args.workload == "mid":
+        return I.single_puncture_config(n_side=10, half_width=5.0)
     return I.single_puncture_config()
 
 

@@ -20,8 +20,9 @@ namespace ccz4 {
 namespace {
 
 constexpr int FILL_THREADS = 256;
+constexpr int GATHER_BATCH = 8;
 
-__global__ void __launch_bounds__(FILL_THREADS) fill_halos_kernel(GridView g, const double *__restrict__ src,
+__global__ void __launch_bounds__(FILL_THREADS, 4) fill_halos_kernel(GridView g, const double *__restrict__ src,
                                                                   double *__restrict__ tile,
                                                                   double *__restrict__ mix, double cmix) {
   extern __shared__ double smem[];
@@ -47,13 +48,26 @@ __global__ void __launch_bounds__(FILL_THREADS) fill_halos_kernel(GridView g, co
   for (int v = 0; v < NV; ++v) {
     const double *sv = src + v * g.S;
     double *tv = tile + ((long long)v * g.n_patches + n) * g.T3;
-    for (int t = threadIdx.x; t < T3; t += blockDim.x) {
-      const int s = idx[t];
-      const double val = s >= 0 ? __ldg(sv + s) : 0.0;
-      ts[t] = val;
-      tv[t] = val;
-    }
     const int slot = mix_slot(v);
+    // Gather in batches of GATHER_BATCH independent loads per thread, so a
+    // field costs a couple of memory latencies rather than one per point.
+    for (int t0 = threadIdx.x; t0 < T3; t0 += GATHER_BATCH * FILL_THREADS) {
+      double val[GATHER_BATCH];
+#pragma unroll
+      for (int u = 0; u < GATHER_BATCH; ++u) {
+        const int t = t0 + u * FILL_THREADS;
+        const int s = t < T3 ? idx[t] : -1;
+        val[u] = s >= 0 ? __ldg(sv + s) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < GATHER_BATCH; ++u) {
+        const int t = t0 + u * FILL_THREADS;
+        if (t < T3) {
+          if (slot >= 0) ts[t] = val[u];
+          __stcs(tv + t, val[u]);  // read once, by the stage kernel
+        }
+      }
+    }
     if (slot < 0) continue;  // uniform across the block
     __syncthreads();
     // pass 0: d_y on the region widened along x, then d_x of it -> d_x d_y
@@ -74,7 +88,7 @@ __global__ void __launch_bounds__(FILL_THREADS) fill_halos_kernel(GridView g, co
         const int x = q % p, y = (q / p) % p, z = q / (p * p);
         const int a = pass == 2 ? y : x, b = pass == 2 ? x : y;
         const int e = (z * p + b) * pe + (a + 2);
-        mv[q] = fma(8.0, ext[e + 1] - ext[e - 1], -(ext[e + 2] - ext[e - 2])) * cmix;
+        __stcs(mv + q, fma(8.0, ext[e + 1] - ext[e - 1], -(ext[e + 2] - ext[e - 2])) * cmix);
       }
       __syncthreads();
     }
