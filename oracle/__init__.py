@@ -59,6 +59,11 @@ def lib():
         L = ctypes.CDLL(path)
         L.og_grid_new.restype = ctypes.c_void_p
         L.og_grid_new.argtypes = [ctypes.c_int] * 5 + [_int_p] + [ctypes.c_double] * 4 + [ctypes.c_int]
+        L.og_mesh_new.restype = ctypes.c_void_p
+        L.og_mesh_new.argtypes = [ctypes.c_int] * 5 + [_int_p, _int_p] + [ctypes.c_double] * 4 + [ctypes.c_int]
+        L.og_n_levels.restype = ctypes.c_int
+        L.og_n_levels.argtypes = [ctypes.c_void_p]
+        L.og_restrict.argtypes = [ctypes.c_void_p, _dbl_p]
         L.og_grid_free.argtypes = [ctypes.c_void_p]
         L.og_n_ghost.restype = ctypes.c_long
         L.og_n_ghost.argtypes = [ctypes.c_void_p]
@@ -90,9 +95,13 @@ def _f64(a, shape):
 
 
 class Grid:
-    """One uniform level of p^3 patches covering np[0] x np[1] x np[2] patch slots."""
+    """p^3 patches: one uniform level covering np[0] x np[1] x np[2] patch
+    slots, or, with ``level``, a statically refined mesh whose level-0
+    patches cover those slots and whose level-l patches (spacing dx / 3^l,
+    slots in level-l units) are complete 3x3x3 child sets of level l-1
+    patches."""
 
-    def __init__(self, p, np_, ijk, origin, dx, bc="periodic"):
+    def __init__(self, p, np_, ijk, origin, dx, bc="periodic", level=None):
         self.p = int(p)
         self.np = tuple(int(v) for v in np_)
         self.ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
@@ -101,11 +110,20 @@ class Grid:
         self.dx = float(dx)
         self.bc = BC[bc] if isinstance(bc, str) else int(bc)
         L = lib()
-        self._h = L.og_grid_new(self.p, *self.np, self.n_patches, self.ijk.ctypes.data_as(_int_p),
-                                *self.origin, self.dx, self.bc)
+        if level is None:
+            self.level = np.zeros(self.n_patches, dtype=np.int32)
+            self._h = L.og_grid_new(self.p, *self.np, self.n_patches, self.ijk.ctypes.data_as(_int_p),
+                                    *self.origin, self.dx, self.bc)
+        else:
+            self.level = np.ascontiguousarray(level, dtype=np.int32).reshape(-1)
+            if self.level.shape[0] != self.n_patches:
+                raise ValueError("oracle: one level per patch")
+            self._h = L.og_mesh_new(self.p, *self.np, self.n_patches, self.level.ctypes.data_as(_int_p),
+                                    self.ijk.ctypes.data_as(_int_p), *self.origin, self.dx, self.bc)
         if not self._h:
             raise ValueError("oracle: invalid grid description")
         self.n_ghost = int(L.og_n_ghost(self._h))
+        self.n_levels = int(L.og_n_levels(self._h))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -164,6 +182,12 @@ class Grid:
         Gini = self._g(Gini)
         lib().og_rk4_step(self._h, ctypes.byref(P), float(dt), _d(U), _d(G), _d(Gini))
         return U, G[:, :self.n_ghost]
+
+    def restrict(self, U):
+        """Coarse points under refined patches <- mean of their 27 fine cells."""
+        U = _f64(U, self.ushape).copy()
+        lib().og_restrict(self._h, _d(U))
+        return U
 
     def enforce(self, U):
         U = _f64(U, self.ushape).copy()

@@ -60,17 +60,28 @@ struct og_grid {
   int *gcoord;        /* [n_ghost][3] global coordinates (x, y, z) */
   long *gid;          /* dense map over [-K, N+K)^3 -> ghost id, or -1 */
   int Mx[3];          /* N + 2K */
+  /* static mesh refinement (appendix "refinement transition"): level 0 is
+     the grid above; each level l >= 1 holds complete sets of 3x3x3 children
+     of level l-1 patches, with spacing dx / 3^l */
+  int n_levels;
+  int *lev;                      /* [n] level of each patch */
+  int *nchild;                   /* [n] children of each patch (0 or 27) */
+  double dxl[OG_MAX_LEVELS];     /* spacing of each level */
+  int llo[OG_MAX_LEVELS][3];     /* levels >= 1: bounding box of the patch slots */
+  int lext[OG_MAX_LEVELS][3];
+  int *lowner[OG_MAX_LEVELS];    /* levels >= 1: dense bounding box -> patch id, or -1 */
 };
 
 /* ------------------------------------------------------------------------ */
 /* grid                                                                     */
 /* ------------------------------------------------------------------------ */
 
-og_grid *og_grid_new(int p, int np0, int np1, int np2, int n_patches, const int *ijk,
-                     double ox, double oy, double oz, double dx, int bc) {
-  if (p < 1 || np0 < 1 || np1 < 1 || np2 < 1 || !(dx > 0.0)) return NULL;
+/* Builds the grid of level 0 (patches with level[n] == 0, or all of them
+   when level is NULL) and, for a refined mesh, the levels above it. */
+static og_grid *grid_build(int p, int np0, int np1, int np2, int n_patches, const int *level,
+                           const int *ijk, double ox, double oy, double oz, double dx, int bc) {
+  if (p < 1 || np0 < 1 || np1 < 1 || np2 < 1 || !(dx > 0.0) || n_patches < 1 || ijk == NULL) return NULL;
   if (bc != OG_BC_PERIODIC && bc != OG_BC_COPY && bc != OG_BC_SOMMERFELD) return NULL;
-  if ((long)n_patches != (long)np0 * np1 * np2 || ijk == NULL) return NULL;
   og_grid *g = (og_grid *)calloc(1, sizeof(og_grid));
   g->p = p;
   g->T = p + 2 * OG_HALO;
@@ -85,17 +96,76 @@ og_grid *og_grid_new(int p, int np0, int np1, int np2, int n_patches, const int 
   g->dx = dx;
   g->ijk = (int *)malloc(sizeof(int) * 3 * (size_t)n_patches);
   memcpy(g->ijk, ijk, sizeof(int) * 3 * (size_t)n_patches);
-  g->owner = (int *)malloc(sizeof(int) * (size_t)n_patches);
-  for (int i = 0; i < n_patches; ++i) g->owner[i] = -1;
+  g->lev = (int *)calloc((size_t)n_patches, sizeof(int));
+  g->nchild = (int *)calloc((size_t)n_patches, sizeof(int));
+  g->n_levels = 1;
+  if (level) {
+    for (int n = 0; n < n_patches; ++n) {
+      if (level[n] < 0 || level[n] >= OG_MAX_LEVELS) { og_grid_free(g); return NULL; }
+      g->lev[n] = level[n];
+      if (level[n] + 1 > g->n_levels) g->n_levels = level[n] + 1;
+    }
+  }
+  for (int l = 0; l < g->n_levels; ++l) g->dxl[l] = l == 0 ? dx : g->dxl[l - 1] / 3.0;
+  /* level 0 covers every slot exactly once */
+  long n0 = (long)np0 * np1 * np2, count0 = 0;
+  g->owner = (int *)malloc(sizeof(int) * (size_t)n0);
+  for (long i = 0; i < n0; ++i) g->owner[i] = -1;
   for (int n = 0; n < n_patches; ++n) {
+    if (g->lev[n] != 0) continue;
     int a = ijk[3 * n], b = ijk[3 * n + 1], c = ijk[3 * n + 2];
     if (a < 0 || a >= np0 || b < 0 || b >= np1 || c < 0 || c >= np2) { og_grid_free(g); return NULL; }
     long cell = ((long)c * np1 + b) * np0 + a;
     if (g->owner[cell] != -1) { og_grid_free(g); return NULL; }
     g->owner[cell] = n;
+    ++count0;
   }
-  /* ghost shell: every cell within K of the domain and outside it, enumerated
-     in lexicographic (z, y, x) order */
+  if (count0 != n0) { og_grid_free(g); return NULL; }
+  /* levels >= 1: slot maps over their bounding boxes */
+  for (int l = 1; l < g->n_levels; ++l) {
+    int lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1}, any = 0;
+    for (int n = 0; n < n_patches; ++n) {
+      if (g->lev[n] != l) continue;
+      for (int d = 0; d < 3; ++d) {
+        int v = ijk[3 * n + d];
+        if (!any || v < lo[d]) lo[d] = v;
+        if (!any || v > hi[d]) hi[d] = v;
+      }
+      any = 1;
+    }
+    if (!any) { og_grid_free(g); return NULL; }
+    long size = 1;
+    for (int d = 0; d < 3; ++d) {
+      g->llo[l][d] = lo[d];
+      g->lext[l][d] = hi[d] - lo[d] + 1;
+      size *= g->lext[l][d];
+    }
+    g->lowner[l] = (int *)malloc(sizeof(int) * (size_t)size);
+    for (long i = 0; i < size; ++i) g->lowner[l][i] = -1;
+    for (int n = 0; n < n_patches; ++n) {
+      if (g->lev[n] != l) continue;
+      long k = 0;
+      for (int d = 2; d >= 0; --d) k = k * g->lext[l][d] + (ijk[3 * n + d] - lo[d]);
+      if (g->lowner[l][k] != -1) { og_grid_free(g); return NULL; }
+      g->lowner[l][k] = n;
+    }
+  }
+  /* every refined patch is the child of a patch one level down, and a
+     parent has either no children or all 27 */
+  for (int n = 0; n < n_patches; ++n) {
+    int l = g->lev[n];
+    if (l == 0) continue;
+    int a = ijk[3 * n] / 3, b = ijk[3 * n + 1] / 3, c = ijk[3 * n + 2] / 3;
+    int par = -1;
+    for (int m = 0; m < n_patches; ++m)
+      if (g->lev[m] == l - 1 && ijk[3 * m] == a && ijk[3 * m + 1] == b && ijk[3 * m + 2] == c) par = m;
+    if (par < 0 || ijk[3 * n] < 0 || ijk[3 * n + 1] < 0 || ijk[3 * n + 2] < 0) { og_grid_free(g); return NULL; }
+    g->nchild[par] += 1;
+  }
+  for (int n = 0; n < n_patches; ++n)
+    if (g->nchild[n] != 0 && g->nchild[n] != 27) { og_grid_free(g); return NULL; }
+  /* ghost shell (level 0): every cell within K of the domain and outside
+     it, enumerated in lexicographic (z, y, x) order */
   long total = (long)g->Mx[0] * g->Mx[1] * g->Mx[2];
   g->gid = (long *)malloc(sizeof(long) * (size_t)total);
   long count = 0;
@@ -118,9 +188,30 @@ og_grid *og_grid_new(int p, int np0, int np1, int np2, int n_patches, const int 
   return g;
 }
 
+static int check_nesting(const og_grid *g);
+
+og_grid *og_grid_new(int p, int np0, int np1, int np2, int n_patches, const int *ijk,
+                     double ox, double oy, double oz, double dx, int bc) {
+  if ((long)n_patches != (long)np0 * np1 * np2) return NULL;
+  return grid_build(p, np0, np1, np2, n_patches, NULL, ijk, ox, oy, oz, dx, bc);
+}
+
+og_grid *og_mesh_new(int p, int np0, int np1, int np2, int n_patches, const int *level,
+                     const int *ijk, double ox, double oy, double oz, double dx, int bc) {
+  og_grid *g = grid_build(p, np0, np1, np2, n_patches, level, ijk, ox, oy, oz, dx, bc);
+  if (g && check_nesting(g)) {
+    og_grid_free(g);
+    return NULL;
+  }
+  return g;
+}
+
+int og_n_levels(const og_grid *g) { return g->n_levels; }
+
 void og_grid_free(og_grid *g) {
   if (!g) return;
-  free(g->ijk); free(g->owner); free(g->gid); free(g->gcoord); free(g);
+  for (int l = 0; l < OG_MAX_LEVELS; ++l) free(g->lowner[l]);
+  free(g->ijk); free(g->owner); free(g->gid); free(g->gcoord); free(g->lev); free(g->nchild); free(g);
 }
 
 long og_n_ghost(const og_grid *g) { return g->n_ghost; }
@@ -160,16 +251,128 @@ static int locate(const og_grid *g, int x, int y, int z, long *idx) {
   return 0;
 }
 
-static double value_at(const og_grid *g, const double *U, const double *G, int v, int x, int y, int z) {
+/* Patch of level l >= 1 holding global level-l point (x, y, z), or -1. */
+static int level_owner(const og_grid *g, int l, int x, int y, int z) {
+  int c[3] = {x, y, z};
+  long k = 0;
+  for (int d = 2; d >= 0; --d) {
+    if (c[d] < 0) return -1;
+    int s = c[d] / g->p - g->llo[l][d];
+    if (s < 0 || s >= g->lext[l][d]) return -1;
+    k = k * g->lext[l][d] + s;
+  }
+  return g->lowner[l][k];
+}
+
+/* locate() on level l: 0 interior point, 1 ghost-shell point (level 0), 2
+   not covered by level l (the value comes from level l-1). */
+static int locate_l(const og_grid *g, int l, int x, int y, int z, long *idx) {
+  if (l == 0) return locate(g, x, y, z, idx);
+  int n = level_owner(g, l, x, y, z);
+  if (n < 0) return 2;
+  int p = g->p;
+  int lx = x - g->ijk[3 * n] * p, ly = y - g->ijk[3 * n + 1] * p, lz = z - g->ijk[3 * n + 2] * p;
+  *idx = (long)n * p * p * p + ((long)lz * p + ly) * p + lx;
+  return 0;
+}
+
+/* Whether level l holds (x, y, z) as an interior point of one of its
+   patches (for level 0: inside the domain, no boundary rule applied). */
+static int level_has(const og_grid *g, int l, int x, int y, int z, long *idx) {
+  if (l == 0 && (x < 0 || x >= g->N[0] || y < 0 || y >= g->N[1] || z < 0 || z >= g->N[2])) return 0;
+  return locate_l(g, l, x, y, z, idx) == 0;
+}
+
+/* Interior value of level l at (x, y, z); NaN where level l has no patch. */
+static double level_value(const og_grid *g, const double *U, int v, int l, int x, int y, int z) {
   long idx;
-  if (locate(g, x, y, z, &idx)) return G[(long)v * g->n_ghost + idx];
+  if (!level_has(g, l, x, y, z, &idx)) return NAN;
   return U[(long)v * n_interior(g) + idx];
+}
+
+/* Coarse-to-fine interpolation (appendix "refinement transition"): the
+   tensor product of three one-dimensional linear maps between cell centres,
+   applied along x, then y, then z. Fine cell i of level l has its centre at
+   coarse coordinate (i - 1)/3 of level l-1 (coarse centres at the integers),
+   so it lies between coarse cells c = floor((i-1)/3) and c+1, at remainder
+   r = i - 1 - 3c, with weights PW[r]: the rows (1), (2/3, 1/3) and
+   (1/3, 2/3) of the printed matrices P^par and P^perp. A weight of one
+   takes the single coarse value. */
+static const double PW[3][2] = {{1.0, 0.0}, {2.0 / 3.0, 1.0 / 3.0}, {1.0 / 3.0, 2.0 / 3.0}};
+
+static void coarse_cell(int i, int *c, int *r) {
+  int q = i - 1;
+  int f = q >= 0 ? q / 3 : -((2 - q) / 3);
+  *c = f;
+  *r = q - 3 * f;
+}
+
+static double interpolate(const og_grid *g, const double *U, int v, int l, int x, int y, int z) {
+  int c0[3], r[3];
+  coarse_cell(x, &c0[0], &r[0]);
+  coarse_cell(y, &c0[1], &r[1]);
+  coarse_cell(z, &c0[2], &r[2]);
+  int nb = r[1] ? 2 : 1, nc = r[2] ? 2 : 1;
+  double t[2][2], s[2];
+  for (int c = 0; c < nc; ++c)
+    for (int b = 0; b < nb; ++b) {
+      double q0 = level_value(g, U, v, l - 1, c0[0], c0[1] + b, c0[2] + c);
+      if (r[0]) {
+        double q1 = level_value(g, U, v, l - 1, c0[0] + 1, c0[1] + b, c0[2] + c);
+        t[c][b] = PW[r[0]][0] * q0 + PW[r[0]][1] * q1;
+      } else {
+        t[c][b] = q0;
+      }
+    }
+  for (int c = 0; c < nc; ++c) s[c] = r[1] ? PW[r[1]][0] * t[c][0] + PW[r[1]][1] * t[c][1] : t[c][0];
+  return r[2] ? PW[r[2]][0] * s[0] + PW[r[2]][1] * s[1] : s[0];
+}
+
+static double value_at_l(const og_grid *g, const double *U, const double *G, int v, int l, int x, int y,
+                         int z) {
+  long idx;
+  int k = locate_l(g, l, x, y, z, &idx);
+  if (k == 0) return U[(long)v * n_interior(g) + idx];
+  if (k == 1) return G[(long)v * g->n_ghost + idx];
+  return interpolate(g, U, v, l, x, y, z);
+}
+
+static double value_at(const og_grid *g, const double *U, const double *G, int v, int x, int y, int z) {
+  return value_at_l(g, U, G, v, 0, x, y, z);
+}
+
+/* Every tile point that a refined level does not cover must interpolate
+   from interior points of the level below (proper nesting). Returns 1 if
+   some point cannot. */
+static int check_nesting(const og_grid *g) {
+  int T = g->T, p = g->p;
+  for (int n = 0; n < g->n_patches; ++n) {
+    int l = g->lev[n];
+    if (l == 0) continue;
+    int bx = g->ijk[3 * n] * p, by = g->ijk[3 * n + 1] * p, bz = g->ijk[3 * n + 2] * p;
+    for (int lz = 0; lz < T; ++lz)
+      for (int ly = 0; ly < T; ++ly)
+        for (int lx = 0; lx < T; ++lx) {
+          int x = bx + lx - OG_HALO, y = by + ly - OG_HALO, z = bz + lz - OG_HALO;
+          long idx;
+          if (locate_l(g, l, x, y, z, &idx) != 2) continue;
+          int c0[3], r[3];
+          coarse_cell(x, &c0[0], &r[0]);
+          coarse_cell(y, &c0[1], &r[1]);
+          coarse_cell(z, &c0[2], &r[2]);
+          for (int c = 0; c <= (r[2] ? 1 : 0); ++c)
+            for (int b = 0; b <= (r[1] ? 1 : 0); ++b)
+              for (int a = 0; a <= (r[0] ? 1 : 0); ++a)
+                if (!level_has(g, l - 1, c0[0] + a, c0[1] + b, c0[2] + c, &idx)) return 1;
+        }
+  }
+  return 0;
 }
 
 /* Halo'd tile of patch n in the oracle's working layout: point-major, the
    25 fields of a point contiguous. */
 static void build_tile(const og_grid *g, int n, const double *U, const double *G, double *tile) {
-  int T = g->T, p = g->p;
+  int T = g->T, p = g->p, l = g->lev[n];
   int bx = g->ijk[3 * n] * p, by = g->ijk[3 * n + 1] * p, bz = g->ijk[3 * n + 2] * p;
   for (int lz = 0; lz < T; ++lz)
     for (int ly = 0; ly < T; ++ly)
@@ -177,7 +380,7 @@ static void build_tile(const og_grid *g, int n, const double *U, const double *G
         long t = ((long)lz * T + ly) * T + lx;
         for (int v = 0; v < OG_NV; ++v)
           tile[t * OG_NV + v] =
-              value_at(g, U, G, v, bx + lx - OG_HALO, by + ly - OG_HALO, bz + lz - OG_HALO);
+              value_at_l(g, U, G, v, l, bx + lx - OG_HALO, by + ly - OG_HALO, bz + lz - OG_HALO);
       }
 }
 
@@ -621,6 +824,7 @@ static void ghost_rhs(const og_grid *g, const og_params *P, const double *U, con
 
 static void patch_rhs(const og_grid *g, const og_params *P, int n, const double *tile, double *rU) {
   int p = g->p, T = g->T;
+  double dx = g->dxl[g->lev[n]];
   long pts = n_interior(g);
   double d1[OG_NV][3], d2[OG_NV][3][3];
   for (int z = 0; z < p; ++z)
@@ -632,10 +836,10 @@ static void patch_rhs(const og_grid *g, const og_params *P, int n, const double 
         tv.st[0] = 1; tv.st[1] = T; tv.st[2] = (long)T * T;
         double q[OG_NV], r[OG_NV];
         for (int v = 0; v < OG_NV; ++v) q[v] = tq(&tv, 0, v);
-        point_derivs(&tv, g->dx, d1, d2);
+        point_derivs(&tv, dx, d1, d2);
         ccz4_point_rhs(P, q, d1, d2, r);
         long li = (long)n * p * p * p + ((long)z * p + y) * p + x;
-        for (int v = 0; v < OG_NV; ++v) rU[(long)v * pts + li] = r[v] + ko_sum(&tv, v, P->ko_eps, g->dx);
+        for (int v = 0; v < OG_NV; ++v) rU[(long)v * pts + li] = r[v] + ko_sum(&tv, v, P->ko_eps, dx);
       }
 }
 
@@ -696,9 +900,48 @@ int og_enforce(const og_grid *g, double *U) {
   return 0;
 }
 
+/* Restriction (appendix "refinement transition", R^par of the average
+   scheme along every axis): each coarse point under a refined patch takes
+   the mean of the 3x3x3 fine cells that tile it, as the tensor product of
+   three one-dimensional averages with weights 1/3 (x, then y, then z).
+   Levels are restricted from the finest down, so level 0 sees the finest
+   data. */
+int og_restrict(const og_grid *g, double *U) {
+  const long pts = n_interior(g);
+  const int p = g->p;
+  const double third = 1.0 / 3.0;
+  for (int l = g->n_levels - 1; l >= 1; --l)
+    for (int n = 0; n < g->n_patches; ++n) {
+      if (g->lev[n] != l - 1 || g->nchild[n] == 0) continue;
+      for (int k = 0; k < p; ++k)
+        for (int j = 0; j < p; ++j)
+          for (int i = 0; i < p; ++i) {
+            int X = 3 * (g->ijk[3 * n] * p + i), Y = 3 * (g->ijk[3 * n + 1] * p + j),
+                Z = 3 * (g->ijk[3 * n + 2] * p + k);
+            long ci = (long)n * p * p * p + ((long)k * p + j) * p + i;
+            for (int v = 0; v < OG_NV; ++v) {
+              double sy[3];
+              for (int c = 0; c < 3; ++c) {
+                double sx[3];
+                for (int b = 0; b < 3; ++b) {
+                  double f0 = level_value(g, U, v, l, X, Y + b, Z + c);
+                  double f1 = level_value(g, U, v, l, X + 1, Y + b, Z + c);
+                  double f2 = level_value(g, U, v, l, X + 2, Y + b, Z + c);
+                  sx[b] = third * f0 + third * f1 + third * f2;
+                }
+                sy[c] = third * sx[0] + third * sx[1] + third * sx[2];
+              }
+              U[(long)v * pts + ci] = third * sy[0] + third * sy[1] + third * sy[2];
+            }
+          }
+    }
+  return 0;
+}
+
 /* Classic RK4 (weights 1/6, 1/3, 1/3, 1/6; nodes 0, 1/2, 1/2, 1) over the
    interior points and the evolved Sommerfeld ghost cells, then the algebraic
-   enforcement on the interior points. */
+   enforcement on the interior points and, on a refined mesh, the
+   restriction. All levels take the same step dt. */
 int og_rk4_step(const og_grid *g, const og_params *P, double dt, double *U, double *G,
                 const double *Gini) {
   long nu = n_interior(g) * OG_NV, ng = g->n_ghost * OG_NV;
@@ -723,6 +966,7 @@ int og_rk4_step(const og_grid *g, const og_params *P, double dt, double *U, doub
   for (long i = 0; i < nu; ++i) U[i] = U[i] + dt / 6.0 * (k[0][i] + 2.0 * k[1][i] + 2.0 * k[2][i] + k[3][i]);
   for (long i = 0; i < ng; ++i) G[i] = G[i] + dt / 6.0 * (kg[0][i] + 2.0 * kg[1][i] + 2.0 * kg[2][i] + kg[3][i]);
   og_enforce(g, U);
+  if (g->n_levels > 1) og_restrict(g, U);
   for (int s = 0; s < 4; ++s) { free(k[s]); free(kg[s]); }
   free(Y); free(YG);
   return 0;
@@ -819,8 +1063,10 @@ static void point_constraints(const double q[OG_NV], const double d1[OG_NV][3],
   }
 }
 
-/* L2 norms over all interior points (Sec. "Gauge Wave":
-   L2 = sqrt(sum H^2 / n), n the number of grid points). out[0] = L2 of H,
+/* L2 norms over all interior points of the leaf patches (Sec. "Gauge Wave":
+   L2 = sqrt(sum H^2 / n), n the number of grid points; on a refined mesh
+   the points a finer level covers are not counted again). H and M are
+   written for every patch. out[0] = L2 of H,
    out[1] = L2 of |M| (|M|^2 = sum_i M_i^2), out[2] = max |H|,
    out[3] = max |M|, out[4] = number of non-finite H or M values. */
 int og_constraints(const og_grid *g, const double *U, const double *G, double *H, double *M,
@@ -830,7 +1076,11 @@ int og_constraints(const og_grid *g, const double *U, const double *G, double *H
   double *tile = (double *)malloc(sizeof(double) * (size_t)T3 * OG_NV);
   double d1[OG_NV][3], d2[OG_NV][3][3];
   double sH = 0.0, sM = 0.0, mH = 0.0, mM = 0.0, bad = 0.0;
+  long n_leaf_pts = 0;
   for (int n = 0; n < g->n_patches; ++n) {
+    const double dx = g->dxl[g->lev[n]];
+    const int leaf = g->nchild[n] == 0;
+    if (leaf) n_leaf_pts += (long)p * p * p;
     build_tile(g, n, U, G, tile);
     for (int z = 0; z < p; ++z)
       for (int y = 0; y < p; ++y)
@@ -841,12 +1091,13 @@ int og_constraints(const og_grid *g, const double *U, const double *G, double *H
           tv.st[0] = 1; tv.st[1] = T; tv.st[2] = (long)T * T;
           double q[OG_NV], c4[4];
           for (int v = 0; v < OG_NV; ++v) q[v] = tq(&tv, 0, v);
-          point_derivs(&tv, g->dx, d1, d2);
+          point_derivs(&tv, dx, d1, d2);
           point_constraints(q, d1, d2, c4);
           long li = (long)n * p * p * p + ((long)z * p + y) * p + x;
           if (H) H[li] = c4[0];
           if (M)
             for (int i = 0; i < 3; ++i) M[(long)i * pts + li] = c4[1 + i];
+          if (!leaf) continue;
           double m2 = c4[1] * c4[1] + c4[2] * c4[2] + c4[3] * c4[3];
           if (!isfinite(c4[0]) || !isfinite(m2)) { bad += 1.0; continue; }
           sH += c4[0] * c4[0];
@@ -856,8 +1107,8 @@ int og_constraints(const og_grid *g, const double *U, const double *G, double *H
         }
   }
   free(tile);
-  out[0] = sqrt(sH / (double)pts);
-  out[1] = sqrt(sM / (double)pts);
+  out[0] = sqrt(sH / (double)n_leaf_pts);
+  out[1] = sqrt(sM / (double)n_leaf_pts);
   out[2] = mH;
   out[3] = mM;
   out[4] = bad;
@@ -873,7 +1124,7 @@ int og_constraints(const og_grid *g, const double *U, const double *G, double *H
 static void build_neigh(const og_grid *g, const double *U, const double *G, long pt, double *nb) {
   int p = g->p;
   long p3 = (long)p * p * p;
-  int n = (int)(pt / p3);
+  int n = (int)(pt / p3), l = g->lev[n];
   long r = pt % p3;
   int lz = (int)(r / (p * p)), ly = (int)((r / p) % p), lx = (int)(r % p);
   int gx = g->ijk[3 * n] * p + lx, gy = g->ijk[3 * n + 1] * p + ly, gz = g->ijk[3 * n + 2] * p + lz;
@@ -883,7 +1134,12 @@ static void build_neigh(const og_grid *g, const double *U, const double *G, long
       for (int a = 0; a < W; ++a)
         for (int v = 0; v < OG_NV; ++v)
           nb[(((long)c * W + b) * W + a) * OG_NV + v] =
-              value_at(g, U, G, v, gx + a - OG_HALO, gy + b - OG_HALO, gz + c - OG_HALO);
+              value_at_l(g, U, G, v, l, gx + a - OG_HALO, gy + b - OG_HALO, gz + c - OG_HALO);
+}
+
+static double point_dx(const og_grid *g, long pt) {
+  long p3 = (long)g->p * g->p * g->p;
+  return g->dxl[g->lev[pt / p3]];
 }
 
 static int sample_view(const og_grid *g, const double *U, const double *G, long pt, double *nb, tview *tv) {
@@ -905,9 +1161,10 @@ int og_rhs_points(const og_grid *g, const og_params *P, const double *U, const d
     if (sample_view(g, U, G, pts[s], nb, &tv)) return 1;
     double q[OG_NV], r[OG_NV];
     for (int v = 0; v < OG_NV; ++v) q[v] = tq(&tv, 0, v);
-    point_derivs(&tv, g->dx, d1, d2);
+    const double dx = point_dx(g, pts[s]);
+    point_derivs(&tv, dx, d1, d2);
     ccz4_point_rhs(P, q, d1, d2, r);
-    for (int v = 0; v < OG_NV; ++v) out[s * OG_NV + v] = r[v] + ko_sum(&tv, v, P->ko_eps, g->dx);
+    for (int v = 0; v < OG_NV; ++v) out[s * OG_NV + v] = r[v] + ko_sum(&tv, v, P->ko_eps, dx);
   }
   return 0;
 }
@@ -921,7 +1178,7 @@ int og_constraints_points(const og_grid *g, const double *U, const double *G, lo
     if (sample_view(g, U, G, pts[s], nb, &tv)) return 1;
     double q[OG_NV];
     for (int v = 0; v < OG_NV; ++v) q[v] = tq(&tv, 0, v);
-    point_derivs(&tv, g->dx, d1, d2);
+    point_derivs(&tv, point_dx(g, pts[s]), d1, d2);
     point_constraints(q, d1, d2, out + 4 * s);
   }
   return 0;
@@ -933,13 +1190,14 @@ int og_point_derivs(const og_grid *g, const double *U, const double *G, long pt,
   double d1[OG_NV][3], d2[OG_NV][3][3];
   tview tv;
   if (sample_view(g, U, G, pt, nb, &tv)) return 1;
-  point_derivs(&tv, g->dx, d1, d2);
+  const double dx = point_dx(g, pt);
+  point_derivs(&tv, dx, d1, d2);
   for (int v = 0; v < OG_NV; ++v) {
     for (int k = 0; k < 3; ++k) {
       d1o[v * 3 + k] = d1[v][k];
       for (int l = 0; l < 3; ++l) d2o[(v * 3 + k) * 3 + l] = d2[v][k][l];
     }
-    koo[v] = ko_sum(&tv, v, ko_eps, g->dx);
+    koo[v] = ko_sum(&tv, v, ko_eps, dx);
   }
   return 0;
 }

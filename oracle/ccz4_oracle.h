@@ -32,6 +32,7 @@ extern "C" {
 
 #define OG_NV 25
 #define OG_HALO 3
+#define OG_MAX_LEVELS 8
 
 enum { OG_BC_PERIODIC = 0, OG_BC_COPY = 1, OG_BC_SOMMERFELD = 2 };
 enum { OG_SLICING_HARMONIC = 0, OG_SLICING_ONE_PLUS_LOG = 1 };
@@ -48,6 +49,19 @@ typedef struct og_grid og_grid;
 
 og_grid *og_grid_new(int p, int np0, int np1, int np2, int n_patches, const int *ijk,
                      double ox, double oy, double oz, double dx, int bc);
+/* Statically refined mesh (appendix "refinement transition"): patches with
+   level[n] == 0 cover the np0 x np1 x np2 slots of the base grid (spacing
+   dx); a patch of level l >= 1 has spacing dx / 3^l (divided by 3.0 once
+   per level) and slot coordinates ijk in units of its own level, and is one
+   of the 27 children (slot / 3) of a level l-1 patch that has all 27. Halo
+   points a refined level does not cover are interpolated from the level
+   below, which must hold them as interior points. NULL if the description
+   breaks any of these rules. */
+og_grid *og_mesh_new(int p, int np0, int np1, int np2, int n_patches, const int *level,
+                     const int *ijk, double ox, double oy, double oz, double dx, int bc);
+int og_n_levels(const og_grid *g);
+/* In place: coarse points under refined patches <- mean of their 27 fine cells. */
+int og_restrict(const og_grid *g, double *U);
 void og_grid_free(og_grid *g);
 long og_n_ghost(const og_grid *g);
 void og_ghost_coords(const og_grid *g, int *out /* [n_ghost][3] (x,y,z) */);

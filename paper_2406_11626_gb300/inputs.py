@@ -54,6 +54,57 @@ def point_coords(p, ijk, origin, dx):
     return tuple(np.broadcast_to(o, (len(ijk), p, p, p)).copy() for o in out)
 
 
+def level_spacing(dx, n_levels):
+    """Grid spacing of each level of a ratio-3 mesh: divided by 3.0 once per level."""
+    out = [float(dx)]
+    for _ in range(1, n_levels):
+        out.append(out[-1] / 3.0)
+    return out
+
+
+def refined_mesh(np_, boxes, permute_seed=None):
+    """A statically refined mesh: level 0 covers the np_ slots; boxes[l-1] =
+    ((lo_x, lo_y, lo_z), (hi_x, hi_y, hi_z)) lists, in slot units of level
+    l-1 with hi exclusive, the level l-1 patches that get their 27 children
+    on level l. Returns (level, ijk) with the levels in order."""
+    level = []
+    ijk = []
+    base = patch_ijk(np_, permute_seed)
+    level += [0] * len(base)
+    ijk += [tuple(r) for r in base]
+    parents = set(map(tuple, base))
+    for l, (lo, hi) in enumerate(boxes, start=1):
+        kids = []
+        for (a, b, c) in sorted(parents, key=lambda t: (t[2], t[1], t[0])):
+            if all(lo[d] <= (a, b, c)[d] < hi[d] for d in range(3)):
+                for k in range(3):
+                    for j in range(3):
+                        for i in range(3):
+                            kids.append((3 * a + i, 3 * b + j, 3 * c + k))
+        kids.sort(key=lambda t: (t[2], t[1], t[0]))
+        level += [l] * len(kids)
+        ijk += kids
+        parents = set(kids)
+    return np.asarray(level, dtype=np.int32), np.asarray(ijk, dtype=np.int32).reshape(-1, 3)
+
+
+def mesh_point_coords(p, level, ijk, origin, dx):
+    """Coordinates of all interior points of a refined mesh, each
+    (n_patches, p, p, p); patch n uses the spacing of its level."""
+    level = np.asarray(level)
+    ijk = np.asarray(ijk).reshape(-1, 3)
+    hs = level_spacing(dx, int(level.max()) + 1)
+    out = [np.empty((len(ijk), p, p, p)) for _ in range(3)]
+    for l, h in enumerate(hs):
+        sel = np.nonzero(level == l)[0]
+        if len(sel) == 0:
+            continue
+        xyz = point_coords(p, ijk[sel], origin, h)
+        for d in range(3):
+            out[d][sel] = xyz[d]
+    return tuple(out)
+
+
 def ghost_cells(N):
     """Global integer coordinates (n_ghost, 3) of the ghost shell of an
     N[0] x N[1] x N[2] point domain, in lexicographic (z, y, x) order."""
