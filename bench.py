@@ -32,7 +32,7 @@ UNIT = "point-stages/s"
 # maximum SM clock (the nominal 1.25 TFLOP/s FP64 rate).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-KERNEL_SOURCES = ("paper_2406_11626_gb300/csrc/rhs.cu", "paper_2406_11626_gb300/csrc/ccz4_algebra.cuh",
+KERNEL_SOURCES = ("paper_2406_11626_gb300/csrc/stage_kernels.cuh", "paper_2406_11626_gb300/csrc/ccz4_algebra.cuh",
                   "paper_2406_11626_gb300/csrc/ccz4_internal.cuh")
 
 
@@ -53,7 +53,7 @@ def parse_args():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--workload", default="puncture144", choices=["puncture144", "mid", "small"],
+    ap.add_argument("--workload", default="puncture144", choices=["puncture144", "puncture3level", "mid", "small"],
                     help="the same physics on fewer points, for profiler captures: mid = 90^3 (10^3 patches), small = 54^3 (6^3 patches)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     return ap.parse_args()
@@ -114,18 +114,29 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ----------------------------------------------------------------------------
-def oracle_sample_config():
-    """Same physics and grid spacing as the 144^3 workload on a 36^3-point
-    sub-box (4^3 patches of 9^3 around the puncture, [-2, 2]^3)."""
+def oracle_sample_config(workload="puncture144"):
+    """Same physics and grid spacing as the workload on a sub-box around the
+    puncture: 36^3 points (4^3 patches of 9^3, [-2, 2]^3); for the
+    three-level workload, those 4^3 level-0 patches with the central 2^3
+    refined once and one level-1 patch refined again (307 patches)."""
     from paper_2406_11626_gb300 import inputs as I
+    if workload == "puncture3level":
+        return I.multilevel_puncture_config(n_side=4, half_width=2.0,
+                                            boxes=[((1, 1, 1), (3, 3, 3)), ((4, 4, 4), (5, 5, 5))])
     return I.single_puncture_config(n_side=4, half_width=2.0)
 
 
-def time_oracle(n_steps, n_warm=0):
+def sample_text(cfg):
+    if getattr(cfg, "level", None) is not None:
+        return "%d patches of 9^3 on 3 levels around the puncture ([-2,2]^3, dx = 1/9, 1/27, 1/81)" % cfg.n_patches
+    return "%d^3 points (4^3 patches of 9^3, [-2,2]^3)" % cfg.N[0]
+
+
+def time_oracle(n_steps, n_warm=0, workload="puncture144"):
     import oracle as O
     from paper_2406_11626_gb300 import inputs as I
-    cfg = oracle_sample_config()
-    og = O.Grid(cfg.p, cfg.np, cfg.ijk(), cfg.origin, cfg.dx, cfg.bc)
+    cfg = oracle_sample_config(workload)
+    og = O.Grid(cfg.p, cfg.np, cfg.ijk(), cfg.origin, cfg.dx, cfg.bc, level=getattr(cfg, "level", None))
     U, G = I.initial_state(cfg)
     P = O.make_params(**cfg.params)
     for _ in range(n_warm):
@@ -138,31 +149,31 @@ def time_oracle(n_steps, n_warm=0):
     return cfg, dt
 
 
-def cpu_baseline(target_s=12.0):
-    cfg, t1 = time_oracle(1)
+def cpu_baseline(target_s=12.0, workload="puncture144"):
+    cfg, t1 = time_oracle(1, workload=workload)
     n = max(1, int(target_s / max(t1, 1e-3)))
-    cfg, t = time_oracle(n)
+    cfg, t = time_oracle(n, workload=workload)
     v = cfg.n_points * 4 * n / t
     return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d RK4 steps of the same puncture physics and dx on %d^3 points "
-                      "(4^3 patches of 9^3, [-2,2]^3), single-threaded plain C FP64" % (n, cfg.N[0])}
+            "sample": "%d RK4 steps of the same puncture physics and dx on %s, single-threaded plain C FP64"
+                      % (n, sample_text(cfg))}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    cfg, _ = time_oracle(args.warmup) if args.warmup > 0 else (oracle_sample_config(), 0.0)
-    cfg, t = time_oracle(max(args.steps, 1))
+    wl = args.workload
+    cfg, _ = time_oracle(args.warmup, workload=wl) if args.warmup > 0 else (oracle_sample_config(wl), 0.0)
+    cfg, t = time_oracle(max(args.steps, 1), workload=wl)
     v = cfg.n_points * 4 * max(args.steps, 1) / t
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / max(args.steps, 1) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(None),
+        "data": "synthetic", "config": workload_config(None, workload=wl),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "each step: one RK4 step of the puncture physics at dx = 1/9 on "
-                                   "%d^3 points (4^3 patches of 9^3)" % cfg.N[0]},
+                         "sample": "each step: one RK4 step of the puncture physics on " + sample_text(cfg)},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -170,10 +181,20 @@ def run_reference(args):
 
 
 def workload_config(g, precision="fp64", K=None, workload="puncture144"):
+    import numpy as np
     from paper_2406_11626_gb300 import inputs as I
     if workload == "small":
         cfg = I.single_puncture_config(n_side=6, half_width=3.0)
         name = "single puncture M=1, [-3,3]^3, 6^3 patches of 9^3 (54^3 points), profiling case"
+    elif workload == "mid":
+        cfg = I.single_puncture_config(n_side=10, half_width=5.0)
+        name = "single puncture M=1, [-5,5]^3, 10^3 patches of 9^3 (90^3 points), profiling case"
+    elif workload == "puncture3level":
+        cfg = I.multilevel_puncture_config()
+        name = ("single puncture M=1 on 3 static ratio-3 levels: [-8,8]^3 as 16^3 patches of 9^3 (dx 1/9), "
+                "central 4^3 refined to 12^3 patches (dx 1/27), their central 4^3 refined to 12^3 patches "
+                "(dx 1/81); 1+log, Gamma-driver eta=2, KO 0.1, Sommerfeld, RK4 dt=0.1 dx_finest, "
+                "restriction after every step")
     else:
         cfg = I.single_puncture_config()
         name = ("single puncture M=1, [-8,8]^3, 16^3 patches of 9^3 (144^3 points), "
@@ -184,9 +205,22 @@ def workload_config(g, precision="fp64", K=None, workload="puncture144"):
          "l2": "inputs larger than L2 (129 MB): each state buffer is 25 x %.2fM doubles = %.0f MB, "
                "the halo tiles %.0f MB" % ((cfg.n_points + 0) / 1e6, 8 * 25 * cfg.n_points / 1e6,
                                          8 * 25 * cfg.n_patches * (cfg.p + 6) ** 3 / 1e6)}
+    if getattr(cfg, "level", None) is not None:
+        c["levels"] = cfg.n_levels
+        c["patches_per_level"] = [int(v) for v in np.bincount(cfg.level)]
+        c["leaf_points"] = int(sum(cfg.p ** 3 for n in range(cfg.n_patches) if not _has_children(cfg, n)))
+        c["units"] = "every evolved point of every level (coarse points under finer patches included)"
     if g is not None:
         c["ghost_cells"] = g.n_ghost
     return c
+
+
+def _has_children(cfg, n):
+    l = cfg.level[n]
+    if l + 1 >= cfg.n_levels:
+        return False
+    kids = cfg.ijk()[cfg.level == l + 1] // 3
+    return bool((kids == cfg.ijk()[n]).all(axis=1).any())
 
 
 # ----------------------------------------------------------------------------
@@ -209,6 +243,8 @@ def bench_config(args):
         return I.single_puncture_config(n_side=6, half_width=3.0)
     if args.workload == "mid":
         return I.single_puncture_config(n_side=10, half_width=5.0)
+    if args.workload == "puncture3level":
+        return I.multilevel_puncture_config()
     return I.single_puncture_config()
 
 
@@ -350,6 +386,7 @@ def run_gb300(args):
                 "fp32_tflops": f32 / t_stage / 1e12,
                 "note": "frac = max(F64/P64, F32/P32) / kernel time"}
     launches_per_stage = 2 + (1 if g.n_ghost > 0 else 0)
+    restrict_per_step = g.n_levels - 1
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -362,13 +399,13 @@ def run_gb300(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * I.NV * n_state,
                 "d2h_bytes_per_step": 8 * I.NV * n_state,
                 "how": "ccz4_evolve_host per step: pinned host state -> device, one RK4 step, device -> host"},
-        "gpu_launches": launches_per_stage * 4 * K,
+        "gpu_launches": (launches_per_stage * 4 + restrict_per_step) * K,
         "constraints_after": {"L2_H": out[0], "L2_M": out[1], "max_H": out[2], "nonfinite": out[4]},
     }
     if mixed is not None:
         line["mixed"] = mixed
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(workload=args.workload)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

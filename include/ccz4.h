@@ -4,8 +4,8 @@
  * The library evolves the second-order CCZ4 formulation of the Einstein
  * equations (ExaGRyPE paper, arXiv 2406.11626, appendix "Spacetime
  * foliation": the nine primary evolution equations with the red terms
- * removed) on one uniform level of p^3 Cartesian patches with a halo of
- * width 3, discretised by fourth-order central finite differences with
+ * removed) on p^3 Cartesian patches with a halo of width 3 -- one uniform
+ * level, or a statically refined mesh of ratio-3 levels -- discretised by fourth-order central finite differences with
  * Kreiss-Oliger dissipation (appendix "Formulation for the kernel FD4
  * Solver") and classic RK4 in time (Sec. "Finite Differences"). All work
  * runs in CUDA kernels on the current device; there is no CPU fallback.
@@ -260,6 +260,76 @@ ccz4_status ccz4_constraints_noalloc(const double *tiles, int p, int n_patches, 
    out[4] = FP64 FMAs, out[5] = FP64 adds and multiplies. These are the
    algorithmic flops behind the roofline of the stage kernel. */
 ccz4_status ccz4_flops_per_point_stage(const ccz4_params *P, double out[6]);
+
+/* ---- statically refined meshes (appendix "refinement transition") ----
+
+   A mesh has ratio-3 levels of p^3 patches. Level 0 covers the np[0] x
+   np[1] x np[2] slots of the base grid (spacing dx, boundary kind bc, the
+   Sommerfeld ghost shell if any); a level-l patch (l >= 1) has spacing
+   dx / 3^l (dx divided by 3.0 once per level), slot coordinates ijk in
+   units of its own level, and is one of the 27 children (slot / 3 along
+   each axis) of a level l-1 patch, which then has all 27. Every level
+   overlaps the coarser ones: the coarse points under a refined patch are
+   evolved too and are replaced after every RK4 step (ccz4_restrict).
+
+   Halo points that a refined level does not cover are interpolated from
+   the level below at the same stage: the tensor product of three linear
+   maps between cell centres, applied along x, then y, then z, each with
+   the weights of the printed matrices P^par / P^perp (fine cell i lies on
+   coarse cells c = floor((i-1)/3) and c+1 with weights (1), (2/3, 1/3) or
+   (1/3, 2/3) for (i-1) mod 3 = 0, 1, 2). Those coarse points must be
+   interior points of the level below, inside the domain (proper nesting);
+   refined levels therefore keep away from the domain boundary.
+
+   The mesh is a ccz4_grid: every call above works on it. Buffers keep the
+   same layout with the patches in descriptor order (all levels in one
+   state vector), the stage kernels apply each level's spacing, all levels
+   share the time step, ccz4_step / ccz4_step_graph / ccz4_evolve_host
+   restrict after each step, and the constraint norms of ccz4_constraints
+   run over the points of leaf patches only (H and M are written for every
+   point). */
+#define CCZ4_MAX_LEVELS 8
+
+typedef struct {
+  int p;              /* points per patch edge, 1..18 */
+  int np[3];          /* level-0 patch slots per axis */
+  int n_patches;      /* patches of all levels */
+  const int *level;   /* host [n_patches] level of each patch, 0..CCZ4_MAX_LEVELS-1 */
+  const int *ijk;     /* host [n_patches][3] slot coordinates in units of the patch's level */
+  double origin[3];   /* lower corner of the domain */
+  double dx;          /* level-0 spacing */
+  int bc;             /* CCZ4_BC_* of the level-0 outer boundary */
+} ccz4_mesh_desc;
+
+/* Creates a mesh on the current device (see above). Validates the
+   descriptor on the host first: CCZ4_ERR_INVALID with a message for a
+   level out of range, a level-0 slot missing or listed twice, a refined
+   patch without its parent or with an incomplete set of siblings, or a
+   halo point whose interpolation sources are not interior points of the
+   level below. */
+ccz4_status ccz4_alloc_mesh(const ccz4_mesh_desc *desc, ccz4_grid **out);
+
+/* Number of levels and of points of leaf patches (the norm's point count). */
+ccz4_status ccz4_mesh_info(const ccz4_grid *g, int *n_levels, long long *n_leaf_points);
+
+/* Restriction (printed R^par of the average scheme along every axis): in
+   state buffer `buf`, every point of a patch that has children <- the mean
+   of the 3x3x3 fine cells that tile it, as three one-dimensional averages
+   with weight 1/3 (x, then y, then z), finest level first. A no-op on a
+   single level. Asynchronous. */
+ccz4_status ccz4_restrict(ccz4_grid *g, int buf, void *stream);
+
+/* Host-only plan of a mesh (needs no GPU): validates the descriptor like
+   ccz4_alloc_mesh and returns the source of every halo'd tile point.
+   n_interp receives the number of interpolated tile points. If src is not
+   NULL it receives [n_patches][(p+6)^3] entries: >= 0 the index of the
+   value within a field of a state buffer (interior points, then the
+   Sommerfeld ghost cells), <= -2 the interpolation entry -(s+2). If interp
+   is not NULL it receives [n_interp][9] ints: the eight source indices of
+   the coarse corners, in the order (z, y, x) with x fastest (corners with
+   weight zero repeat a used index), then the remainders rx | ry << 2 |
+   rz << 4. */
+ccz4_status ccz4_mesh_plan(const ccz4_mesh_desc *desc, long long *n_interp, int *src, int *interp);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *ccz4_last_error(void);

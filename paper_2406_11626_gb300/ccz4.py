@@ -34,6 +34,12 @@ class GridDesc(ctypes.Structure):
                 ("dx", ctypes.c_double), ("bc", ctypes.c_int)]
 
 
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("np", ctypes.c_int * 3), ("n_patches", ctypes.c_int),
+                ("level", ctypes.POINTER(ctypes.c_int)), ("ijk", ctypes.POINTER(ctypes.c_int)),
+                ("origin", ctypes.c_double * 3), ("dx", ctypes.c_double), ("bc", ctypes.c_int)]
+
+
 class Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("kappa1", "kappa2", "kappa3", "e", "c", "tau", "mu", "f", "eta", "s", "K0", "ko_eps")] + [
@@ -77,6 +83,11 @@ def lib():
                              _dbl_p, _dbl_p, _dbl_p, _dbl_p, vp],
         "ccz4_enforce": [vp, ctypes.c_int, vp],
         "ccz4_constraints": [vp, ctypes.c_int, _dbl_p, _dbl_p, _dbl_p, vp],
+        "ccz4_alloc_mesh": [ctypes.POINTER(MeshDesc), ctypes.POINTER(vp)],
+        "ccz4_mesh_info": [vp, ctypes.POINTER(ctypes.c_int), ll_p],
+        "ccz4_restrict": [vp, ctypes.c_int, vp],
+        "ccz4_mesh_plan": [ctypes.POINTER(MeshDesc), ll_p, ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -144,6 +155,17 @@ def _stream(stream):
     return ctypes.c_void_p(int(stream))
 
 
+def _wrap_device(ptr, shape, dtype):
+    """Zero-copy torch view of device memory owned by the library."""
+    import torch
+    typestr = {torch.float64: "<f8", torch.float32: "<f4", torch.int32: "<i4"}[dtype]
+
+    class _CAI:
+        __cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                    "version": 3, "strides": None}
+    return torch.as_tensor(_CAI(), device="cuda")
+
+
 def _buf(b):
     return BUF[b] if isinstance(b, str) else int(b)
 
@@ -152,36 +174,82 @@ def _d(a):
     return a.ctypes.data_as(_dbl_p) if a is not None else None
 
 
-class Grid:
-    """One uniform level of p^3 patches on the current CUDA device."""
+def _mesh_desc(p, np_, level, ijk, origin, dx, bc):
+    level = np.ascontiguousarray(level, dtype=np.int32).reshape(-1)
+    ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+    d = MeshDesc()
+    d.p = int(p)
+    for q in range(3):
+        d.np[q] = int(np_[q])
+        d.origin[q] = float(origin[q])
+    d.n_patches = len(ijk)
+    d.level = level.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    d.ijk = ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    d.dx = float(dx)
+    d.bc = BC[bc] if isinstance(bc, str) else int(bc)
+    return d, (level, ijk)  # keep the arrays alive with the descriptor
 
-    def __init__(self, p, np_, ijk, origin, dx, bc="periodic"):
+
+def mesh_plan(p, np_, level, ijk, origin, dx, bc="periodic"):
+    """Host-only plan of a refined mesh (no GPU needed): returns the tile
+    sources (n_patches, (p+6)^3) and the interpolation entries (n_interp, 9),
+    as ccz4_mesh_plan describes them."""
+    d, keep = _mesh_desc(p, np_, level, ijk, origin, dx, bc)
+    n = ctypes.c_longlong()
+    _check(lib().ccz4_mesh_plan(ctypes.byref(d), ctypes.byref(n), None, None))
+    T3 = (int(p) + 6) ** 3
+    src = np.empty((len(keep[1]), T3), dtype=np.int32)
+    interp = np.empty((max(n.value, 1), 9), dtype=np.int32)
+    ip = ctypes.POINTER(ctypes.c_int)
+    _check(lib().ccz4_mesh_plan(ctypes.byref(d), ctypes.byref(n), src.ctypes.data_as(ip), interp.ctypes.data_as(ip)))
+    return src, interp[:n.value]
+
+
+class Grid:
+    """p^3 patches on the current CUDA device: one uniform level, or (with
+    ``level``) a statically refined mesh of ratio-3 levels whose level-l
+    patches have spacing dx / 3^l and slots ijk in level-l units."""
+
+    def __init__(self, p, np_, ijk, origin, dx, bc="periodic", level=None):
         L = lib()
         self.p = int(p)
         self.np = tuple(int(v) for v in np_)
         self.ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
         self.n_patches = len(self.ijk)
-        d = GridDesc()
-        d.p = self.p
-        for q in range(3):
-            d.np[q] = self.np[q]
-            d.origin[q] = float(origin[q])
-        d.n_patches = self.n_patches
-        d.ijk = self.ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
-        d.dx = float(dx)
-        d.bc = BC[bc] if isinstance(bc, str) else int(bc)
         h = ctypes.c_void_p()
-        _check(L.ccz4_alloc_patches(ctypes.byref(d), ctypes.byref(h)))
+        if level is None:
+            d = GridDesc()
+            d.p = self.p
+            for q in range(3):
+                d.np[q] = self.np[q]
+                d.origin[q] = float(origin[q])
+            d.n_patches = self.n_patches
+            d.ijk = self.ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+            d.dx = float(dx)
+            d.bc = BC[bc] if isinstance(bc, str) else int(bc)
+            _check(L.ccz4_alloc_patches(ctypes.byref(d), ctypes.byref(h)))
+            self.level = np.zeros(self.n_patches, dtype=np.int32)
+        else:
+            d, keep = _mesh_desc(self.p, self.np, level, self.ijk, origin, dx, bc)
+            _check(L.ccz4_alloc_mesh(ctypes.byref(d), ctypes.byref(h)))
+            self.level = keep[0]
         self._h = h
         n, g, s = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
         _check(L.ccz4_grid_info(h, ctypes.byref(n), ctypes.byref(g), ctypes.byref(s)))
         self.n_points, self.n_ghost, self.field_stride = n.value, g.value, s.value
+        nl, nleaf = ctypes.c_int(), ctypes.c_longlong()
+        _check(L.ccz4_mesh_info(h, ctypes.byref(nl), ctypes.byref(nleaf)))
+        self.n_levels, self.n_leaf_points = nl.value, nleaf.value
         self.origin = tuple(float(v) for v in origin)
         self.dx = float(dx)
 
     @classmethod
     def from_config(cls, cfg):
-        return cls(cfg.p, cfg.np, cfg.ijk(), cfg.origin, cfg.dx, cfg.bc)
+        return cls(cfg.p, cfg.np, cfg.ijk(), cfg.origin, cfg.dx, cfg.bc, level=getattr(cfg, "level", None))
+
+    def restrict(self, buf="U", stream=None):
+        """Coarse points under refined patches <- mean of their 27 fine cells."""
+        _check(lib().ccz4_restrict(self._h, _buf(buf), _stream(stream)))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -227,11 +295,7 @@ class Grid:
         """Zero-copy torch view (1-D, float64) of a device buffer."""
         import torch
         ptr, n = self.device_ptr(buf)
-
-        class _CAI:
-            __cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (ptr, False),
-                                        "version": 3, "strides": None}
-        return torch.as_tensor(_CAI(), device="cuda")
+        return _wrap_device(ptr, (n,), torch.float64)
 
     # -- the hot path -----------------------------------------------------------
     def fill_halos(self, buf="U", stream=None):

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "ccz4_internal.cuh"
+#include "mesh_plan.h"
 
 namespace ccz4 {
 
@@ -82,8 +83,20 @@ static void free_all(ccz4_grid *g) {
   cudaFree(g->red_partial);
   cudaFree(g->red_out);
   cudaFreeHost(g->host_out);
+  cudaFree(g->d_src);
+  cudaFree(g->d_interp);
+  cudaFree(g->d_ibeg);
+  cudaFree(g->d_plev);
+  cudaFree(g->d_leaf);
+  for (int l = 0; l < CCZ4_MAX_LEVELS; ++l) {
+    cudaFree(g->d_rpar[l]);
+    cudaFree(g->d_rkid[l]);
+  }
   free(g);
 }
+
+static ccz4_status create_grid(const ccz4_grid_desc *d, const std::vector<int> &owner, const MeshPlan *mesh,
+                               ccz4_grid **out);
 
 extern "C" ccz4_status ccz4_alloc_patches(const ccz4_grid_desc *d, ccz4_grid **out) {
   if (!out) {
@@ -132,6 +145,44 @@ extern "C" ccz4_status ccz4_alloc_patches(const ccz4_grid_desc *d, ccz4_grid **o
     }
     owner[cell] = n;
   }
+  return create_grid(d, owner, nullptr, out);
+}
+
+extern "C" ccz4_status ccz4_alloc_mesh(const ccz4_mesh_desc *m, ccz4_grid **out) {
+  if (!out) {
+    set_error("out is NULL");
+    return CCZ4_ERR_INVALID;
+  }
+  *out = nullptr;
+  MeshPlan plan;
+  ccz4_status st = plan_mesh(m, true, plan);
+  if (st != CCZ4_OK) return st;
+  ccz4_grid_desc d;
+  d.p = m->p;
+  d.n_patches = m->n_patches;
+  d.ijk = m->ijk;
+  for (int q = 0; q < 3; ++q) {
+    d.np[q] = m->np[q];
+    d.origin[q] = m->origin[q];
+  }
+  d.dx = m->dx;
+  d.bc = m->bc;
+  return create_grid(&d, plan.owner0, &plan, out);
+}
+
+template <class T>
+static bool upload_table(T **dst, const T *src, size_t n) {
+  if (n == 0) return true;
+  if (cudaMalloc(dst, sizeof(T) * n) != cudaSuccess) return false;
+  return cudaMemcpy(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+// Builds the device grid of a validated descriptor: level-0 slot owners in
+// `owner`; `mesh` holds the tables of a refined mesh, or is NULL.
+static ccz4_status create_grid(const ccz4_grid_desc *d, const std::vector<int> &owner, const MeshPlan *mesh,
+                               ccz4_grid **out) {
+  const long long slots = (long long)d->np[0] * d->np[1] * d->np[2];
+  const long long Nx = (long long)d->np[0] * d->p, Ny = (long long)d->np[1] * d->p, Nz = (long long)d->np[2] * d->p;
   ccz4_grid *g = (ccz4_grid *)calloc(1, sizeof(ccz4_grid));
   if (!g) {
     set_error("host allocation failed");
@@ -152,6 +203,10 @@ extern "C" ccz4_status ccz4_alloc_patches(const ccz4_grid_desc *d, ccz4_grid **o
   v.dx = d->dx;
   v.n_points = (long long)d->n_patches * d->p * d->p * d->p;
   v.T3 = (long long)v.T * v.T * v.T;
+  v.n_levels = mesh ? mesh->n_levels : 1;
+  v.n_leaf_points = mesh ? mesh->n_leaf_points : v.n_points;
+  v.ldx[0] = d->dx;
+  for (int l = 1; l < MAX_LEVELS; ++l) v.ldx[l] = v.ldx[l - 1] / 3.0;
   std::vector<int> gcoord;
   if (d->bc == CCZ4_BC_SOMMERFELD) {
     v.n_ghost = (Nx + 6) * (Ny + 6) * (Nz + 6) - Nx * Ny * Nz;
@@ -213,6 +268,23 @@ extern "C" ccz4_status ccz4_alloc_patches(const ccz4_grid_desc *d, ccz4_grid **o
   if (!gcoord.empty())
     cudaMemcpy(g->d_gcoord, gcoord.data(), sizeof(int) * gcoord.size(), cudaMemcpyHostToDevice);
   cudaMemset(g->d_status, 0, sizeof(unsigned));
+  if (mesh) {
+    ok = upload_table(&g->d_src, mesh->src.data(), mesh->src.size()) &&
+         upload_table(&g->d_interp, mesh->interp.data(), mesh->interp.size()) &&
+         upload_table(&g->d_ibeg, mesh->ibeg.data(), mesh->ibeg.size()) &&
+         upload_table(&g->d_plev, mesh->level.data(), mesh->level.size()) &&
+         upload_table(&g->d_leaf, mesh->leaf.data(), mesh->leaf.size());
+    for (int l = 1; l < mesh->n_levels && ok; ++l) {
+      g->n_rpar[l] = (int)mesh->rpar[l].size();
+      ok = upload_table(&g->d_rpar[l], mesh->rpar[l].data(), mesh->rpar[l].size()) &&
+           upload_table(&g->d_rkid[l], mesh->rkid[l].data(), mesh->rkid[l].size());
+    }
+    if (!ok) {
+      set_error("device allocation of the mesh tables failed: %s", cudaGetErrorString(cudaGetLastError()));
+      free_all(g);
+      return CCZ4_ERR_NOMEM;
+    }
+  }
   prepare_fill_halos(v.p);
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -224,6 +296,11 @@ extern "C" ccz4_status ccz4_alloc_patches(const ccz4_grid_desc *d, ccz4_grid **o
   v.owner = g->d_owner;
   v.gcoord = g->d_gcoord;
   v.status = g->d_status;
+  v.src = g->d_src;
+  v.interp = g->d_interp;
+  v.ibeg = g->d_ibeg;
+  v.plev = g->d_plev;
+  v.leaf = g->d_leaf;
   *out = g;
   return CCZ4_OK;
 }
@@ -341,11 +418,30 @@ extern "C" ccz4_status ccz4_rhs(ccz4_grid *g, const ccz4_params *P, int in_buf, 
 static const int kStageIn[4] = {CCZ4_BUF_U, CCZ4_BUF_Y0, CCZ4_BUF_Y1, CCZ4_BUF_Y0};
 static const int kStageOut[4] = {CCZ4_BUF_Y0, CCZ4_BUF_Y1, CCZ4_BUF_Y0, CCZ4_BUF_U};
 
+// Restriction of every refined level onto the one below, finest first.
+static ccz4_status restrict_levels(ccz4_grid *g, double *U, cudaStream_t s) {
+  for (int l = g->v.n_levels - 1; l >= 1; --l)
+    CUDA_TRY(launch_restrict(g->v, g->d_rpar[l], g->d_rkid[l], g->n_rpar[l], U, s));
+  return CCZ4_OK;
+}
+
+// One RK4 stage from the halo'd tiles; stage 3 ends the step (enforcement
+// in the stage kernel, then the restriction on a mesh).
 static ccz4_status stage_kernel(ccz4_grid *g, const ccz4_params *P, int stage, double dt, cudaStream_t s) {
   double *in = g->buf[kStageIn[stage]];
   CUDA_TRY(launch_rk_stage(g->v, *P, stage, dt, g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], in, ini_ptr(g), g->buf[CCZ4_BUF_U],
                            g->buf[CCZ4_BUF_ACC], g->buf[kStageOut[stage]], s));
+  if (stage == 3 && g->v.n_levels > 1) return restrict_levels(g, g->buf[kStageOut[stage]], s);
   return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_restrict(ccz4_grid *g, int buf, void *stream) {
+  if (check_grid(g)) return CCZ4_ERR_INVALID;
+  if (!state_buffer(buf) || !g->buf[buf]) {
+    set_error("restrict: buffer %d is not a state buffer of this grid", buf);
+    return CCZ4_ERR_INVALID;
+  }
+  return restrict_levels(g, g->buf[buf], (cudaStream_t)stream);
 }
 
 extern "C" ccz4_status ccz4_stage_buffers(int stage, int *in_buf, int *out_buf) {

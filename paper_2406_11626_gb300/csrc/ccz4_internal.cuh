@@ -32,6 +32,19 @@ __host__ __device__ __forceinline__ constexpr int mix_slot(int v) {
                                : -1;
 }
 
+constexpr int MAX_LEVELS = CCZ4_MAX_LEVELS;
+
+// One interpolated halo point of a refined mesh: the source indices of the
+// 2x2x2 coarse corners, (z, y, x) with x fastest, the remainders
+// r = rx | ry << 2 | rz << 4 that select the weights along each axis, and
+// the point's index t in its patch's tile. The entries of a patch are
+// contiguous (patch after patch).
+struct InterpEntry {
+  int src[8];
+  int r;
+  int t;
+};
+
 // Plain-data view of a grid, passed by value to every kernel.
 struct GridView {
   int p, T;                    // points per patch edge; tile edge p + 2*HALO
@@ -47,7 +60,21 @@ struct GridView {
   const int *owner;            // [np2][np1][np0] -> patch id
   const int *gcoord;           // [n_ghost][3] global coordinates of the ghost cells
   unsigned *status;            // device status word
+  // refined meshes only (src == nullptr on a single level)
+  int n_levels;
+  long long n_leaf_points;     // points of patches without children
+  const int *src;              // [n_patches][T3] tile sources: >= 0 index, <= -2 entry -(s+2)
+  const InterpEntry *interp;   // interpolated tile points
+  const int *ibeg;             // [n_patches + 1] first entry of each patch in interp
+  const int *plev;             // [n_patches] level of each patch
+  const unsigned char *leaf;   // [n_patches] 1 if the patch has no children
+  double ldx[MAX_LEVELS];      // spacing of each level (ldx[0] = dx)
 };
+
+// Level of patch n (0 on a single level).
+__device__ __forceinline__ int patch_level(const GridView &g, int n) {
+  return g.plev ? __ldg(g.plev + n) : 0;
+}
 
 __host__ __device__ __forceinline__ int wrap(int a, int n) {
   int r = a % n;
@@ -124,6 +151,15 @@ struct ccz4_grid {
   cudaGraphExec_t step_exec; // one captured RK4 step, or NULL
   ccz4_params step_P;        // parameters and dt baked into step_exec
   double step_dt;
+  // refined meshes: tile sources, interpolation entries, levels, leaf flags
+  // and, per level l >= 1, the parents on level l-1 with their 27 children
+  int *d_src;
+  ccz4::InterpEntry *d_interp;
+  int *d_ibeg;
+  int *d_plev;
+  unsigned char *d_leaf;
+  int *d_rpar[CCZ4_MAX_LEVELS], *d_rkid[CCZ4_MAX_LEVELS];
+  int n_rpar[CCZ4_MAX_LEVELS];
 };
 
 // Kernel launchers (one translation unit each).
@@ -140,6 +176,9 @@ cudaError_t launch_rk_stage(const GridView &g, const ccz4_params &P, int stage, 
                             const double *tile, const double *mix, const double *in, const double *ini,
                             const double *U, double *acc, double *out, cudaStream_t s);
 cudaError_t launch_enforce(const GridView &g, double *U, cudaStream_t s);
+// restriction of level l onto the n_par parents par[] of level l-1 (children kid[n_par][27])
+cudaError_t launch_restrict(const GridView &g, const int *par, const int *kid, int n_par, double *U,
+                            cudaStream_t s);
 cudaError_t launch_constraints(const GridView &g, const double *tile, double *H, double *M,
                                double *partial, int blocks, double *out5, cudaStream_t s);
 }  // namespace ccz4

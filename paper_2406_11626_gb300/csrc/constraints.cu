@@ -199,7 +199,11 @@ __device__ void constraints_point(const Nbhd &N, const StencilCoef<double> &C, d
   }
 }
 
-__global__ void __launch_bounds__(RED_THREADS) constraints_kernel(GridView g, StencilCoef<double> C,
+struct ConsCoef {
+  StencilCoef<double> C[MAX_LEVELS];
+};
+
+__global__ void __launch_bounds__(RED_THREADS) constraints_kernel(GridView g, ConsCoef LC,
                                                                   const double *__restrict__ tile,
                                                                   double *H, double *M, double *partial) {
   __shared__ double sh[5][RED_THREADS];
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(RED_THREADS) constraints_kernel(GridView g, St
     N.mix = nullptr;
     N.ms = 0;
     double h, m[3];
-    constraints_point(N, C, h, m);
+    constraints_point(N, LC.C[patch_level(g, n)], h, m);
     if (H) H[i] = h;
     if (M) {
       M[i] = m[0];
@@ -228,12 +232,14 @@ __global__ void __launch_bounds__(RED_THREADS) constraints_kernel(GridView g, St
       M[2 * g.n_points + i] = m[2];
     }
     const double m2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
-    if (isfinite(h) && isfinite(m2)) {
+    // the norms count leaf patches only (a covered point is not counted twice)
+    const bool counted = !g.leaf || __ldg(g.leaf + n);
+    if (counted && isfinite(h) && isfinite(m2)) {
       v[0] = h * h;
       v[1] = m2;
       v[2] = fabs(h);
       v[3] = sqrt(m2);
-    } else {
+    } else if (counted) {
       v[4] = 1.0;
     }
   }
@@ -310,17 +316,20 @@ int constraint_blocks(long long n_points) { return (int)((n_points + RED_THREADS
 
 cudaError_t launch_constraints(const GridView &g, const double *tile, double *H, double *M, double *partial,
                                int blocks, double *out5, cudaStream_t s) {
-  StencilCoef<double> C;
-  C.c1 = 1.0 / (12.0 * g.dx);
-  C.c2 = 1.0 / (12.0 * g.dx * g.dx);
-  C.c3 = 1.0 / (144.0 * g.dx * g.dx);
-  C.cko = 0.0;
+  ConsCoef LC;
+  for (int l = 0; l < MAX_LEVELS; ++l) {
+    const double dx = g.ldx[l];
+    LC.C[l].c1 = 1.0 / (12.0 * dx);
+    LC.C[l].c2 = 1.0 / (12.0 * dx * dx);
+    LC.C[l].c3 = 1.0 / (144.0 * dx * dx);
+    LC.C[l].cko = 0.0;
+  }
   if (blocks > 0) {
-    constraints_kernel<<<blocks, RED_THREADS, 0, s>>>(g, C, tile, H, M, partial);
+    constraints_kernel<<<blocks, RED_THREADS, 0, s>>>(g, LC, tile, H, M, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  reduce_partials<<<1, RED_THREADS, 0, s>>>(partial, blocks, (double)g.n_points, out5);
+  reduce_partials<<<1, RED_THREADS, 0, s>>>(partial, blocks, (double)g.n_leaf_points, out5);
   return cudaGetLastError();
 }
 

@@ -4,8 +4,9 @@
 // sits in shared memory.
 //
 // One CTA per patch. It resolves the source of every tile point once
-// (neighbour patch, periodic wrap, clamped copy or Sommerfeld ghost cell)
-// into an index table, then for each of the 25 fields gathers the field's
+// (neighbour patch, periodic wrap, clamped copy or Sommerfeld ghost cell;
+// on a refined mesh it reads the host-built table instead, whose entries
+// may also be coarse-to-fine interpolations) into an index table, then for each of the 25 fields gathers the field's
 // tile into shared memory and writes it out with coalesced stores. For g~,
 // alpha, beta and phi it also forms the mixed derivatives d_x d_y, d_x d_z,
 // d_y d_z as the first-derivative stencil applied to first derivatives
@@ -22,9 +23,46 @@ namespace {
 constexpr int FILL_THREADS = 256;
 constexpr int GATHER_BATCH = 8;
 
+// Scale of the mixed derivatives, 1 / (144 dx^2), per level.
+struct LevelScale {
+  double cmix[MAX_LEVELS];
+};
+
+// Linear-interpolation weights between coarse cell centres for remainder
+// r = (i - 1) mod 3 of fine index i: the rows (1), (2/3, 1/3), (1/3, 2/3)
+// of the printed matrices P^par and P^perp.
+__device__ __forceinline__ double pw(int r, int k) {
+  return r == 0 ? (k == 0 ? 1.0 : 0.0) : r == 1 ? (k == 0 ? 2.0 / 3.0 : 1.0 / 3.0) : (k == 0 ? 1.0 / 3.0 : 2.0 / 3.0);
+}
+
+// Value of an interpolated halo point of a refined mesh: the tensor product
+// of three linear maps, along x, then y, then z; every product and sum is
+// rounded on its own (no fused multiply-add), in that order.
+__device__ __forceinline__ double interp_value(const InterpEntry *__restrict__ e, const double *__restrict__ sv) {
+  const int r = __ldg(&e->r);
+  const int rx = r & 3, ry = (r >> 2) & 3, rz = (r >> 4) & 3;
+  double t[2][2], u[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    if (c == 1 && rz == 0) break;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      if (b == 1 && ry == 0) break;
+      const double q0 = __ldg(sv + __ldg(&e->src[(c * 2 + b) * 2]));
+      t[c][b] = rx ? __dadd_rn(__dmul_rn(pw(rx, 0), q0), __dmul_rn(pw(rx, 1), __ldg(sv + __ldg(&e->src[(c * 2 + b) * 2 + 1]))))
+                   : q0;
+    }
+    u[c] = ry ? __dadd_rn(__dmul_rn(pw(ry, 0), t[c][0]), __dmul_rn(pw(ry, 1), t[c][1])) : t[c][0];
+  }
+  return rz ? __dadd_rn(__dmul_rn(pw(rz, 0), u[0]), __dmul_rn(pw(rz, 1), u[1])) : u[0];
+}
+
+// MESH: the tile sources come from the host-built table of a refined mesh
+// (and may be interpolations); otherwise they are resolved here.
+template <bool MESH>
 __global__ void __launch_bounds__(FILL_THREADS, 4) fill_halos_kernel(GridView g, const double *__restrict__ src,
                                                                   double *__restrict__ tile,
-                                                                  double *__restrict__ mix, double cmix) {
+                                                                  double *__restrict__ mix, LevelScale ls) {
   extern __shared__ double smem[];
   const int n = blockIdx.x;
   const int p = g.p, T = g.T;
@@ -37,11 +75,18 @@ __global__ void __launch_bounds__(FILL_THREADS, 4) fill_halos_kernel(GridView g,
   const int bx = __ldg(g.ijk + 3 * n) * p - HALO;
   const int by = __ldg(g.ijk + 3 * n + 1) * p - HALO;
   const int bz = __ldg(g.ijk + 3 * n + 2) * p - HALO;
-  for (int t = threadIdx.x; t < T3; t += blockDim.x) {
-    const int lz = t / (T * T), ly = (t / T) % T, lx = t % T;
-    const long long s = locate(g, bx + lx, by + ly, bz + lz);
-    idx[t] = (int)s;
+  if (MESH) {
+    // refined mesh: sources resolved once on the host
+    const int *sp = g.src + (long long)n * T3;
+    for (int t = threadIdx.x; t < T3; t += blockDim.x) idx[t] = __ldg(sp + t);
+  } else {
+    for (int t = threadIdx.x; t < T3; t += blockDim.x) {
+      const int lz = t / (T * T), ly = (t / T) % T, lx = t % T;
+      const long long s = locate(g, bx + lx, by + ly, bz + lz);
+      idx[t] = (int)s;
+    }
   }
+  const double cmix = MESH ? ls.cmix[patch_level(g, n)] : ls.cmix[0];
   __syncthreads();
   const long long p3 = (long long)p * p * p;
   const long long pbase = (long long)n * p3;
@@ -62,10 +107,21 @@ __global__ void __launch_bounds__(FILL_THREADS, 4) fill_halos_kernel(GridView g,
 #pragma unroll
       for (int u = 0; u < GATHER_BATCH; ++u) {
         const int t = t0 + u * FILL_THREADS;
-        if (t < T3) {
+        // on a mesh, interpolated points (s <= -2) are written by the pass below
+        if (t < T3 && (!MESH || idx[t] > -2)) {
           if (slot >= 0) ts[t] = val[u];
           __stcs(tv + t, val[u]);  // read once, by the stage kernel
         }
+      }
+    }
+    if (MESH) {
+      // the patch's interpolated halo points, one entry per thread
+      const int e1 = __ldg(g.ibeg + n + 1);
+      for (int e = __ldg(g.ibeg + n) + threadIdx.x; e < e1; e += FILL_THREADS) {
+        const double val = interp_value(g.interp + e, sv);
+        const int t = __ldg(&g.interp[e].t);
+        if (slot >= 0) ts[t] = val;
+        __stcs(tv + t, val);
       }
     }
     if (slot < 0) continue;  // uniform across the block
@@ -105,14 +161,21 @@ size_t fill_smem_bytes(int p) {
 // Raises the kernel's dynamic shared-memory limit for patch edge p (once per
 // grid, outside any stream capture).
 cudaError_t prepare_fill_halos(int p) {
-  return cudaFuncSetAttribute(fill_halos_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)fill_smem_bytes(MAX_P > p ? MAX_P : p));
+  const int bytes = (int)fill_smem_bytes(MAX_P > p ? MAX_P : p);
+  cudaError_t e = cudaFuncSetAttribute(fill_halos_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fill_halos_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile, double *mix, cudaStream_t s) {
   if (g.n_patches == 0) return cudaSuccess;
   const size_t bytes = fill_smem_bytes(g.p);
-  fill_halos_kernel<<<g.n_patches, FILL_THREADS, bytes, s>>>(g, src, tile, mix, 1.0 / (144.0 * g.dx * g.dx));
+  LevelScale ls;
+  for (int l = 0; l < MAX_LEVELS; ++l) ls.cmix[l] = 1.0 / (144.0 * g.ldx[l] * g.ldx[l]);
+  if (g.src)
+    fill_halos_kernel<true><<<g.n_patches, FILL_THREADS, bytes, s>>>(g, src, tile, mix, ls);
+  else
+    fill_halos_kernel<false><<<g.n_patches, FILL_THREADS, bytes, s>>>(g, src, tile, mix, ls);
   return cudaGetLastError();
 }
 

@@ -83,6 +83,10 @@ extern "C" ccz4_status ccz4_constraints_noalloc(const double *tiles, int p, int 
   v.n_points = n_points;
   v.T3 = (long long)v.T * v.T * v.T;
   v.dx = dx;
+  v.n_levels = 1;
+  v.n_leaf_points = n_points;
+  v.ldx[0] = dx;
+  for (int l = 1; l < MAX_LEVELS; ++l) v.ldx[l] = v.ldx[l - 1] / 3.0;
   const int blocks = constraint_blocks(n_points);
   cudaError_t e = launch_constraints(v, tiles, dev_H, dev_M, partials, blocks, dev_out, (cudaStream_t)stream);
   if (e != cudaSuccess) {

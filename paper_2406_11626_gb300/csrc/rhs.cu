@@ -1,210 +1,34 @@
-// Right-hand side and fused RK4 stage kernels.
-//
-// interior_kernel: one thread per interior point reads its halo'd
-// neighbourhood from the tile buffer, evaluates the CCZ4 right-hand side
-// plus Kreiss-Oliger dissipation, and either stores it (plain RHS) or
-// applies the RK4 stage update in the same pass, so the right-hand side
-// never travels through HBM. The last stage also enforces the algebraic
-// constraints on the new state. R is the type of the pointwise algebra
-// (double: FP64 path; float: mixed path).
-// ghost_kernel: one thread per evolved Sommerfeld ghost cell (Eq.
-// exa_sommerfeld_inter), same stage update, no enforcement, FP64.
-#include "ccz4_algebra.cuh"
-
-// Minimum resident blocks of 128 threads per SM requested for the stage
-// kernel. 4 caps ptxas at 128 registers per thread (16 warps per SM): the
-// kernel spills more than at 255 registers (8 warps per SM), but the extra
-// warps hide the latency of the narrow FP64 pipe and of instruction fetch
-// (measured on GB300: 51.2 -> 42.5 ms per RK4 step for the mixed path at
-// 144^3, 62.7 -> 62.2 ms for the FP64 path).
-#ifndef CCZ4_INTERIOR_MIN_BLOCKS
-#define CCZ4_INTERIOR_MIN_BLOCKS 4
-#endif
+// Stage kernels of a single uniform level, and the dispatch of the stage
+// launches between single levels and refined meshes.
+#include "stage_kernels.cuh"
 
 namespace ccz4 {
-namespace {
 
-struct StageArgs {
-  const double *U;  // U_n
-  double *acc;      // RK accumulator
-  double *out;      // plain RHS (MODE < 0), next stage state, or U_{n+1}
-  double dt;
-};
-
-// MODE < 0: store k. MODE = s in 0..3: RK4 stage s.
-template <int MODE>
-__device__ __forceinline__ void finish_point(const GridView &g, long long i, double k[NV],
-                                             const StageArgs &a, bool interior) {
-  const long long S = g.S;
-  if (MODE < 0) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) a.out[v * S + i] = k[v];
-    return;
-  }
-  double un[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    double acc = MODE == 0 ? 0.0 : a.acc[v * S + i];
-    un[v] = rk_combine<(MODE < 0 ? 0 : MODE), double>(a.U[v * S + i], acc, k[v], a.dt);
-    if (MODE < 3) a.acc[v * S + i] = acc;
-  }
-  if (MODE == 3 && interior) enforce_point<double>(un + GXX, un + AXX);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) a.out[v * S + i] = un[v];
+cudaError_t launch_stage_uniform(const GridView &g, const ccz4_params &P, int stage, const double *tile,
+                                 const double *mix, const double *in, const double *ini, const StageArgs &a,
+                                 cudaStream_t s) {
+  return launch_stage<false>(g, P, stage, tile, mix, in, ini, a, s);
 }
 
-// Receives d_t Q_v of one interior point field by field and applies the
-// stage update at once, so finished values leave the registers early. The
-// last stage holds g~ and A~ back for the algebraic enforcement.
-template <int MODE>
-struct StageSink {
-  const GridView &g;
-  long long i;
-  const StageArgs &a;
-  double ug[6], uA[6];
-  __device__ __forceinline__ void operator()(int v, double k) {
-    const long long o = v * g.S + i;
-    if (MODE < 0) {
-      a.out[o] = k;
-      return;
-    }
-    double acc = MODE == 0 ? 0.0 : a.acc[o];
-    const double un = rk_combine<(MODE < 0 ? 0 : MODE), double>(a.U[o], acc, k, a.dt);
-    if (MODE < 3) a.acc[o] = acc;
-    if (MODE == 3 && v >= GXX && v <= GZZ) {
-      ug[v - GXX] = un;
-      return;
-    }
-    if (MODE == 3 && v >= AXX && v <= AZZ) {
-      uA[v - AXX] = un;
-      return;
-    }
-    a.out[o] = un;
-  }
-  __device__ __forceinline__ void finish() {
-    if (MODE != 3) return;
-    enforce_point<double>(ug, uA);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      a.out[(GXX + c) * g.S + i] = ug[c];
-      a.out[(AXX + c) * g.S + i] = uA[c];
-    }
-  }
-};
-
-template <int MODE, class R>
-__global__ void __launch_bounds__(128, CCZ4_INTERIOR_MIN_BLOCKS) interior_kernel(GridView g, Phys<R> P, StencilCoef<double> C,
-                                                          StencilCoef<R> CR, const double *__restrict__ tile,
-                                                          const double *__restrict__ mix, StageArgs a) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.n_points) return;
-  const int p = g.p, T = g.T;
-  const long long p3 = (long long)p * p * p;
-  const int n = (int)(i / p3);
-  const int r = (int)(i - n * p3);
-  const int z = r / (p * p), y = (r / p) % p, x = r % p;
-  Nbhd N;
-  N.c = tile + n * g.T3 + ((long long)(z + HALO) * T + (y + HALO)) * T + (x + HALO);
-  N.fs = (long long)g.n_patches * g.T3;
-  N.st[0] = 1;
-  N.st[1] = T;
-  N.st[2] = T * T;
-  N.mix = mix + i;
-  N.ms = g.n_points;
-  StageSink<MODE> sink{g, i, a};
-  ccz4_rhs_point<double, R>(P, N, C, CR, sink);
-  sink.finish();
+static cudaError_t dispatch(const GridView &g, const ccz4_params &P, int stage, const double *tile,
+                            const double *mix, const double *in, const double *ini, const StageArgs &a,
+                            cudaStream_t s) {
+  if (g.src) return launch_stage_mesh(g, P, stage, tile, mix, in, ini, a, s);
+  return launch_stage_uniform(g, P, stage, tile, mix, in, ini, a, s);
 }
-
-template <int MODE>
-__global__ void __launch_bounds__(128) ghost_kernel(GridView g, ccz4_params P, const double *__restrict__ in,
-                                                    const double *__restrict__ ini, StageArgs a) {
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= g.n_ghost) return;
-  int c[3] = {__ldg(g.gcoord + 3 * id), __ldg(g.gcoord + 3 * id + 1), __ldg(g.gcoord + 3 * id + 2)};
-  // the face a ghost cell belongs to: its highest outside axis
-  int d = 0, side = 0;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    if (c[q] < 0) { d = q; side = -1; }
-    if (c[q] >= g.N[q]) { d = q; side = 1; }
-  }
-  int nb[3] = {c[0], c[1], c[2]};
-  nb[d] -= side;
-  const long long sn = locate(g, nb[0], nb[1], nb[2]);
-  if (sn < 0 || side == 0) return;
-  double xs[3];
-#pragma unroll
-  for (int q = 0; q < 3; ++q) xs[q] = g.origin[q] + (c[q] + 0.5) * g.dx;
-  const double rr = sqrt(xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2]);
-  const double ir = 1.0 / rr;
-  const double geo = rr / xs[d] * (side > 0 ? 1.0 : -1.0) / g.dx;  // (r / x_d) * sign / dx
-  const long long self = g.n_points + id;
-  double k[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const double qg = __ldg(in + v * g.S + self);
-    const double qn = __ldg(in + v * g.S + sn);
-    const double cv = P.somm_speed[v];
-    k[v] = -cv * geo * (qg - qn) - cv * ir * (qg - __ldg(ini + v * g.S + self));
-  }
-  finish_point<MODE>(g, self, k, a, false);
-}
-
-StencilCoef<double> coefs(const GridView &g, const ccz4_params &P) {
-  StencilCoef<double> C;
-  C.c1 = 1.0 / (12.0 * g.dx);
-  C.c2 = 1.0 / (12.0 * g.dx * g.dx);
-  C.c3 = 1.0 / (144.0 * g.dx * g.dx);
-  C.cko = P.ko_eps / (64.0 * g.dx);
-  return C;
-}
-
-template <int MODE, class R>
-cudaError_t launch_mode(const GridView &g, const ccz4_params &P, const double *tile, const double *mix,
-                        const double *in, const double *ini, const StageArgs &a, cudaStream_t s) {
-  if (g.n_points > 0) {
-    const long long blocks = (g.n_points + 127) / 128;
-    const StencilCoef<double> C = coefs(g, P);
-    const StencilCoef<R> CR{R(C.c1), R(C.c2), R(C.c3), R(C.cko)};
-    interior_kernel<MODE, R><<<(unsigned)blocks, 128, 0, s>>>(g, make_phys<R>(P), C, CR, tile, mix, a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  if (g.n_ghost > 0) {
-    const long long blocks = (g.n_ghost + 127) / 128;
-    ghost_kernel<MODE><<<(unsigned)blocks, 128, 0, s>>>(g, P, in, ini, a);
-    return cudaGetLastError();
-  }
-  return cudaSuccess;
-}
-
-template <int MODE>
-cudaError_t launch_prec(const GridView &g, const ccz4_params &P, const double *tile, const double *mix,
-                        const double *in, const double *ini, const StageArgs &a, cudaStream_t s) {
-  if (P.precision == CCZ4_PREC_MIXED) return launch_mode<MODE, float>(g, P, tile, mix, in, ini, a, s);
-  return launch_mode<MODE, double>(g, P, tile, mix, in, ini, a, s);
-}
-
-}  // namespace
 
 cudaError_t launch_rhs(const GridView &g, const ccz4_params &P, const double *tile, const double *mix,
                        const double *in, const double *ini, double *out, cudaStream_t s) {
   StageArgs a{nullptr, nullptr, out, 0.0};
-  return launch_prec<-1>(g, P, tile, mix, in, ini, a, s);
+  return dispatch(g, P, -1, tile, mix, in, ini, a, s);
 }
 
 cudaError_t launch_rk_stage(const GridView &g, const ccz4_params &P, int stage, double dt,
                             const double *tile, const double *mix, const double *in, const double *ini,
                             const double *U, double *acc, double *out, cudaStream_t s) {
+  if (stage < 0 || stage > 3) return cudaErrorInvalidValue;
   StageArgs a{U, acc, out, dt};
-  switch (stage) {
-    case 0: return launch_prec<0>(g, P, tile, mix, in, ini, a, s);
-    case 1: return launch_prec<1>(g, P, tile, mix, in, ini, a, s);
-    case 2: return launch_prec<2>(g, P, tile, mix, in, ini, a, s);
-    case 3: return launch_prec<3>(g, P, tile, mix, in, ini, a, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return dispatch(g, P, stage, tile, mix, in, ini, a, s);
 }
 
 }  // namespace ccz4

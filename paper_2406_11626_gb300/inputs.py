@@ -281,11 +281,51 @@ def single_puncture_config(p=9, n_side=16, half_width=8.0, steps=200, cfl=0.1, p
                   dict(PUNCTURE_PARAMS), cfl * dx, steps, permute_seed, dict(M=1.0))
 
 
+@dataclass
+class MeshConfig(Config):
+    """A workload on a statically refined mesh: Config's level-0 grid plus
+    the level and slot (in units of its level) of every patch."""
+    level: np.ndarray = None
+    mesh_ijk: np.ndarray = None
+
+    @property
+    def n_patches(self):
+        return len(self.level)
+
+    @property
+    def n_levels(self):
+        return int(self.level.max()) + 1
+
+    def ijk(self):
+        return self.mesh_ijk
+
+
+def multilevel_puncture_config(p=9, n_side=16, half_width=8.0, boxes=None, steps=20, cfl=0.1):
+    """The single-puncture physics on ratio-3 static levels around the
+    puncture. Default: [-8, 8]^3 as 16^3 level-0 patches of 9^3 (dx = 1/9),
+    the central 4^3 of them refined into 12^3 level-1 patches, whose central
+    4^3 are refined into 12^3 level-2 patches (dx = 1/81): 7552 patches,
+    5.5M points. One global dt = cfl * (finest dx)."""
+    if boxes is None:
+        c0 = n_side // 2
+        c1 = 3 * c0
+        boxes = [((c0 - 2,) * 3, (c0 + 2,) * 3), ((c1 - 2,) * 3, (c1 + 2,) * 3)]
+    level, ijk = refined_mesh((n_side,) * 3, boxes)
+    N = n_side * p
+    dx = 2.0 * half_width / N
+    h = level_spacing(dx, int(level.max()) + 1)
+    return MeshConfig("single_puncture", p, (n_side,) * 3, (-half_width,) * 3, dx, "sommerfeld",
+                      dict(PUNCTURE_PARAMS), cfl * h[-1], steps, None, dict(M=1.0), level, ijk)
+
+
 def initial_state(cfg):
     """(U, G) at t = 0 for a config; G (the Sommerfeld ghost shell) is empty
     for other boundary kinds. For Sommerfeld, G also serves as Q_ini."""
     ijk = cfg.ijk()
-    x, y, z = point_coords(cfg.p, ijk, cfg.origin, cfg.dx)
+    if isinstance(cfg, MeshConfig):
+        x, y, z = mesh_point_coords(cfg.p, cfg.level, ijk, cfg.origin, cfg.dx)
+    else:
+        x, y, z = point_coords(cfg.p, ijk, cfg.origin, cfg.dx)
     gx = gy = gz = None
     if cfg.bc == "sommerfeld":
         gx, gy, gz = ghost_positions(cfg.N, cfg.origin, cfg.dx)

@@ -1,0 +1,208 @@
+"""Parity of the CUDA path with the oracle on statically refined ratio-3
+meshes (appendix "refinement transition"): halo fill with coarse-to-fine
+interpolation (bit-exact), right-hand side with per-level spacing, RK4 steps
+with restriction, leaf-only constraint norms, mixed precision, and the
+three-level puncture workload at full size on sampled points."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import both_params, rel_err
+from paper_2406_11626_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+PUNC = dict(I.PUNCTURE_PARAMS)
+
+MESHES = {
+    "two": (6, (4, 4, 4), [((1, 1, 1), (3, 3, 3))]),
+    "three": (6, (4, 4, 4), [((1, 1, 1), (3, 3, 3)), ((5, 5, 5), (7, 7, 7))]),
+    "small_p": (3, (5, 4, 4), [((1, 1, 1), (4, 3, 3)), ((4, 4, 4), (6, 5, 5))]),
+    "p9": (9, (3, 3, 3), [((1, 1, 1), (2, 2, 2))]),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2406_11626_gb300 import ccz4
+    ccz4.lib()
+
+
+def mesh_pair(name, bc, dx=0.3, shuffle=0):
+    from paper_2406_11626_gb300 import ccz4 as C
+    p, np_, boxes = MESHES[name]
+    lev, ijk = I.refined_mesh(np_, boxes)
+    if shuffle:
+        perm = np.random.default_rng(shuffle).permutation(len(lev))
+        lev, ijk = lev[perm], ijk[perm]
+    origin = tuple(-0.5 * n * p * dx + o for n, o in zip(np_, (0.0, -0.013, 0.021)))
+    gg = C.Grid(p, np_, ijk, origin, dx, bc, level=lev)
+    og = O.Grid(p, np_, ijk, origin, dx, bc, level=lev)
+    return gg, og, lev, ijk, origin
+
+
+def mesh_state(gg, lev, ijk, origin, dx, bc, seed, base, amp=0.02):
+    p = gg.p
+    x, y, z = I.mesh_point_coords(p, lev, ijk, origin, dx)
+    box = gg.np[0] * p * dx
+    U0 = I.brill_lindquist(x, y, z) if base == "puncture" else I.flat(x.shape)
+    U = I.smooth_perturbation(x, y, z, seed, amp=amp, box=box, base=U0)
+    G = np.zeros((I.NV, 0))
+    if bc == "sommerfeld":
+        N = tuple(n * p for n in gg.np)
+        gx, gy, gz = I.ghost_positions(N, origin, dx)
+        G0 = I.brill_lindquist(gx, gy, gz) if base == "puncture" else I.flat(gx.shape)
+        G = I.smooth_perturbation(gx, gy, gz, seed, amp=amp, box=box, base=G0)
+    return np.ascontiguousarray(U), np.ascontiguousarray(G)
+
+
+@pytest.mark.parametrize("name,bc", [("two", "periodic"), ("two", "copy"), ("three", "sommerfeld"),
+                                     ("small_p", "periodic"), ("p9", "sommerfeld")])
+def test_mesh_halo_fill_is_bit_exact(name, bc):
+    """Same-level copies, level-0 boundary rules and the interpolated halo
+    of refined patches all equal the oracle bit for bit (the kernel rounds
+    every product and sum of the interpolation on its own, in the oracle's
+    order)."""
+    gg, og, lev, ijk, origin = mesh_pair(name, bc, shuffle=3)
+    rng = np.random.default_rng(1)
+    U = rng.standard_normal(og.ushape)
+    G = rng.standard_normal((I.NV, og.n_ghost))
+    gg.upload(U, G)
+    gg.fill_halos("U")
+    np.testing.assert_array_equal(gg.download("TILE"), og.fill_tiles(U, G))
+
+
+@pytest.mark.parametrize("name,bc,base", [("two", "periodic", "flat"), ("three", "sommerfeld", "puncture"),
+                                          ("small_p", "copy", "flat")])
+def test_mesh_rhs_matches_oracle(name, bc, base):
+    dx = 0.3
+    gg, og, lev, ijk, origin = mesh_pair(name, bc, dx=dx, shuffle=5)
+    U, G = mesh_state(gg, lev, ijk, origin, dx, bc, seed=4, base=base)
+    Gini = G * 0.999
+    cp, op = both_params(**dict(PUNC, ko_eps=0.3))
+    gg.upload(U, G)
+    if gg.n_ghost:
+        gg.upload(U, Gini, buf="INI")
+    gg.rhs(cp, "U", "RHS")
+    rU, rG = gg.download("RHS")
+    oU, oG = og.rhs(op, U, G, Gini)
+    assert rel_err(rU, oU).max() < TOL
+    assert rel_err(rG, oG).max() < TOL
+    assert np.abs(oU).max() > 1e-3
+
+
+def test_mesh_restriction_is_bit_exact():
+    gg, og, lev, ijk, origin = mesh_pair("three", "copy", shuffle=2)
+    U = np.random.default_rng(9).standard_normal(og.ushape)
+    gg.upload(U)
+    gg.restrict("U")
+    gU, _ = gg.download("U")
+    np.testing.assert_array_equal(gU, og.restrict(U))
+
+
+@pytest.mark.parametrize("name,bc", [("three", "sommerfeld"), ("two", "periodic")])
+def test_mesh_rk4_steps_match_oracle(name, bc):
+    """Three RK4 steps (halo interpolation at every stage, enforcement and
+    restriction after every step, one global dt from the finest level)."""
+    dx = 0.3
+    gg, og, lev, ijk, origin = mesh_pair(name, bc, dx=dx, shuffle=7)
+    U, G = mesh_state(gg, lev, ijk, origin, dx, bc, seed=6, base="puncture" if bc == "sommerfeld" else "flat",
+                      amp=0.01)
+    cp, op = both_params(**PUNC)
+    gg.upload(U, G)
+    if gg.n_ghost:
+        gg.upload(U, G, buf="INI")
+    dt = 0.1 * I.level_spacing(dx, og.n_levels)[-1]
+    gg.step(cp, dt, 3)
+    gU, gG = gg.download("U")
+    oU, oG = U, G
+    for _ in range(3):
+        oU, oG = og.rk4_step(op, dt, oU, oG, G)
+    assert rel_err(gU, oU).max() < TOL
+    assert rel_err(gG, oG).max() < TOL
+    # graph replay is bit-identical to the plain launches
+    gg.upload(U, G)
+    gg.step_graph(cp, dt, 3)
+    hU, hG = gg.download("U")
+    np.testing.assert_array_equal(hU, gU)
+    np.testing.assert_array_equal(hG, gG)
+
+
+def test_mesh_constraints_count_leaf_points_only():
+    import torch
+    dx = 0.3
+    gg, og, lev, ijk, origin = mesh_pair("three", "sommerfeld", dx=dx, shuffle=1)
+    U, G = mesh_state(gg, lev, ijk, origin, dx, "sommerfeld", seed=8, base="puncture")
+    gg.upload(U, G)
+    H = torch.zeros(gg.n_points, dtype=torch.float64, device="cuda")
+    M = torch.zeros(3 * gg.n_points, dtype=torch.float64, device="cuda")
+    out = gg.constraints("U", H.data_ptr(), M.data_ptr())
+    oH, oM, oout = og.constraints(U, G)
+    h = H.cpu().numpy()
+    m = M.cpu().numpy().reshape(3, -1)
+    assert np.abs(h - oH.ravel()).max() / max(np.abs(oH).max(), 1.0) < TOL
+    assert np.abs(m - oM.reshape(3, -1)).max() / max(np.abs(oM).max(), 1.0) < TOL
+    np.testing.assert_allclose(out[:4], oout[:4], rtol=1e-12)
+    assert gg.n_leaf_points < gg.n_points
+
+
+def test_mesh_mixed_precision_tracks_fp64():
+    """The mixed path on a mesh stays within the mixed tolerance of FP64."""
+    from paper_2406_11626_gb300 import ccz4 as C
+    dx = 0.3
+    out = []
+    for prec in ("fp64", "mixed"):
+        gg, og, lev, ijk, origin = mesh_pair("three", "sommerfeld", dx=dx)
+        U, G = mesh_state(gg, lev, ijk, origin, dx, "sommerfeld", seed=6, base="puncture", amp=0.01)
+        gg.upload(U, G)
+        gg.upload(U, G, buf="INI")
+        P = C.make_params(**PUNC, precision=prec)
+        gg.step(P, 0.1 * I.level_spacing(dx, 3)[-1], 3)
+        out.append(gg.download("U")[0])
+    assert rel_err(out[1], out[0]).max() < 1e-5
+
+
+def test_mesh_rejected_on_invalid_nesting():
+    from paper_2406_11626_gb300 import ccz4 as C
+    lev, ijk = I.refined_mesh((4, 4, 4), [((0, 1, 1), (2, 3, 3))])
+    with pytest.raises(C.CCZ4Error) as e:
+        C.Grid(6, (4, 4, 4), ijk, (0, 0, 0), 0.1, "copy", level=lev)
+    assert e.value.code == C.ERR_INVALID
+
+
+@pytest.mark.slow
+def test_three_level_puncture_full_size_sampled_parity():
+    """The three-level puncture workload (7552 patches of 9^3, levels at
+    dx = 1/9, 1/27, 1/81) in the launch configuration the benchmark times:
+    after one fused RK stage the accumulator holds k0; sampled points of
+    every level, including those whose stencils reach interpolated halos,
+    agree with the oracle evaluated point by point."""
+    from paper_2406_11626_gb300 import ccz4 as C
+    cfg = I.multilevel_puncture_config()
+    g = C.Grid.from_config(cfg)
+    og = O.Grid(cfg.p, cfg.np, cfg.ijk(), cfg.origin, cfg.dx, cfg.bc, level=cfg.level)
+    U, G = I.initial_state(cfg)
+    g.upload(U, G)
+    g.upload(U, G, buf="INI")
+    P = C.make_params(**cfg.params)
+    g.rk_stage(P, 0, cfg.dt)
+    acc, _ = g.download("ACC")
+    p3 = cfg.p ** 3
+    rng = np.random.default_rng(0)
+    pts = []
+    for l in range(3):
+        on = np.nonzero(np.repeat(cfg.level == l, p3))[0]
+        pts.append(rng.choice(on, 120, replace=False))
+        # points of boundary patches of the level (their stencils reach the interpolated halo)
+        sl = cfg.ijk()[cfg.level == l]
+        lo, hi = sl.min(axis=0), sl.max(axis=0)
+        edge = np.nonzero((cfg.level == l) & ((cfg.ijk() == lo) | (cfg.ijk() == hi)).any(axis=1))[0]
+        pts.append(rng.choice(edge, 8, replace=False) * p3 + rng.integers(0, p3, 8))
+    pts = np.concatenate(pts)
+    ref = og.rhs_points(O.make_params(**cfg.params), U, G, pts)
+    got = acc.reshape(I.NV, -1)[:, pts].T
+    scale = np.maximum(np.abs(ref).max(axis=0), 1.0)
+    assert (np.abs(got - ref) / scale).max() < TOL
