@@ -234,3 +234,106 @@ class Grid:
         if rc:
             raise IndexError("oracle: sample point out of range")
         return d1, d2, ko
+
+
+# ---------------------------------------------------------------------------
+# Bowen-York puncture initial data (bowen_york.h)
+# ---------------------------------------------------------------------------
+MAX_PUNCTURES = 4
+
+
+class Punctures(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_double * MAX_PUNCTURES),
+                ("c", (ctypes.c_double * 3) * MAX_PUNCTURES), ("P", (ctypes.c_double * 3) * MAX_PUNCTURES),
+                ("S", (ctypes.c_double * 3) * MAX_PUNCTURES)]
+
+
+def make_punctures(masses, centres, momenta=None, spins=None):
+    B = Punctures()
+    B.n = len(masses)
+    if not 1 <= B.n <= MAX_PUNCTURES:
+        raise ValueError("1..%d punctures" % MAX_PUNCTURES)
+    for k in range(B.n):
+        B.m[k] = float(masses[k])
+        for d in range(3):
+            B.c[k][d] = float(centres[k][d])
+            B.P[k][d] = float(momenta[k][d]) if momenta is not None else 0.0
+            B.S[k][d] = float(spins[k][d]) if spins is not None else 0.0
+    return B
+
+
+def _by_lib():
+    L = lib()
+    if not getattr(L, "_by_ready", False):
+        bp = ctypes.POINTER(Punctures)
+        L.og_by_points.argtypes = [bp, ctypes.c_long, _dbl_p, _dbl_p, _dbl_p, _dbl_p, _dbl_p, _dbl_p]
+        L.og_by_residual.restype = ctypes.c_double
+        L.og_by_residual.argtypes = [bp, ctypes.c_int, ctypes.c_double, _dbl_p, _dbl_p]
+        L.og_by_sweeps.argtypes = [bp, ctypes.c_int, ctypes.c_double, _dbl_p, ctypes.c_int]
+        L.og_by_solve.restype = ctypes.c_int
+        L.og_by_solve.argtypes = [bp, ctypes.c_int, ctypes.c_double, _dbl_p, ctypes.c_double, ctypes.c_int,
+                                  ctypes.c_int, _dbl_p]
+        L.og_by_interp.argtypes = [ctypes.c_int, ctypes.c_double, _dbl_p, ctypes.c_long, _dbl_p, _dbl_p, _dbl_p,
+                                   _dbl_p]
+        L.og_by_state.argtypes = [bp, ctypes.c_int, ctypes.c_double, _dbl_p, ctypes.c_long, _dbl_p, _dbl_p, _dbl_p,
+                                  _dbl_p]
+        L._by_ready = True
+    return L
+
+
+def by_points(B, x, y, z):
+    """(Abar[m, 6], Abar.Abar[m], psi_BL[m]) at the points."""
+    x, y, z = (np.ascontiguousarray(v, dtype=np.float64).ravel() for v in (x, y, z))
+    m = len(x)
+    A = np.empty((m, 6))
+    aa = np.empty(m)
+    psi = np.empty(m)
+    _by_lib().og_by_points(ctypes.byref(B), m, _d(x), _d(y), _d(z), _d(A), _d(aa), _d(psi))
+    return A, aa, psi
+
+
+def by_cell_coords(n, L):
+    """Cell centres of the initial-data grid, each (n, n, n) as [z][y][x]."""
+    c = -L + (np.arange(n) + 0.5) * (2.0 * L / n)
+    return (np.broadcast_to(c[None, None, :], (n, n, n)), np.broadcast_to(c[None, :, None], (n, n, n)),
+            np.broadcast_to(c[:, None, None], (n, n, n)))
+
+
+def by_residual(B, n, L, u):
+    u = _f64(u, (n, n, n))
+    res = np.empty((n, n, n))
+    mx = _by_lib().og_by_residual(ctypes.byref(B), int(n), float(L), _d(u), _d(res))
+    return res, mx
+
+
+def by_sweeps(B, n, L, u, n_sweeps):
+    u = _f64(u, (n, n, n)).copy()
+    _by_lib().og_by_sweeps(ctypes.byref(B), int(n), float(L), _d(u), int(n_sweeps))
+    return u
+
+
+def by_solve(B, n, L, u0=None, tol=1e-10, max_sweeps=1000000, check=10):
+    """Solves from u0 (default 0); returns (u, sweeps or -1, final residual)."""
+    u = np.zeros((n, n, n)) if u0 is None else _f64(u0, (n, n, n)).copy()
+    r = ctypes.c_double()
+    k = _by_lib().og_by_solve(ctypes.byref(B), int(n), float(L), _d(u), float(tol), int(max_sweeps), int(check),
+                              ctypes.byref(r))
+    return u, k, r.value
+
+
+def by_interp(n, L, u, x, y, z):
+    """Tricubic interpolation of the solver grid u at the points."""
+    u = _f64(u, (n, n, n))
+    x, y, z = (np.ascontiguousarray(v, dtype=np.float64).ravel() for v in (x, y, z))
+    out = np.empty(len(x))
+    _by_lib().og_by_interp(int(n), float(L), _d(u), len(x), _d(x), _d(y), _d(z), _d(out))
+    return out
+
+
+def by_state(B, n, L, u, x, y, z):
+    """The 25 CCZ4 fields (25, m) of the solved data at the points."""
+    u = _f64(u, (n, n, n))
+    x, y, z = (np.ascontiguousarray(v, dtype=np.float64).ravel() for v in (x, y, z))
+    Q = np.empty((NV, len(x)))
+    _by_lib().og_by_state(ctypes.byref(B), int(n), float(L), _d(u), len(x), _d(x), _d(y), _d(z), _d(Q))
+    return Q

@@ -1,0 +1,371 @@
+// Puncture initial data on the GPU (include/ccz4_id.h): Bowen-York
+// curvature and the Brill-Lindquist part of the conformal factor per cell,
+// and the red-black nonlinear Gauss-Seidel solve of the Hamiltonian
+// constraint for the regular correction u.
+//
+// A half-sweep updates the cells of one colour; their 7-point neighbours
+// all have the other colour, so the update order within a colour does not
+// matter and one thread per cell reproduces the serial sweep. The grid is
+// small (96^3 cells are 7 MB per field) and stays in L2 across sweeps, so a
+// sweep costs about two kernel launches; the solve replays a CUDA graph of
+// `check` sweeps between residual checks.
+#include <string.h>
+
+#include "../../include/ccz4_id.h"
+#include "ccz4_internal.cuh"
+
+struct ccz4_idsolver {
+  int n;
+  double L, h;
+  double *u, *aa, *psi;
+  double *partial;      // per-block maxima of the residual
+  int blocks;
+  double *dev_max;      // device [1]
+  double *host_max;     // pinned [1]
+  cudaStream_t cap;     // private stream for the graph capture
+  cudaGraphExec_t exec; // `exec_check` sweeps, or NULL
+  int exec_check;
+};
+
+namespace {
+
+constexpr int ID_THREADS = 256;
+
+struct PunctureSet {
+  int n;
+  double m[CCZ4_ID_MAX_PUNCTURES];
+  double c[CCZ4_ID_MAX_PUNCTURES][3];
+  double P[CCZ4_ID_MAX_PUNCTURES][3];
+  double S[CCZ4_ID_MAX_PUNCTURES][3];
+};
+
+__device__ __forceinline__ double cell_coord(double L, double h, int i) { return -L + (i + 0.5) * h; }
+
+__global__ void __launch_bounds__(ID_THREADS) setup_kernel(int n, double L, double h, PunctureSet B,
+                                                            double *aa, double *psi) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= (long long)n * n * n) return;
+  const int i = (int)(c % n), j = (int)((c / n) % n), k = (int)(c / ((long long)n * n));
+  const double X[3] = {cell_coord(L, h, i), cell_coord(L, h, j), cell_coord(L, h, k)};
+  double A[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+  double s = 1.0;
+  for (int p = 0; p < B.n; ++p) {
+    double d[3], nv[3];
+    for (int q = 0; q < 3; ++q) d[q] = X[q] - B.c[p][q];
+    const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int q = 0; q < 3; ++q) nv[q] = d[q] / r;
+    const double Pn = B.P[p][0] * nv[0] + B.P[p][1] * nv[1] + B.P[p][2] * nv[2];
+    // w = S x n: the spin term is 3/r^3 (w_i n_j + w_j n_i)
+    const double w[3] = {B.S[p][1] * nv[2] - B.S[p][2] * nv[1], B.S[p][2] * nv[0] - B.S[p][0] * nv[2],
+                         B.S[p][0] * nv[1] - B.S[p][1] * nv[0]};
+    const double cp = 1.5 / (r * r), cs = 3.0 / (r * r * r);
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const double dab = a == b ? 1.0 : 0.0;
+        A[a][b] += cp * (B.P[p][a] * nv[b] + B.P[p][b] * nv[a] - (dab - nv[a] * nv[b]) * Pn) +
+                   cs * (w[a] * nv[b] + w[b] * nv[a]);
+      }
+    s += B.m[p] / (2.0 * r);
+  }
+  double q = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) q += A[a][b] * A[a][b];
+  aa[c] = q;
+  psi[c] = s;
+}
+
+// Laplacian neighbours of cell (i, j, k) with the 1/r ghosts; returns the
+// neighbour sum and adds to *ghost_w the ghosts' weights r_cell / r_ghost.
+__device__ __forceinline__ double neighbour_sum(int n, double L, double h, const double *u, int i, int j, int k,
+                                                double uc, double *ghost_w) {
+  const long long c = ((long long)k * n + j) * n + i;
+  const int I[3] = {i, j, k};
+  const long long st[3] = {1, n, (long long)n * n};
+  double s = 0.0, gw = 0.0;
+  double rc = -1.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int side = -1; side <= 1; side += 2) {
+      const int o = I[d] + side;
+      if (o >= 0 && o < n) {
+        s += u[c + side * st[d]];
+      } else {
+        if (rc < 0.0) {
+          const double x = cell_coord(L, h, i), y = cell_coord(L, h, j), z = cell_coord(L, h, k);
+          rc = sqrt(x * x + y * y + z * z);
+        }
+        double g[3] = {cell_coord(L, h, i), cell_coord(L, h, j), cell_coord(L, h, k)};
+        g[d] = cell_coord(L, h, o);
+        const double w = rc / sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        s += uc * w;
+        gw += w;
+      }
+    }
+  *ghost_w = gw;
+  return s;
+}
+
+__global__ void __launch_bounds__(ID_THREADS) sweep_kernel(int n, double L, double h, double ih2, int color,
+                                                            const double *__restrict__ aa,
+                                                            const double *__restrict__ psi, double *u) {
+  const int half = (n + 1) / 2;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)half * n * n) return;
+  const int i2 = (int)(q % half), j = (int)((q / half) % n), k = (int)(q / ((long long)half * n));
+  const int i = 2 * i2 + ((j + k + color) & 1);
+  if (i >= n) return;
+  const long long c = ((long long)k * n + j) * n + i;
+  const double uc = u[c];
+  double gw;
+  const double s = neighbour_sum(n, L, h, u, i, j, k, uc, &gw);
+  const double a = __ldg(aa + c);
+  const double iq = 1.0 / (__ldg(psi + c) + uc);
+  const double iq2 = iq * iq, iq4 = iq2 * iq2;
+  const double F = (s - 6.0 * uc) * ih2 + 0.125 * a * (iq4 * iq2 * iq);
+  const double dF = (gw - 6.0) * ih2 - 0.875 * a * (iq4 * iq4);
+  u[c] = uc - F / dF;
+}
+
+__global__ void __launch_bounds__(ID_THREADS) residual_kernel(int n, double L, double h, double ih2,
+                                                               const double *__restrict__ aa,
+                                                               const double *__restrict__ psi,
+                                                               const double *__restrict__ u, double *res,
+                                                               double *partial) {
+  __shared__ double sh[ID_THREADS];
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (c < (long long)n * n * n) {
+    const int i = (int)(c % n), j = (int)((c / n) % n), k = (int)(c / ((long long)n * n));
+    const double uc = u[c];
+    double gw;
+    const double s = neighbour_sum(n, L, h, u, i, j, k, uc, &gw);
+    const double iq = 1.0 / (psi[c] + uc);
+    const double iq2 = iq * iq, iq4 = iq2 * iq2;
+    const double F = (s - 6.0 * uc) * ih2 + 0.125 * aa[c] * (iq4 * iq2 * iq);
+    if (res) res[c] = F;
+    v = fabs(F);
+    if (!(v == v)) v = INFINITY;  // a NaN residual never passes a tolerance
+  }
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = ID_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(ID_THREADS) max_kernel(const double *partial, int blocks, double *out) {
+  __shared__ double sh[ID_THREADS];
+  double v = 0.0;
+  for (int b = threadIdx.x; b < blocks; b += ID_THREADS) v = fmax(v, partial[b]);
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = ID_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+cudaError_t launch_sweeps(const ccz4_idsolver *s, int n_sweeps, cudaStream_t st) {
+  const int n = s->n;
+  const long long work = (long long)((n + 1) / 2) * n * n;
+  const unsigned grid = (unsigned)((work + ID_THREADS - 1) / ID_THREADS);
+  const double ih2 = 1.0 / (s->h * s->h);
+  for (int k = 0; k < n_sweeps; ++k)
+    for (int color = 0; color < 2; ++color) {
+      sweep_kernel<<<grid, ID_THREADS, 0, st>>>(n, s->L, s->h, ih2, color, s->aa, s->psi, s->u);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+using namespace ccz4;
+
+#define ID_TRY(call)                                                                       \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      set_error("%s failed: %s", #call, cudaGetErrorString(e_));                           \
+      return CCZ4_ERR_CUDA;                                                                \
+    }                                                                                      \
+  } while (0)
+
+static void id_release(ccz4_idsolver *s) {
+  if (s->exec) cudaGraphExecDestroy(s->exec);
+  if (s->cap) cudaStreamDestroy(s->cap);
+  cudaFree(s->u);
+  cudaFree(s->aa);
+  cudaFree(s->psi);
+  cudaFree(s->partial);
+  cudaFree(s->dev_max);
+  cudaFreeHost(s->host_max);
+  free(s);
+}
+
+extern "C" ccz4_status ccz4_id_create(int n, double L, ccz4_idsolver **out) {
+  if (!out || n < 2 || n > 1024 || !(L > 0.0)) {
+    set_error("id_create: need out, 2 <= n <= 1024 and L > 0 (n=%d L=%g)", n, L);
+    return CCZ4_ERR_INVALID;
+  }
+  *out = nullptr;
+  ccz4_idsolver *s = (ccz4_idsolver *)calloc(1, sizeof(ccz4_idsolver));
+  if (!s) {
+    set_error("host allocation failed");
+    return CCZ4_ERR_NOMEM;
+  }
+  s->n = n;
+  s->L = L;
+  s->h = 2.0 * L / n;
+  const size_t cells = (size_t)n * n * n;
+  s->blocks = (int)((cells + ID_THREADS - 1) / ID_THREADS);
+  bool ok = cudaMalloc(&s->u, sizeof(double) * cells) == cudaSuccess &&
+            cudaMalloc(&s->aa, sizeof(double) * cells) == cudaSuccess &&
+            cudaMalloc(&s->psi, sizeof(double) * cells) == cudaSuccess &&
+            cudaMalloc(&s->partial, sizeof(double) * (size_t)s->blocks) == cudaSuccess &&
+            cudaMalloc(&s->dev_max, sizeof(double)) == cudaSuccess &&
+            cudaMallocHost(&s->host_max, sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    set_error("id_create: device allocation failed: %s", cudaGetErrorString(cudaGetLastError()));
+    id_release(s);
+    return CCZ4_ERR_NOMEM;
+  }
+  cudaMemset(s->u, 0, sizeof(double) * cells);
+  cudaMemset(s->aa, 0, sizeof(double) * cells);
+  cudaMemset(s->psi, 0, sizeof(double) * cells);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    set_error("id_create: %s", cudaGetErrorString(e));
+    id_release(s);
+    return CCZ4_ERR_CUDA;
+  }
+  *out = s;
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_id_free(ccz4_idsolver *s) {
+  if (!s) return CCZ4_OK;
+  cudaDeviceSynchronize();
+  id_release(s);
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_id_set_punctures(ccz4_idsolver *s, const ccz4_punctures *B, void *stream) {
+  if (!s || !B || B->n < 1 || B->n > CCZ4_ID_MAX_PUNCTURES) {
+    set_error("id_set_punctures: need a solver and 1..%d punctures", CCZ4_ID_MAX_PUNCTURES);
+    return CCZ4_ERR_INVALID;
+  }
+  PunctureSet P;
+  memset(&P, 0, sizeof(P));
+  P.n = B->n;
+  for (int p = 0; p < B->n; ++p) {
+    P.m[p] = B->m[p];
+    for (int d = 0; d < 3; ++d) {
+      P.c[p][d] = B->c[p][d];
+      P.P[p][d] = B->P[p][d];
+      P.S[p][d] = B->S[p][d];
+    }
+  }
+  const long long cells = (long long)s->n * s->n * s->n;
+  setup_kernel<<<(unsigned)((cells + ID_THREADS - 1) / ID_THREADS), ID_THREADS, 0, (cudaStream_t)stream>>>(
+      s->n, s->L, s->h, P, s->aa, s->psi);
+  ID_TRY(cudaGetLastError());
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_id_u_ptr(ccz4_idsolver *s, double **dev_u) {
+  if (!s || !dev_u) {
+    set_error("id_u_ptr: NULL argument");
+    return CCZ4_ERR_INVALID;
+  }
+  *dev_u = s->u;
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_id_sweeps(ccz4_idsolver *s, int n_sweeps, void *stream) {
+  if (!s || n_sweeps < 0) {
+    set_error("id_sweeps: need a solver and n_sweeps >= 0");
+    return CCZ4_ERR_INVALID;
+  }
+  ID_TRY(launch_sweeps(s, n_sweeps, (cudaStream_t)stream));
+  return CCZ4_OK;
+}
+
+static ccz4_status residual(ccz4_idsolver *s, double *max_res, double *res_dev, cudaStream_t st) {
+  const double ih2 = 1.0 / (s->h * s->h);
+  residual_kernel<<<s->blocks, ID_THREADS, 0, st>>>(s->n, s->L, s->h, ih2, s->aa, s->psi, s->u, res_dev,
+                                                     s->partial);
+  ID_TRY(cudaGetLastError());
+  max_kernel<<<1, ID_THREADS, 0, st>>>(s->partial, s->blocks, s->dev_max);
+  ID_TRY(cudaGetLastError());
+  ID_TRY(cudaMemcpyAsync(s->host_max, s->dev_max, sizeof(double), cudaMemcpyDeviceToHost, st));
+  ID_TRY(cudaStreamSynchronize(st));
+  *max_res = *s->host_max;
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_id_residual(ccz4_idsolver *s, double *max_res, double *res_dev, void *stream) {
+  if (!s || !max_res) {
+    set_error("id_residual: NULL argument");
+    return CCZ4_ERR_INVALID;
+  }
+  return residual(s, max_res, res_dev, (cudaStream_t)stream);
+}
+
+static ccz4_status capture_sweeps(ccz4_idsolver *s, int check) {
+  if (s->exec) {
+    cudaGraphExecDestroy(s->exec);
+    s->exec = nullptr;
+  }
+  if (!s->cap) ID_TRY(cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  ID_TRY(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = launch_sweeps(s, check, s->cap);
+  cudaError_t e2 = cudaStreamEndCapture(s->cap, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    set_error("id_solve: sweep capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return CCZ4_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(&s->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    s->exec = nullptr;
+    set_error("id_solve: graph instantiation failed: %s", cudaGetErrorString(e));
+    return CCZ4_ERR_CUDA;
+  }
+  s->exec_check = check;
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_id_solve(ccz4_idsolver *s, double tol, int max_sweeps, int check, int *sweeps,
+                                     double *final_res, void *stream) {
+  if (!s || !(tol > 0.0) || max_sweeps < 0 || check < 1) {
+    set_error("id_solve: need a solver, tol > 0, max_sweeps >= 0 and check >= 1");
+    return CCZ4_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!s->exec || s->exec_check != check) {
+    ID_TRY(cudaStreamSynchronize(st));
+    ccz4_status r = capture_sweeps(s, check);
+    if (r != CCZ4_OK) return r;
+  }
+  double res = 0.0;
+  ccz4_status r = residual(s, &res, nullptr, st);
+  if (r != CCZ4_OK) return r;
+  int done = 0;
+  while (!(res < tol) && done < max_sweeps) {
+    ID_TRY(cudaGraphLaunch(s->exec, st));
+    done += check;
+    r = residual(s, &res, nullptr, st);
+    if (r != CCZ4_OK) return r;
+  }
+  if (sweeps) *sweeps = res < tol ? done : -1;
+  if (final_res) *final_res = res;
+  return CCZ4_OK;
+}

@@ -1,0 +1,127 @@
+"""Python binding of the puncture initial-data solve (include/ccz4_id.h):
+argument marshalling only; every step runs in the CUDA kernels of the
+library (no CPU fallback)."""
+import ctypes
+
+import numpy as np
+
+from .ccz4 import _check, _stream, lib as _lib
+
+MAX_PUNCTURES = 4
+
+
+class Punctures(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_double * MAX_PUNCTURES),
+                ("c", (ctypes.c_double * 3) * MAX_PUNCTURES), ("P", (ctypes.c_double * 3) * MAX_PUNCTURES),
+                ("S", (ctypes.c_double * 3) * MAX_PUNCTURES)]
+
+
+def make_punctures(masses, centres, momenta=None, spins=None):
+    B = Punctures()
+    B.n = len(masses)
+    for k in range(B.n):
+        B.m[k] = float(masses[k])
+        for d in range(3):
+            B.c[k][d] = float(centres[k][d])
+            B.P[k][d] = float(momenta[k][d]) if momenta is not None else 0.0
+            B.S[k][d] = float(spins[k][d]) if spins is not None else 0.0
+    return B
+
+
+def binary(m1, m2, d, P, S):
+    """Two punctures on the x axis at -d/2 (mass m1) and +d/2 (mass m2),
+    momenta (0, -P, 0) and (0, +P, 0) (a circular-orbit pattern), spins
+    (0, 0, S) each."""
+    return make_punctures([m1, m2], [(-0.5 * d, 0.0, 0.0), (0.5 * d, 0.0, 0.0)],
+                          [(0.0, -P, 0.0), (0.0, P, 0.0)], [(0.0, 0.0, S), (0.0, 0.0, S)])
+
+
+def _sig():
+    L = _lib()
+    if getattr(L, "_id_ready", False):
+        return L
+    vp = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    sigs = {
+        "ccz4_id_create": [ctypes.c_int, ctypes.c_double, ctypes.POINTER(vp)],
+        "ccz4_id_free": [vp],
+        "ccz4_id_set_punctures": [vp, ctypes.POINTER(Punctures), vp],
+        "ccz4_id_u_ptr": [vp, ctypes.POINTER(dp)],
+        "ccz4_id_sweeps": [vp, ctypes.c_int, vp],
+        "ccz4_id_residual": [vp, dp, dp, vp],
+        "ccz4_id_solve": [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, vp],
+    }
+    for name, args in sigs.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L._id_ready = True
+    return L
+
+
+class Solver:
+    """The Hamiltonian-constraint solve for u on n^3 cells of [-L, L]^3."""
+
+    def __init__(self, n, L):
+        self.n, self.L = int(n), float(L)
+        h = ctypes.c_void_p()
+        _check(_sig().ccz4_id_create(self.n, self.L, ctypes.byref(h)))
+        self._h = h
+        p = ctypes.POINTER(ctypes.c_double)()
+        _check(_sig().ccz4_id_u_ptr(h, ctypes.byref(p)))
+        self.u_ptr = ctypes.cast(p, ctypes.c_void_p).value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _sig().ccz4_id_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def u_tensor(self):
+        """u as a torch tensor view of the device buffer ([n][n][n], x fastest)."""
+        import torch
+        from .ccz4 import _wrap_device
+        return _wrap_device(self.u_ptr, (self.n,) * 3, torch.float64)
+
+    def set_punctures(self, B, stream=None):
+        _check(_sig().ccz4_id_set_punctures(self._h, ctypes.byref(B), _stream(stream)))
+
+    def set_u(self, u, stream=None):
+        self.u_tensor().copy_(_as_tensor(u).reshape((self.n,) * 3))
+
+    def get_u(self):
+        return self.u_tensor().cpu().numpy().copy()
+
+    def sweeps(self, k, stream=None):
+        _check(_sig().ccz4_id_sweeps(self._h, int(k), _stream(stream)))
+
+    def residual(self, stream=None, cells=False):
+        r = ctypes.c_double()
+        res = None
+        if cells:
+            import torch
+            res = torch.empty((self.n,) * 3, dtype=torch.float64, device="cuda")
+            ptr = ctypes.cast(ctypes.c_void_p(res.data_ptr()), ctypes.POINTER(ctypes.c_double))
+        else:
+            ptr = None
+        _check(_sig().ccz4_id_residual(self._h, ctypes.byref(r), ptr, _stream(stream)))
+        return (r.value, res.cpu().numpy()) if cells else r.value
+
+    def solve(self, tol=1e-10, max_sweeps=1000000, check=50, stream=None):
+        """Sweeps from the current u; returns (sweeps or -1, final residual)."""
+        k, r = ctypes.c_int(), ctypes.c_double()
+        _check(_sig().ccz4_id_solve(self._h, float(tol), int(max_sweeps), int(check), ctypes.byref(k),
+                                    ctypes.byref(r), _stream(stream)))
+        return k.value, r.value
+
+
+def _as_tensor(a):
+    import torch
+    if isinstance(a, torch.Tensor):
+        return a.to(device="cuda", dtype=torch.float64)
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")

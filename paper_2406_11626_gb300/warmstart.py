@@ -1,0 +1,216 @@
+"""Learned warm start of the puncture initial-data solve.
+
+Binding of include/ccz4_mlp.h (argument marshalling only: the network's
+forward pass, back-propagation, Adam, feature assembly and the hand-over of
+its output to the solver run in the library's CUDA kernels) and the
+orchestration of the experiment:
+
+1. draws: a scrambled Sobol sequence (seed 0) over the binary parameters
+   m1, m2 in [0.3, 0.7], d in [2, 12], P in [0, 0.2], S in [0, 0.3];
+2. data: the plain relaxation solve (initial_data.Solver, from u = 0, to a
+   max residual of 1e-10) of every training draw on n^3 cells of
+   [-L, L]^3, kept on the device in FP32;
+3. training: Adam on the mean squared error of the scaled correction at
+   cells drawn uniformly (host-seeded) from the stored solutions;
+4. evaluation: on held-out draws, sweeps to the same tolerance from the
+   network's guess against sweeps from u = 0. The plain solve stays the
+   judge: a guess is only a starting point, and a solve that does not reach
+   the tolerance reports -1.
+"""
+import ctypes
+import time
+
+import numpy as np
+
+from .ccz4 import _check, _stream, _wrap_device, lib as _lib
+from . import initial_data as ID
+
+N_FEATURES = 8
+U_SCALE = 10.0
+RANGES = ((0.3, 0.7), (0.3, 0.7), (2.0, 12.0), (0.0, 0.2), (0.0, 0.3))  # m1, m2, d, P, S
+
+
+def _sig():
+    L = _lib()
+    if getattr(L, "_mlp_ready", False):
+        return L
+    vp = ctypes.c_void_p
+    fp = ctypes.POINTER(ctypes.c_float)
+    ll = ctypes.POINTER(ctypes.c_longlong)
+    sigs = {
+        "ccz4_mlp_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)],
+        "ccz4_mlp_free": [vp],
+        "ccz4_mlp_params": [vp, ctypes.POINTER(fp), ll],
+        "ccz4_mlp_grads": [vp, ctypes.POINTER(fp), ll],
+        "ccz4_mlp_forward": [vp, vp, ctypes.c_int, vp, vp],
+        "ccz4_mlp_loss_grad": [vp, vp, vp, ctypes.c_int, vp, vp],
+        "ccz4_mlp_adam": [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, vp],
+        "ccz4_mlp_features_grid": [ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double), vp, vp],
+        "ccz4_mlp_features_sample": [ctypes.c_int, ctypes.c_double, vp, vp, vp, ctypes.c_int, vp, vp, vp],
+        "ccz4_mlp_output_to_u": [vp, ctypes.c_longlong, vp, vp],
+    }
+    for name, args in sigs.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L._mlp_ready = True
+    return L
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def init_params(n_in=8, width=128, depth=4, seed=0):
+    """Layer-wise uniform initialisation, bound 1/sqrt(fan_in), in the flat
+    layout of the network (FP32)."""
+    rng = np.random.default_rng(seed)
+    dims = [n_in] + [width] * depth + [1]
+    out = []
+    for l in range(depth + 1):
+        bound = 1.0 / np.sqrt(dims[l])
+        out.append(rng.uniform(-bound, bound, dims[l + 1] * dims[l]))
+        out.append(rng.uniform(-bound, bound, dims[l + 1]))
+    return np.concatenate(out).astype(np.float32)
+
+
+class MLP:
+    """The perceptron on the current CUDA device (FP32)."""
+
+    def __init__(self, n_in=8, width=128, depth=4, max_batch=65536):
+        self.n_in, self.width, self.depth, self.max_batch = n_in, width, depth, max_batch
+        h = ctypes.c_void_p()
+        _check(_sig().ccz4_mlp_create(n_in, width, depth, max_batch, ctypes.byref(h)))
+        self._h = h
+        import torch
+        p, n = ctypes.POINTER(ctypes.c_float)(), ctypes.c_longlong()
+        _check(_sig().ccz4_mlp_params(h, ctypes.byref(p), ctypes.byref(n)))
+        self.n_params = n.value
+        self.theta = _wrap_device(ctypes.cast(p, ctypes.c_void_p).value, (n.value,), torch.float32)
+        _check(_sig().ccz4_mlp_grads(h, ctypes.byref(p), ctypes.byref(n)))
+        self.grad = _wrap_device(ctypes.cast(p, ctypes.c_void_p).value, (n.value,), torch.float32)
+        self._loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _sig().ccz4_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        import torch
+        self.theta.copy_(torch.as_tensor(np.asarray(theta, dtype=np.float32), device="cuda"))
+
+    def forward(self, x, stream=None):
+        """y (batch,) for x (batch, n_in) float32 on the device."""
+        import torch
+        B = x.shape[0]
+        y = torch.empty(B, dtype=torch.float32, device="cuda")
+        for r0 in range(0, B, self.max_batch):
+            r1 = min(B, r0 + self.max_batch)
+            _check(_sig().ccz4_mlp_forward(self._h, _p(x[r0:r1]), r1 - r0, _p(y[r0:r1]), _stream(stream)))
+        return y
+
+    def loss_grad(self, x, t, stream=None):
+        """Loss (device scalar tensor); the gradient lands in self.grad."""
+        _check(_sig().ccz4_mlp_loss_grad(self._h, _p(x), _p(t), x.shape[0], _p(self._loss), _stream(stream)))
+        return self._loss
+
+    def adam(self, lr, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+        _check(_sig().ccz4_mlp_adam(self._h, lr, b1, b2, eps, _stream(stream)))
+
+
+def features_grid(n, L, p5, stream=None):
+    import torch
+    x = torch.empty((n ** 3, N_FEATURES), dtype=torch.float32, device="cuda")
+    arr = (ctypes.c_double * 5)(*[float(v) for v in p5])
+    _check(_sig().ccz4_mlp_features_grid(n, float(L), arr, _p(x), _stream(stream)))
+    return x
+
+
+def features_sample(n, L, p5, u_store, idx, stream=None):
+    """x (B, 8) and t (B,) for flat indices idx = solution * n^3 + cell."""
+    import torch
+    B = idx.shape[0]
+    x = torch.empty((B, N_FEATURES), dtype=torch.float32, device="cuda")
+    t = torch.empty(B, dtype=torch.float32, device="cuda")
+    _check(_sig().ccz4_mlp_features_sample(n, float(L), _p(p5), _p(u_store), _p(idx), B, _p(x), _p(t),
+                                           _stream(stream)))
+    return x, t
+
+
+def output_to_u(y, u_ptr, stream=None):
+    _check(_sig().ccz4_mlp_output_to_u(_p(y), y.shape[0], ctypes.c_void_p(u_ptr), _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# the experiment
+# ---------------------------------------------------------------------------
+def sobol_draws(count, seed=0):
+    """count x 5 parameter draws (m1, m2, d, P, S) from a scrambled Sobol sequence."""
+    import torch
+    eng = torch.quasirandom.SobolEngine(dimension=5, scramble=True, seed=seed)
+    q = eng.draw(count).double().numpy()
+    lo = np.array([r[0] for r in RANGES])
+    hi = np.array([r[1] for r in RANGES])
+    return lo + q * (hi - lo)
+
+
+def solve_draws(draws, n, L, tol=1e-10, check=100, max_sweeps=2000000, keep=True):
+    """Plain solves from u = 0; returns (u_store (len, n^3) float32 or None, sweeps, seconds)."""
+    import torch
+    s = ID.Solver(n, L)
+    store = torch.empty((len(draws), n ** 3), dtype=torch.float32, device="cuda") if keep else None
+    sweeps = []
+    t0 = time.perf_counter()
+    for k, d in enumerate(draws):
+        s.set_punctures(ID.binary(*d))
+        s.u_tensor().zero_()
+        it, _ = s.solve(tol=tol, check=check, max_sweeps=max_sweeps)
+        sweeps.append(it)
+        if keep:
+            store[k] = s.u_tensor().reshape(-1).float()
+    torch.cuda.synchronize()
+    return store, np.array(sweeps), time.perf_counter() - t0
+
+
+def train(mlp, u_store, draws, n, L, steps, batch=16384, lr=1e-3, seed=1, log_every=0):
+    """Adam on uniformly drawn (solution, cell) rows; returns the loss history."""
+    import torch
+    rng = np.random.default_rng(seed)
+    p5 = torch.as_tensor(np.asarray(draws, dtype=np.float32), device="cuda").contiguous()
+    n3 = n ** 3
+    hist = []
+    for k in range(steps):
+        idx = torch.as_tensor(rng.integers(0, len(draws) * n3, batch, dtype=np.int64), device="cuda")
+        x, t = features_sample(n, L, p5, u_store, idx)
+        loss = mlp.loss_grad(x, t)
+        mlp.adam(lr)
+        if log_every and (k % log_every == 0 or k == steps - 1):
+            hist.append((k, float(loss.item())))
+    return hist
+
+
+def evaluate(mlp, draws, n, L, tol=1e-10, check=100, max_sweeps=2000000):
+    """Per held-out draw: (sweeps from u = 0, sweeps from the network's guess,
+    max |guess - solution| / max |solution|)."""
+    import torch
+    s = ID.Solver(n, L)
+    out = []
+    for d in draws:
+        s.set_punctures(ID.binary(*d))
+        s.u_tensor().zero_()
+        k0, _ = s.solve(tol=tol, check=check, max_sweeps=max_sweeps)
+        sol = s.u_tensor().clone()
+        y = mlp.forward(features_grid(n, L, d))
+        output_to_u(y, s.u_ptr)
+        guess = s.u_tensor().clone()
+        k1, _ = s.solve(tol=tol, check=check, max_sweeps=max_sweeps)
+        err = float((guess - sol).abs().max() / sol.abs().max())
+        out.append((k0, k1, err))
+    return np.array(out)
