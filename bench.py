@@ -53,7 +53,7 @@ def parse_args():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--workload", default="puncture144", choices=["puncture144", "puncture3level", "mid", "small"],
+    ap.add_argument("--workload", default="puncture144", choices=["puncture144", "puncture3level", "binary", "mid", "small"],
                     help="the same physics on fewer points, for profiler captures: mid = 90^3 (10^3 patches), small = 54^3 (6^3 patches)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     return ap.parse_args()
@@ -120,7 +120,9 @@ def oracle_sample_config(workload="puncture144"):
     three-level workload, those 4^3 level-0 patches with the central 2^3
     refined once and one level-1 patch refined again (307 patches)."""
     from paper_2406_11626_gb300 import inputs as I
-    if workload == "puncture3level":
+    if workload in ("puncture3level", "binary"):
+        # the binary uses the same multi-level sample: the oracle's rate per
+        # point-stage does not depend on the data
         return I.multilevel_puncture_config(n_side=4, half_width=2.0,
                                             boxes=[((1, 1, 1), (3, 3, 3)), ((4, 4, 4), (5, 5, 5))])
     return I.single_puncture_config(n_side=4, half_width=2.0)
@@ -189,6 +191,12 @@ def workload_config(g, precision="fp64", K=None, workload="puncture144"):
     elif workload == "mid":
         cfg = I.single_puncture_config(n_side=10, half_width=5.0)
         name = "single puncture M=1, [-5,5]^3, 10^3 patches of 9^3 (90^3 points), profiling case"
+    elif workload == "binary":
+        cfg = I.binary_puncture_config()
+        name = ("rotating binary puncture: bare masses 0.487 at x = -3, +3, momenta (0, -+0.0934, 0), no spin, "
+                "Bowen-York data (u by the plain relaxation solve on 192^3 cells of [-32,32]^3 to residual "
+                "1e-10); [-32,32]^3 on 4 ratio-3 levels of 9^3 patches (4096/5832/3456/6912, dx 4/9 .. 4/243); "
+                "1+log, Gamma-driver f=0.75 eta=1, KO 0.1, Sommerfeld, RK4 dt=0.1 dx_finest")
     elif workload == "puncture3level":
         cfg = I.multilevel_puncture_config()
         name = ("single puncture M=1 on 3 static ratio-3 levels: [-8,8]^3 as 16^3 patches of 9^3 (dx 1/9), "
@@ -245,7 +253,29 @@ def bench_config(args):
         return I.single_puncture_config(n_side=10, half_width=5.0)
     if args.workload == "puncture3level":
         return I.multilevel_puncture_config()
+    if args.workload == "binary":
+        return I.binary_puncture_config()
     return I.single_puncture_config()
+
+
+_ID_CACHE = {}
+
+
+def init_state(C, I, cfg, g):
+    """Initial state into U and INI: closed-form data uploaded from the host,
+    or, for the binary, the state assembled on the device from the
+    initial-data solve (solved once per process, outside any timed region)."""
+    if cfg.name == "binary_puncture":
+        from paper_2406_11626_gb300 import initial_data as ID
+        if "binary" not in _ID_CACHE:
+            _ID_CACHE["binary"] = ID.solve_config(cfg)
+        s, B, _ = _ID_CACHE["binary"]
+        s.assemble(B, g, "U")
+        s.assemble(B, g, "INI")
+        return
+    U0, G0 = I.initial_state(cfg)
+    g.upload(U0, G0)
+    g.upload(U0, G0, buf="INI")
 
 
 def time_path(C, I, cfg, precision, K, W, stream, dist, clocks_index=None):
@@ -253,15 +283,13 @@ def time_path(C, I, cfg, precision, K, W, stream, dist, clocks_index=None):
     the time of the K steps and the per-stage kernel times (ms)."""
     import torch
     g = C.Grid.from_config(cfg)
-    U0, G0 = I.initial_state(cfg)
-    g.upload(U0, G0)
-    g.upload(U0, G0, buf="INI")
+    init_state(C, I, cfg, g)
     P = C.make_params(**cfg.params, precision=precision)
     bufs = [C.stage_buffers(s) for s in range(4)]
 
     def step(ev=None):
         for s in range(4):
-            g.fill_halos(bufs[s][0], stream)
+            g.fill_halos(bufs[s][0], stream, P)
             if ev is not None:
                 ev[s][0].record(stream)
             g.rk_stage(P, s, cfg.dt, stream, fill=False)
@@ -358,6 +386,7 @@ def run_gb300(args):
                  "dtype": "f64 state/differences/1-over-phi terms/update + f32 algebra",
                  "max_rel_state_error_vs_fp64": float(err.max()),
                  "worst_field": I.FIELDS[int(err.argmax())],
+                 "rel_state_error_per_field": {f: float(e) for f, e in zip(I.FIELDS, err)},
                  "after_steps": K + args.warmup,
                  "L2_H": cmx[0], "L2_H_fp64": c64[0], "L2_M": cmx[1], "L2_M_fp64": c64[1],
                  "roofline_frac": t_roof_mx / t_stage_mx,

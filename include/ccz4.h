@@ -159,6 +159,17 @@ ccz4_status ccz4_download(ccz4_grid *g, int buf, double *U, double *G, void *str
    first-derivative stencils) into CCZ4_BUF_MIX. */
 ccz4_status ccz4_fill_halos(ccz4_grid *g, int buf, void *stream);
 
+/* The halo fill as the stage kernel for parameters P needs it: the same
+   tiles; for P->precision == CCZ4_PREC_MIXED, the mixed derivatives that
+   the mixed stage kernel uses in FP32 -- those of g~ and beta -- take their
+   differences in FP64 and their weights in FP32 and are stored as FP32 in
+   the first 27 x n_points floats of CCZ4_BUF_MIX (g~'s 18 slots, then
+   beta's 9), while those of alpha and phi stay FP64 in their slots;
+   otherwise the buffers equal ccz4_fill_halos'. A mixed-precision
+   ccz4_rk_stage must follow this fill (ccz4_rhs, ccz4_step and
+   ccz4_step_graph fill this way). */
+ccz4_status ccz4_fill_halos_for(ccz4_grid *g, int buf, const ccz4_params *P, void *stream);
+
 /* Right-hand side d_t Q of the second-order CCZ4 system (appendix
    "Spacetime foliation", Eqs. NR_foccz4_gamma_ij ... NR_foccz4_b^i, closed
    by the listed relations and Eq. NR_foccz4_modified_ricci) plus the
@@ -330,6 +341,15 @@ ccz4_status ccz4_restrict(ccz4_grid *g, int buf, void *stream);
    weight zero repeat a used index), then the remainders rx | ry << 2 |
    rz << 4. */
 ccz4_status ccz4_mesh_plan(const ccz4_mesh_desc *desc, long long *n_interp, int *src, int *interp);
+
+/* Launch of the fused stage kernel (a tuning choice; results are
+   identical): CCZ4_LAUNCH_FLAT (default), one warp per 32 consecutive
+   interior points of all levels; CCZ4_LAUNCH_QUEUE, a persistent launch
+   sized to the resident blocks whose warps take 32-point items from a
+   device work counter (reset by a memset node before each stage) until the
+   points of every level are done. Drops a captured step graph. */
+enum { CCZ4_LAUNCH_FLAT = 0, CCZ4_LAUNCH_QUEUE = 1 };
+ccz4_status ccz4_set_launch(ccz4_grid *g, int mode);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *ccz4_last_error(void);

@@ -19,7 +19,10 @@
  * from the 1/r fall-off rule u_ghost = u_cell * r_cell / r_ghost (r from the
  * origin). Solver: red-black nonlinear Gauss-Seidel, one Newton step per
  * cell (red = i+j+k even first; the derivative includes the boundary
- * ghosts' dependence on their cell). Residual: max over the cells of
+ * ghosts' dependence on their cell), optionally over-relaxed. The
+ * residual F is evaluated in FP64; the reciprocals of the update are an
+ * FP32 estimate refined by two Newton-Raphson steps in FP64 (within a few
+ * ulps of a division). Residual: max over the cells of
  * |Lap_h u + 1/8 AA (psi_BL + u)^-7|. The grid u is [n][n][n], x fastest.
  *
  * The CCZ4 state of the data (phi = psi^-2, A~_ij = psi^-6 Abar_ij,
@@ -62,6 +65,11 @@ ccz4_status ccz4_id_set_punctures(ccz4_idsolver *s, const ccz4_punctures *B, voi
    initial guess there, read the solution from there. */
 ccz4_status ccz4_id_u_ptr(ccz4_idsolver *s, double **dev_u);
 
+/* Relaxation factor omega of the point update u <- u - omega F / F'
+   (1, the default: plain Newton-Gauss-Seidel; 1 < omega < 2: successive
+   over-relaxation, far fewer sweeps). 0 < omega < 2, else CCZ4_ERR_INVALID. */
+ccz4_status ccz4_id_set_relaxation(ccz4_idsolver *s, double omega);
+
 /* n_sweeps red-black sweeps (two launches each). */
 ccz4_status ccz4_id_sweeps(ccz4_idsolver *s, int n_sweeps, void *stream);
 
@@ -76,6 +84,18 @@ ccz4_status ccz4_id_residual(ccz4_idsolver *s, double *max_res, double *res_dev,
    Synchronises. */
 ccz4_status ccz4_id_solve(ccz4_idsolver *s, double tol, int max_sweeps, int check, int *sweeps,
                           double *final_res, void *stream);
+
+/* Writes the CCZ4 state of the data at every interior point (all levels of
+   a mesh) and every Sommerfeld ghost cell of grid g into its state buffer
+   `buf`: g~ = delta; alpha = ((1 - s)/(1 + s) + 1)/2 with
+   s = sum m_n/(2 r_n), the averaged lapse of the paper's binary setup;
+   beta = b = 0; phi = psi^-2 with psi = psi_BL + u, u interpolated from the
+   solver grid by tricubic Lagrange interpolation (along each axis the four
+   cell centres around the point, shifted inwards at the faces; x, then y,
+   then z); A~_ij = psi^-6 Abar_ij; K = Theta = 0; Gamma-hat = 0. Points of g
+   should lie inside [-L, L]^3 (outside, the outermost stencil
+   extrapolates). Asynchronous. */
+ccz4_status ccz4_id_assemble(ccz4_idsolver *s, const ccz4_punctures *B, ccz4_grid *g, int buf, void *stream);
 
 #ifdef __cplusplus
 }

@@ -269,10 +269,10 @@ def _by_lib():
         L.og_by_points.argtypes = [bp, ctypes.c_long, _dbl_p, _dbl_p, _dbl_p, _dbl_p, _dbl_p, _dbl_p]
         L.og_by_residual.restype = ctypes.c_double
         L.og_by_residual.argtypes = [bp, ctypes.c_int, ctypes.c_double, _dbl_p, _dbl_p]
-        L.og_by_sweeps.argtypes = [bp, ctypes.c_int, ctypes.c_double, _dbl_p, ctypes.c_int]
+        L.og_by_sweeps.argtypes = [bp, ctypes.c_int, ctypes.c_double, _dbl_p, ctypes.c_int, ctypes.c_double]
         L.og_by_solve.restype = ctypes.c_int
         L.og_by_solve.argtypes = [bp, ctypes.c_int, ctypes.c_double, _dbl_p, ctypes.c_double, ctypes.c_int,
-                                  ctypes.c_int, _dbl_p]
+                                  ctypes.c_int, ctypes.c_double, _dbl_p]
         L.og_by_interp.argtypes = [ctypes.c_int, ctypes.c_double, _dbl_p, ctypes.c_long, _dbl_p, _dbl_p, _dbl_p,
                                    _dbl_p]
         L.og_by_state.argtypes = [bp, ctypes.c_int, ctypes.c_double, _dbl_p, ctypes.c_long, _dbl_p, _dbl_p, _dbl_p,
@@ -306,18 +306,18 @@ def by_residual(B, n, L, u):
     return res, mx
 
 
-def by_sweeps(B, n, L, u, n_sweeps):
+def by_sweeps(B, n, L, u, n_sweeps, omega=1.0):
     u = _f64(u, (n, n, n)).copy()
-    _by_lib().og_by_sweeps(ctypes.byref(B), int(n), float(L), _d(u), int(n_sweeps))
+    _by_lib().og_by_sweeps(ctypes.byref(B), int(n), float(L), _d(u), int(n_sweeps), float(omega))
     return u
 
 
-def by_solve(B, n, L, u0=None, tol=1e-10, max_sweeps=1000000, check=10):
+def by_solve(B, n, L, u0=None, tol=1e-10, max_sweeps=1000000, check=10, omega=1.0):
     """Solves from u0 (default 0); returns (u, sweeps or -1, final residual)."""
     u = np.zeros((n, n, n)) if u0 is None else _f64(u0, (n, n, n)).copy()
     r = ctypes.c_double()
     k = _by_lib().og_by_solve(ctypes.byref(B), int(n), float(L), _d(u), float(tol), int(max_sweeps), int(check),
-                              ctypes.byref(r))
+                              float(omega), ctypes.byref(r))
     return u, k, r.value
 
 

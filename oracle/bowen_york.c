@@ -135,7 +135,7 @@ double og_by_residual(const og_punctures *B, int n, double L, const double *u, d
   return mx;
 }
 
-static void sweeps(const grid_t *g, double *u, int n_sweeps) {
+static void sweeps(const grid_t *g, double *u, int n_sweeps, double omega) {
   int n = g->n;
   double ih2 = 1.0 / (g->h * g->h);
   for (int s = 0; s < n_sweeps; ++s)
@@ -163,26 +163,26 @@ static void sweeps(const grid_t *g, double *u, int n_sweeps) {
               }
             }
             double dF = diag * ih2 - 0.875 * g->aa[c] * pow(q, -8.0);
-            u[c] = u[c] - F / dF;
+            u[c] = u[c] - omega * (F / dF);
           }
 }
 
-void og_by_sweeps(const og_punctures *B, int n, double L, double *u, int n_sweeps) {
+void og_by_sweeps(const og_punctures *B, int n, double L, double *u, int n_sweeps, double omega) {
   grid_t g;
   grid_init(&g, B, n, L);
-  sweeps(&g, u, n_sweeps);
+  sweeps(&g, u, n_sweeps, omega);
   grid_free(&g);
 }
 
 int og_by_solve(const og_punctures *B, int n, double L, double *u, double tol, int max_sweeps, int check,
-                double *final_res) {
+                double omega, double *final_res) {
   grid_t g;
   grid_init(&g, B, n, L);
   if (check < 1) check = 1;
   int done = 0;
   double r = og_by_residual(B, n, L, u, NULL);
   while (r >= tol && done < max_sweeps) {
-    sweeps(&g, u, check);
+    sweeps(&g, u, check, omega);
     done += check;
     r = og_by_residual(B, n, L, u, NULL);
   }

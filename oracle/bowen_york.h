@@ -60,13 +60,15 @@ void og_by_points(const og_punctures *B, long m, const double *x, const double *
 
 /* Residual of the discrete equation at every cell; returns max |res|. */
 double og_by_residual(const og_punctures *B, int n, double L, const double *u, double *res);
-/* n_sweeps red-black Newton-Gauss-Seidel sweeps (red: i+j+k even, first). */
-void og_by_sweeps(const og_punctures *B, int n, double L, double *u, int n_sweeps);
+/* n_sweeps red-black Newton-Gauss-Seidel sweeps (red: i+j+k even, first),
+   each point update scaled by the relaxation factor omega (1: plain
+   Gauss-Seidel; 1 < omega < 2: successive over-relaxation). */
+void og_by_sweeps(const og_punctures *B, int n, double L, double *u, int n_sweeps, double omega);
 /* Sweeps until the max residual is below tol, checked every `check`
    sweeps; returns the number of sweeps done (or -1 if max_sweeps is hit).
    *final_res receives the last residual. */
 int og_by_solve(const og_punctures *B, int n, double L, double *u, double tol, int max_sweeps, int check,
-                double *final_res);
+                double omega, double *final_res);
 
 /* Tricubic Lagrange interpolation of u (n^3 cells of [-L, L]^3) at m
    points: along each axis the four cell centres around the point (the

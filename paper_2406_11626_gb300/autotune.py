@@ -1,15 +1,18 @@
-"""Autotuner for the patch edge p.
+"""Autotuner for the patch edge p and the launch of the stage kernel.
 
-The cost of a step depends on the patch edge: the halo'd tile of a patch
-holds (p+6)^3 points for p^3 interior ones (8x at p = 6, 4.6x at p = 9,
-3.4x at p = 12, 2.6x at p = 17), so small patches move more halo data,
+The cost of a step depends on the patch edge and on how the stage kernel
+is launched. The halo'd tile of a patch holds (p+6)^3 points for p^3
+interior ones (8x at p = 6, 4.6x at p = 9, 3.4x at p = 12, 2.6x at
+p = 17), so small patches move more halo data,
 while large ones fill the GPU with fewer, larger halo-fill blocks (one per
-patch, with up to 218 KB of shared memory at p = 18). The tuner times one
-RK4 step (captured as a CUDA graph, the way a production loop runs it) for
-every candidate p on the same physics at about the same number of points,
-and keeps the fastest by point-stages per second. Results are cached as JSON,
-keyed by the GPU, the library build and the workload, so a production run
-pays for the sweep once.
+patch, with up to 218 KB of shared memory at p = 18); the stage kernel
+runs either as a flat grid (one thread per point) or as a persistent
+launch whose warps take 32-point items from a device work queue. The tuner
+times one RK4 step (captured as a CUDA graph, the way a production loop
+runs it) for every candidate (p, launch) on the same physics at about the
+same number of points, and keeps the fastest by point-stages per second.
+Results are cached as JSON, keyed by the GPU, the library build and the
+workload, so a production run pays for the sweep once.
 
 Inputs are the closed-form puncture data of ``inputs`` (deterministic); the
 timing uses CUDA events on the current stream.
@@ -24,6 +27,7 @@ from . import inputs as I
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ccz4_gb300", "autotune.json")
 # the patch edges of the paper's patch-size study, plus the largest edge the fill kernel takes
 CANDIDATES = (6, 9, 12, 17, 18)
+LAUNCHES = ("flat", "queue")
 
 
 def layouts(n_target, candidates=CANDIDATES, max_p=18):
@@ -51,7 +55,7 @@ def _gpu_name():
     return torch.cuda.get_device_name(torch.cuda.current_device())
 
 
-def time_layout(p, n_side, h, precision="fp64", steps=3, warmup=2):
+def time_layout(p, n_side, h, precision="fp64", steps=3, warmup=2, launch="flat"):
     """Seconds per RK4 step of the single-puncture physics on n_side^3
     patches of p^3 with spacing h (graph replay, CUDA events)."""
     import torch
@@ -59,6 +63,7 @@ def time_layout(p, n_side, h, precision="fp64", steps=3, warmup=2):
     half = 0.5 * n_side * p * h
     cfg = I.single_puncture_config(p=p, n_side=n_side, half_width=half)
     g = C.Grid.from_config(cfg)
+    g.set_launch(launch)
     U, G = I.initial_state(cfg)
     g.upload(U, G)
     g.upload(U, G, buf="INI")
@@ -78,17 +83,19 @@ def time_layout(p, n_side, h, precision="fp64", steps=3, warmup=2):
 
 
 def tune(n_target=144, h=1.0 / 9.0, precision="fp64", candidates=CANDIDATES, steps=3, warmup=2,
-         cache=DEFAULT_CACHE, timer=None, key_extra=None, refresh=False):
-    """Chooses the patch edge for a uniform grid of about n_target^3 points
-    at spacing h. Returns {"p", "n_side", "results": {p: {...}}, "key"}.
+         cache=DEFAULT_CACHE, timer=None, key_extra=None, refresh=False, launches=LAUNCHES):
+    """Chooses the patch edge and the launch of the stage kernel for a
+    uniform grid of about n_target^3 points at spacing h. Returns {"p",
+    "n_side", "launch", "results": {"p/launch": {...}}, "key"}.
 
-    timer(p, n_side, h, precision, steps, warmup) -> (seconds per step,
-    points) may replace the GPU timing (tests use a fake one); key_extra
-    replaces the GPU/library part of the cache key."""
+    timer(p, n_side, h, precision, steps, warmup, launch) -> (seconds per
+    step, points) may replace the GPU timing (tests use a fake one);
+    key_extra replaces the GPU/library part of the cache key."""
     if timer is None:
         timer = time_layout
         key_extra = key_extra or "%s|%s" % (_gpu_name(), _lib_hash())
-    key = "%s|n=%d|h=%.17g|%s|%s" % (key_extra, n_target, h, precision, ",".join(map(str, candidates)))
+    key = "%s|n=%d|h=%.17g|%s|%s|%s" % (key_extra, n_target, h, precision, ",".join(map(str, candidates)),
+                                         ",".join(launches))
     store = {}
     if cache and os.path.exists(cache):
         with open(cache) as f:
@@ -97,12 +104,13 @@ def tune(n_target=144, h=1.0 / 9.0, precision="fp64", candidates=CANDIDATES, ste
             return store[key]
     results = {}
     for p, n_side in layouts(n_target, candidates):
-        sec, n_points = timer(p, n_side, h, precision, steps, warmup)
-        results[str(p)] = {"n_side": n_side, "points": n_points, "s_per_step": sec,
-                           "point_stages_per_s": 4.0 * n_points / sec}
+        for launch in launches:
+            sec, n_points = timer(p, n_side, h, precision, steps, warmup, launch)
+            results["%d/%s" % (p, launch)] = {"p": p, "launch": launch, "n_side": n_side, "points": n_points,
+                                              "s_per_step": sec, "point_stages_per_s": 4.0 * n_points / sec}
     best = max(results, key=lambda q: results[q]["point_stages_per_s"])
-    entry = {"p": int(best), "n_side": results[best]["n_side"], "results": results, "key": key,
-             "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
+    entry = {"p": results[best]["p"], "launch": results[best]["launch"], "n_side": results[best]["n_side"],
+             "results": results, "key": key, "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
     if cache:
         os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
         store[key] = entry

@@ -74,6 +74,7 @@ def lib():
         "ccz4_upload": [vp, ctypes.c_int, _dbl_p, _dbl_p, vp],
         "ccz4_download": [vp, ctypes.c_int, _dbl_p, _dbl_p, vp],
         "ccz4_fill_halos": [vp, ctypes.c_int, vp],
+        "ccz4_fill_halos_for": [vp, ctypes.c_int, ctypes.POINTER(Params), vp],
         "ccz4_rhs": [vp, ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int, vp],
         "ccz4_rk_stage": [vp, ctypes.POINTER(Params), ctypes.c_int, ctypes.c_double, vp],
         "ccz4_stage_buffers": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
@@ -86,6 +87,7 @@ def lib():
         "ccz4_alloc_mesh": [ctypes.POINTER(MeshDesc), ctypes.POINTER(vp)],
         "ccz4_mesh_info": [vp, ctypes.POINTER(ctypes.c_int), ll_p],
         "ccz4_restrict": [vp, ctypes.c_int, vp],
+        "ccz4_set_launch": [vp, ctypes.c_int],
         "ccz4_mesh_plan": [ctypes.POINTER(MeshDesc), ll_p, ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_int)],
     }
@@ -247,6 +249,10 @@ class Grid:
     def from_config(cls, cfg):
         return cls(cfg.p, cfg.np, cfg.ijk(), cfg.origin, cfg.dx, cfg.bc, level=getattr(cfg, "level", None))
 
+    def set_launch(self, mode):
+        """'flat' (default) or 'queue' launch of the stage kernel."""
+        _check(lib().ccz4_set_launch(self._h, {"flat": 0, "queue": 1}[mode] if isinstance(mode, str) else int(mode)))
+
     def restrict(self, buf="U", stream=None):
         """Coarse points under refined patches <- mean of their 27 fine cells."""
         _check(lib().ccz4_restrict(self._h, _buf(buf), _stream(stream)))
@@ -298,8 +304,13 @@ class Grid:
         return _wrap_device(ptr, (n,), torch.float64)
 
     # -- the hot path -----------------------------------------------------------
-    def fill_halos(self, buf="U", stream=None):
-        _check(lib().ccz4_fill_halos(self._h, _buf(buf), _stream(stream)))
+    def fill_halos(self, buf="U", stream=None, P=None):
+        """Halo fill of a state buffer; with parameters P, as the stage kernel
+        for P needs it (FP32 weights of the mixed derivatives in the mixed path)."""
+        if P is None:
+            _check(lib().ccz4_fill_halos(self._h, _buf(buf), _stream(stream)))
+        else:
+            _check(lib().ccz4_fill_halos_for(self._h, _buf(buf), ctypes.byref(P), _stream(stream)))
 
     def rhs(self, P, in_buf="U", out_buf="RHS", stream=None):
         _check(lib().ccz4_rhs(self._h, ctypes.byref(P), _buf(in_buf), _buf(out_buf), _stream(stream)))
@@ -307,7 +318,7 @@ class Grid:
     def rk_stage(self, P, stage, dt, stream=None, fill=True):
         """RK4 stage s; with fill=True the halo of the stage input is filled first."""
         if fill:
-            self.fill_halos(stage_buffers(stage)[0], stream)
+            self.fill_halos(stage_buffers(stage)[0], stream, P)
         _check(lib().ccz4_rk_stage(self._h, ctypes.byref(P), int(stage), float(dt), _stream(stream)))
 
     def step(self, P, dt, n_steps=1, stream=None):

@@ -107,6 +107,8 @@ struct Nbhd {
   int st[3];                       // distance between neighbours along x, y, z
   const double *__restrict__ mix;  // mixed second derivatives of this point, slot 0
   long long ms;                    // distance between slots
+  const float *__restrict__ mixf;  // mixed path: those of g~ and beta in FP32 (mix_fslot order)
+  long long msf;                   // distance between FP32 slots
   __host__ __device__ __forceinline__ double at(int v, int off) const {
 #ifdef __CUDA_ARCH__
     return __ldg(c + v * fs + off);
@@ -119,6 +121,13 @@ struct Nbhd {
     return __ldg(mix + slot * ms);
 #else
     return mix[slot * ms];
+#endif
+  }
+  __host__ __device__ __forceinline__ float mixedf(int fslot) const {
+#ifdef __CUDA_ARCH__
+    return __ldg(mixf + fslot * msf);
+#else
+    return mixf[fslot * msf];
 #endif
   }
 };
@@ -234,11 +243,19 @@ __host__ __device__ __forceinline__ void second_ko(const Nbhd &N, int v, const S
   dd[0] = d2[0];
   dd[3] = d2[1];
   dd[5] = d2[2];
-  // the mixed derivatives come from the halo fill (CCZ4_BUF_MIX)
+  // the mixed derivatives come from the halo fill (CCZ4_BUF_MIX); the
+  // mixed path's fill stores those it uses in FP32 as FP32
   const int m = mix_slot(v);
-  dd[1] = cvt<O>(D(N.mixed(m)));
-  dd[2] = cvt<O>(D(N.mixed(m + 1)));
-  dd[4] = cvt<O>(D(N.mixed(m + 2)));
+  if constexpr (std::is_same<O, float>::value) {
+    const int fm = mix_fslot(m);
+    dd[1] = N.mixedf(fm);
+    dd[2] = N.mixedf(fm + 1);
+    dd[4] = N.mixedf(fm + 2);
+  } else {
+    dd[1] = cvt<O>(D(N.mixed(m)));
+    dd[2] = cvt<O>(D(N.mixed(m + 1)));
+    dd[4] = cvt<O>(D(N.mixed(m + 2)));
+  }
 }
 
 // Parameters of the equations, combined on the host and stored in the

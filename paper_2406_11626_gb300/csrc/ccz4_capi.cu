@@ -92,6 +92,7 @@ static void free_all(ccz4_grid *g) {
     cudaFree(g->d_rpar[l]);
     cudaFree(g->d_rkid[l]);
   }
+  cudaFree(g->d_queue);
   free(g);
 }
 
@@ -398,6 +399,17 @@ extern "C" ccz4_status ccz4_fill_halos(ccz4_grid *g, int buf, void *stream) {
   return CCZ4_OK;
 }
 
+extern "C" ccz4_status ccz4_fill_halos_for(ccz4_grid *g, int buf, const ccz4_params *P, void *stream) {
+  if (check_grid(g) || check_params(P)) return CCZ4_ERR_INVALID;
+  if (!state_buffer(buf) || !g->buf[buf]) {
+    set_error("fill_halos_for: buffer %d is not a state buffer of this grid", buf);
+    return CCZ4_ERR_INVALID;
+  }
+  CUDA_TRY(launch_fill_halos(g->v, g->buf[buf], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], (cudaStream_t)stream,
+                             P->precision == CCZ4_PREC_MIXED));
+  return CCZ4_OK;
+}
+
 static const double *ini_ptr(ccz4_grid *g) {
   return g->buf[CCZ4_BUF_INI] ? g->buf[CCZ4_BUF_INI] : g->buf[CCZ4_BUF_U];
 }
@@ -410,7 +422,8 @@ extern "C" ccz4_status ccz4_rhs(ccz4_grid *g, const ccz4_params *P, int in_buf, 
     return CCZ4_ERR_INVALID;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  CUDA_TRY(launch_fill_halos(g->v, g->buf[in_buf], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], s));
+  CUDA_TRY(launch_fill_halos(g->v, g->buf[in_buf], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], s,
+                             P->precision == CCZ4_PREC_MIXED));
   CUDA_TRY(launch_rhs(g->v, *P, g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], g->buf[in_buf], ini_ptr(g), g->buf[out_buf], s));
   return CCZ4_OK;
 }
@@ -432,6 +445,27 @@ static ccz4_status stage_kernel(ccz4_grid *g, const ccz4_params *P, int stage, d
   CUDA_TRY(launch_rk_stage(g->v, *P, stage, dt, g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], in, ini_ptr(g), g->buf[CCZ4_BUF_U],
                            g->buf[CCZ4_BUF_ACC], g->buf[kStageOut[stage]], s));
   if (stage == 3 && g->v.n_levels > 1) return restrict_levels(g, g->buf[kStageOut[stage]], s);
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_set_launch(ccz4_grid *g, int mode) {
+  if (check_grid(g)) return CCZ4_ERR_INVALID;
+  if (mode != CCZ4_LAUNCH_FLAT && mode != CCZ4_LAUNCH_QUEUE) {
+    set_error("set_launch: unknown launch mode %d", mode);
+    return CCZ4_ERR_INVALID;
+  }
+  if (mode == CCZ4_LAUNCH_QUEUE && !g->d_queue) {
+    if (cudaMalloc(&g->d_queue, sizeof(unsigned long long)) != cudaSuccess) {
+      set_error("set_launch: allocation of the work counter failed: %s", cudaGetErrorString(cudaGetLastError()));
+      return CCZ4_ERR_NOMEM;
+    }
+  }
+  unsigned long long *q = mode == CCZ4_LAUNCH_QUEUE ? g->d_queue : nullptr;
+  if (q != g->v.queue && g->step_exec) {
+    cudaGraphExecDestroy(g->step_exec);  // the captured step used the other launch
+    g->step_exec = nullptr;
+  }
+  g->v.queue = q;
   return CCZ4_OK;
 }
 
@@ -472,7 +506,8 @@ extern "C" ccz4_status ccz4_step(ccz4_grid *g, const ccz4_params *P, double dt, 
   cudaStream_t s = (cudaStream_t)stream;
   for (int n = 0; n < n_steps; ++n)
     for (int st = 0; st < 4; ++st) {
-      CUDA_TRY(launch_fill_halos(g->v, g->buf[kStageIn[st]], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], s));
+      CUDA_TRY(launch_fill_halos(g->v, g->buf[kStageIn[st]], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], s,
+                                 P->precision == CCZ4_PREC_MIXED));
       ccz4_status r = stage_kernel(g, P, st, dt, s);
       if (r != CCZ4_OK) return r;
     }
@@ -492,7 +527,8 @@ static ccz4_status capture_step(ccz4_grid *g, const ccz4_params *P, double dt) {
   CUDA_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
   ccz4_status st = CCZ4_OK;
   for (int s = 0; s < 4 && st == CCZ4_OK; ++s) {
-    cudaError_t e = launch_fill_halos(g->v, g->buf[kStageIn[s]], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], g->cap_stream);
+    cudaError_t e = launch_fill_halos(g->v, g->buf[kStageIn[s]], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX],
+                                      g->cap_stream, P->precision == CCZ4_PREC_MIXED);
     if (e != cudaSuccess) {
       set_error("capture: halo fill launch failed: %s", cudaGetErrorString(e));
       st = CCZ4_ERR_CUDA;

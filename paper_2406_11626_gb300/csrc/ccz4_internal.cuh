@@ -45,6 +45,15 @@ struct InterpEntry {
   int t;
 };
 
+// The mixed path keeps the mixed derivatives it uses in FP32 -- those of
+// g~ (slots 0..17) and beta (slots 21..29) -- as FP32 in the first 27 float
+// slots of the mixed-derivative buffer: FP32 slot of slot s, or -1 for the
+// FP64-only slots of alpha and phi.
+__host__ __device__ __forceinline__ constexpr int mix_fslot(int s) {
+  return s < 18 ? s : (s >= 21 && s < 30 ? s - 3 : -1);
+}
+constexpr int NMIXF = 27;
+
 // Plain-data view of a grid, passed by value to every kernel.
 struct GridView {
   int p, T;                    // points per patch edge; tile edge p + 2*HALO
@@ -69,6 +78,7 @@ struct GridView {
   const int *plev;             // [n_patches] level of each patch
   const unsigned char *leaf;   // [n_patches] 1 if the patch has no children
   double ldx[MAX_LEVELS];      // spacing of each level (ldx[0] = dx)
+  unsigned long long *queue;   // work counter of the queue launch of the stage kernel, or nullptr (flat)
 };
 
 // Level of patch n (0 on a single level).
@@ -160,11 +170,14 @@ struct ccz4_grid {
   unsigned char *d_leaf;
   int *d_rpar[CCZ4_MAX_LEVELS], *d_rkid[CCZ4_MAX_LEVELS];
   int n_rpar[CCZ4_MAX_LEVELS];
+  unsigned long long *d_queue;  // work counter of the queue launch (allocated on first use)
 };
 
 // Kernel launchers (one translation unit each).
 namespace ccz4 {
-cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile, double *mix, cudaStream_t s);
+// fp32_weights: mixed derivatives with FP32 weights (for the mixed-precision stage kernel)
+cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile, double *mix, cudaStream_t s,
+                              bool fp32_weights = false);
 cudaError_t prepare_fill_halos(int p);
 // number of mixed second derivatives kept per point (d_xy, d_xz, d_yz of g~, alpha, beta, phi)
 constexpr int NMIX = 33;

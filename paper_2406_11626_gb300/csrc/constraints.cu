@@ -223,6 +223,8 @@ __global__ void __launch_bounds__(RED_THREADS) constraints_kernel(GridView g, Co
     N.st[2] = T * T;
     N.mix = nullptr;
     N.ms = 0;
+    N.mixf = nullptr;
+    N.msf = 0;
     double h, m[3];
     constraints_point(N, LC.C[patch_level(g, n)], h, m);
     if (H) H[i] = h;

@@ -83,6 +83,8 @@ extern "C" ccz4_status ccz4_flops_per_point_stage(const ccz4_params *P, double o
   Nbhd N;
   N.mix = mixbuf.data();
   N.ms = 1;
+  N.mixf = nullptr;  // the counting types read the FP64 slots
+  N.msf = 0;
   N.c = buf.data() + (3 * W * W + 3 * W + 3);
   N.fs = W * W * W;
   N.st[0] = 1;

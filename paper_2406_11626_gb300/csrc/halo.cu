@@ -15,6 +15,7 @@
 // costs about half the FP64 operations of evaluating each point's 16-point
 // tensor-product stencil on its own. The result is the same FD4 mixed
 // derivative (the tensor product of two first-derivative stencils).
+#include "ccz4_algebra.cuh"
 #include "ccz4_internal.cuh"
 
 namespace ccz4 {
@@ -22,11 +23,39 @@ namespace {
 
 constexpr int FILL_THREADS = 256;
 constexpr int GATHER_BATCH = 8;
+constexpr size_t FILL_SMEM_LIMIT = 227 * 1024;  // dynamic shared memory one block may use
 
-// Scale of the mixed derivatives, 1 / (144 dx^2), per level.
+// Whether the d_z pass of the mixed derivatives fits on the region widened
+// along both x and y (one pass for d_x d_z and d_y d_z).
+__host__ __device__ constexpr bool fill_wide(int p) {
+  return sizeof(double) * ((size_t)(p + 6) * (p + 6) * (p + 6) + (size_t)(p + 4) * (p + 4) * p) +
+             sizeof(int) * (size_t)(p + 6) * (p + 6) * (p + 6) <=
+         FILL_SMEM_LIMIT;
+}
+
+// Scale of the mixed derivatives, 1 / (144 dx^2), per level (and rounded
+// to FP32 for the FP32 weights of the mixed path).
 struct LevelScale {
   double cmix[MAX_LEVELS];
+  float cmixf[MAX_LEVELS];
 };
+
+// Second stage of a mixed derivative: d_a of the first derivatives e[] at
+// stride s, stored to mixed-derivative slot `slot` of this patch's point q.
+// FP64 weights and an FP64 slot; or, for the fields whose mixed derivatives
+// the mixed path's stage kernel uses in FP32 (g~ and beta, f32 set), the
+// differences in FP64, the weights in FP32 (the split the stage kernel
+// applies to its own stencils) and an FP32 slot (half the traffic).
+__device__ __forceinline__ void mixed_out(const double *e, int s, double cmix, float cmixf, bool f32, double *mix,
+                                          long long n_points, long long pbase, int slot, int q) {
+  const double d1 = e[s] - e[-s], d2 = e[2 * s] - e[-2 * s];
+  if (f32) {
+    float *mf = reinterpret_cast<float *>(mix) + (long long)mix_fslot(slot) * n_points + pbase;
+    __stcs(mf + q, fmaf(8.0f, d2f_bits(d1), -d2f_bits(d2)) * cmixf);
+  } else {
+    __stcs(mix + (long long)slot * n_points + pbase + q, fma(8.0, d1, -d2) * cmix);
+  }
+}
 
 // Linear-interpolation weights between coarse cell centres for remainder
 // r = (i - 1) mod 3 of fine index i: the rows (1), (2/3, 1/3), (1/3, 2/3)
@@ -58,8 +87,9 @@ __device__ __forceinline__ double interp_value(const InterpEntry *__restrict__ e
 }
 
 // MESH: the tile sources come from the host-built table of a refined mesh
-// (and may be interpolations); otherwise they are resolved here.
-template <bool MESH>
+// (and may be interpolations); otherwise they are resolved here. F32W: FP32
+// weights for the mixed derivatives (see mixed_out).
+template <bool MESH, bool F32W>
 __global__ void __launch_bounds__(FILL_THREADS, 4) fill_halos_kernel(GridView g, const double *__restrict__ src,
                                                                   double *__restrict__ tile,
                                                                   double *__restrict__ mix, LevelScale ls) {
@@ -69,9 +99,10 @@ __global__ void __launch_bounds__(FILL_THREADS, 4) fill_halos_kernel(GridView g,
   const int T3 = (int)g.T3;
   const int pe = p + 4;             // patch edge widened by two points on each side
   const int next = pe * p * p;      // widened region of one first-derivative pass
+  const bool wide = fill_wide(p);   // room for the region widened along two axes
   double *ts = smem;                // [T3] tile of the current field
-  double *ext = smem + T3;          // [next] first derivatives on the widened region
-  int *idx = (int *)(ext + next);   // [T3] source index of each tile point
+  double *ext = smem + T3;          // [next or pe^2 p] first derivatives on the widened region
+  int *idx = (int *)(ext + (wide ? pe * pe * p : next));  // [T3] source index of each tile point
   const int bx = __ldg(g.ijk + 3 * n) * p - HALO;
   const int by = __ldg(g.ijk + 3 * n + 1) * p - HALO;
   const int bz = __ldg(g.ijk + 3 * n + 2) * p - HALO;
@@ -87,6 +118,7 @@ __global__ void __launch_bounds__(FILL_THREADS, 4) fill_halos_kernel(GridView g,
     }
   }
   const double cmix = MESH ? ls.cmix[patch_level(g, n)] : ls.cmix[0];
+  const float cmixf = MESH ? ls.cmixf[patch_level(g, n)] : ls.cmixf[0];
   __syncthreads();
   const long long p3 = (long long)p * p * p;
   const long long pbase = (long long)n * p3;
@@ -125,11 +157,15 @@ __global__ void __launch_bounds__(FILL_THREADS, 4) fill_halos_kernel(GridView g,
       }
     }
     if (slot < 0) continue;  // uniform across the block
+    const bool f32 = F32W && mix_fslot(slot) >= 0;
     __syncthreads();
-    // pass 0: d_y on the region widened along x, then d_x of it -> d_x d_y
-    // pass 1: d_z widened along x -> d_x d_z ; pass 2: d_z widened along y -> d_y d_z
+    // pass 0: d_y on the region widened along x, then d_x of it -> d_x d_y.
+    // wide: d_z once on the region widened along x and y (corners skipped),
+    // then d_x and d_y of it -> d_x d_z, d_y d_z; otherwise (the block does
+    // not fit in shared memory) pass 1: d_z widened along x -> d_x d_z and
+    // pass 2: d_z widened along y -> d_y d_z. Both give the same values.
 #pragma unroll 1
-    for (int pass = 0; pass < 3; ++pass) {
+    for (int pass = 0; pass < (wide ? 1 : 3); ++pass) {
       const int si = pass == 0 ? T : T * T;  // stride of the inner derivative in the tile
       for (int e = threadIdx.x; e < next; e += blockDim.x) {
         const int a = e % pe - 2, b = (e / pe) % p, c = e / (pe * p);
@@ -139,43 +175,71 @@ __global__ void __launch_bounds__(FILL_THREADS, 4) fill_halos_kernel(GridView g,
         ext[e] = fma(8.0, ts[c0 + si] - ts[c0 - si], -(ts[c0 + 2 * si] - ts[c0 - 2 * si]));
       }
       __syncthreads();
-      double *mv = mix + (long long)(slot + pass) * g.n_points + pbase;
       for (int q = threadIdx.x; q < p3; q += blockDim.x) {
         const int x = q % p, y = (q / p) % p, z = q / (p * p);
         const int a = pass == 2 ? y : x, b = pass == 2 ? x : y;
         const int e = (z * p + b) * pe + (a + 2);
-        __stcs(mv + q, fma(8.0, ext[e + 1] - ext[e - 1], -(ext[e + 2] - ext[e - 2])) * cmix);
+        mixed_out(ext + e, 1, cmix, cmixf, f32, mix, g.n_points, pbase, slot + pass, q);
       }
       __syncthreads();
     }
+    if (!wide) continue;
+    const int T2 = T * T;
+    for (int e = threadIdx.x; e < pe * pe * p; e += blockDim.x) {
+      const int a = e % pe - 2, b = (e / pe) % pe - 2, c = e / (pe * pe);
+      if ((a < 0 || a >= p) && (b < 0 || b >= p)) continue;  // corner: not needed
+      const int c0 = ((c + HALO) * T + (b + HALO)) * T + (a + HALO);
+      ext[e] = fma(8.0, ts[c0 + T2] - ts[c0 - T2], -(ts[c0 + 2 * T2] - ts[c0 - 2 * T2]));
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < p3; q += blockDim.x) {
+      const int x = q % p, y = (q / p) % p, z = q / (p * p);
+      const int e = (z * pe + (y + 2)) * pe + (x + 2);
+      mixed_out(ext + e, 1, cmix, cmixf, f32, mix, g.n_points, pbase, slot + 1, q);
+      mixed_out(ext + e, pe, cmix, cmixf, f32, mix, g.n_points, pbase, slot + 2, q);
+    }
+    __syncthreads();
   }
 }
 
 }  // namespace
 
 size_t fill_smem_bytes(int p) {
-  const size_t T = (size_t)p + 2 * HALO;
-  return sizeof(double) * (T * T * T + (size_t)(p + 4) * p * p) + sizeof(int) * T * T * T;
+  const size_t T = (size_t)p + 2 * HALO, pe = (size_t)p + 4;
+  return sizeof(double) * (T * T * T + (fill_wide(p) ? pe * pe * p : pe * p * p)) + sizeof(int) * T * T * T;
 }
 
 // Raises the kernel's dynamic shared-memory limit for patch edge p (once per
 // grid, outside any stream capture).
 cudaError_t prepare_fill_halos(int p) {
   const int bytes = (int)fill_smem_bytes(MAX_P > p ? MAX_P : p);
-  cudaError_t e = cudaFuncSetAttribute(fill_halos_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fill_halos_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const void *kernels[4] = {(const void *)fill_halos_kernel<false, false>, (const void *)fill_halos_kernel<false, true>,
+                            (const void *)fill_halos_kernel<true, false>, (const void *)fill_halos_kernel<true, true>};
+  for (const void *k : kernels) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
-cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile, double *mix, cudaStream_t s) {
+cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile, double *mix, cudaStream_t s,
+                              bool fp32_weights) {
   if (g.n_patches == 0) return cudaSuccess;
   const size_t bytes = fill_smem_bytes(g.p);
   LevelScale ls;
-  for (int l = 0; l < MAX_LEVELS; ++l) ls.cmix[l] = 1.0 / (144.0 * g.ldx[l] * g.ldx[l]);
-  if (g.src)
-    fill_halos_kernel<true><<<g.n_patches, FILL_THREADS, bytes, s>>>(g, src, tile, mix, ls);
+  for (int l = 0; l < MAX_LEVELS; ++l) {
+    ls.cmix[l] = 1.0 / (144.0 * g.ldx[l] * g.ldx[l]);
+    ls.cmixf[l] = (float)ls.cmix[l];
+  }
+  const dim3 grid(g.n_patches), block(FILL_THREADS);
+  if (g.src && fp32_weights)
+    fill_halos_kernel<true, true><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
+  else if (g.src)
+    fill_halos_kernel<true, false><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
+  else if (fp32_weights)
+    fill_halos_kernel<false, true><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
   else
-    fill_halos_kernel<false><<<g.n_patches, FILL_THREADS, bytes, s>>>(g, src, tile, mix, ls);
+    fill_halos_kernel<false, false><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
   return cudaGetLastError();
 }
 

@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include "../../include/ccz4_id.h"
+#include "ccz4_algebra.cuh"
 #include "ccz4_internal.cuh"
 
 struct ccz4_idsolver {
@@ -25,6 +26,7 @@ struct ccz4_idsolver {
   cudaStream_t cap;     // private stream for the graph capture
   cudaGraphExec_t exec; // `exec_check` sweeps, or NULL
   int exec_check;
+  double omega;         // relaxation factor
 };
 
 namespace {
@@ -40,6 +42,16 @@ struct PunctureSet {
 };
 
 __device__ __forceinline__ double cell_coord(double L, double h, int i) { return -L + (i + 0.5) * h; }
+
+// 1/d for positive or negative normal d of moderate size: an FP32
+// reciprocal (conversions by integer bit operations) refined by two
+// Newton-Raphson steps r <- r + r (1 - d r) in FP64, i.e. four FMAs on the
+// narrow FP64 pipe instead of a division; the result is within a few ulps.
+__device__ __forceinline__ double recip(double d) {
+  double r = ccz4::f2d_bits(__frcp_rn(ccz4::d2f_bits(d)));
+  r = fma(r, fma(-d, r, 1.0), r);
+  return fma(r, fma(-d, r, 1.0), r);
+}
 
 __global__ void __launch_bounds__(ID_THREADS) setup_kernel(int n, double L, double h, PunctureSet B,
                                                             double *aa, double *psi) {
@@ -74,28 +86,26 @@ __global__ void __launch_bounds__(ID_THREADS) setup_kernel(int n, double L, doub
   psi[c] = s;
 }
 
-// Laplacian neighbours of cell (i, j, k) with the 1/r ghosts; returns the
-// neighbour sum and adds to *ghost_w the ghosts' weights r_cell / r_ghost.
-__device__ __forceinline__ double neighbour_sum(int n, double L, double h, const double *u, int i, int j, int k,
-                                                double uc, double *ghost_w) {
+// Laplacian neighbour sum of a cell on the boundary of the grid, where
+// one or more neighbours are 1/r ghosts; adds the ghosts' weights
+// r_cell / r_ghost to *ghost_w. Kept out of line so that the interior cells
+// (94 % of a 96^3 grid) do not pay for its coordinates, roots and
+// divisions.
+__device__ __noinline__ double boundary_sum(int n, double L, double h, const double *u, int i, int j, int k,
+                                            double uc, double *ghost_w) {
   const long long c = ((long long)k * n + j) * n + i;
   const int I[3] = {i, j, k};
   const long long st[3] = {1, n, (long long)n * n};
+  const double X[3] = {cell_coord(L, h, i), cell_coord(L, h, j), cell_coord(L, h, k)};
+  const double rc = sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
   double s = 0.0, gw = 0.0;
-  double rc = -1.0;
-#pragma unroll
   for (int d = 0; d < 3; ++d)
-#pragma unroll
     for (int side = -1; side <= 1; side += 2) {
       const int o = I[d] + side;
       if (o >= 0 && o < n) {
         s += u[c + side * st[d]];
       } else {
-        if (rc < 0.0) {
-          const double x = cell_coord(L, h, i), y = cell_coord(L, h, j), z = cell_coord(L, h, k);
-          rc = sqrt(x * x + y * y + z * z);
-        }
-        double g[3] = {cell_coord(L, h, i), cell_coord(L, h, j), cell_coord(L, h, k)};
+        double g[3] = {X[0], X[1], X[2]};
         g[d] = cell_coord(L, h, o);
         const double w = rc / sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
         s += uc * w;
@@ -106,8 +116,21 @@ __device__ __forceinline__ double neighbour_sum(int n, double L, double h, const
   return s;
 }
 
+// Laplacian neighbour sum of cell (i, j, k) with the 1/r ghosts; returns
+// the sum and sets *ghost_w to the ghosts' weights (0 inside).
+__device__ __forceinline__ double neighbour_sum(int n, double L, double h, const double *u, int i, int j, int k,
+                                                double uc, double *ghost_w) {
+  if (i > 0 && i < n - 1 && j > 0 && j < n - 1 && k > 0 && k < n - 1) {
+    const long long c = ((long long)k * n + j) * n + i;
+    const long long nn = (long long)n * n;
+    *ghost_w = 0.0;
+    return ((u[c - 1] + u[c + 1]) + (u[c - n] + u[c + n])) + (u[c - nn] + u[c + nn]);
+  }
+  return boundary_sum(n, L, h, u, i, j, k, uc, ghost_w);
+}
+
 __global__ void __launch_bounds__(ID_THREADS) sweep_kernel(int n, double L, double h, double ih2, int color,
-                                                            const double *__restrict__ aa,
+                                                            double omega, const double *__restrict__ aa,
                                                             const double *__restrict__ psi, double *u) {
   const int half = (n + 1) / 2;
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -120,11 +143,11 @@ __global__ void __launch_bounds__(ID_THREADS) sweep_kernel(int n, double L, doub
   double gw;
   const double s = neighbour_sum(n, L, h, u, i, j, k, uc, &gw);
   const double a = __ldg(aa + c);
-  const double iq = 1.0 / (__ldg(psi + c) + uc);
+  const double iq = recip(__ldg(psi + c) + uc);
   const double iq2 = iq * iq, iq4 = iq2 * iq2;
   const double F = (s - 6.0 * uc) * ih2 + 0.125 * a * (iq4 * iq2 * iq);
   const double dF = (gw - 6.0) * ih2 - 0.875 * a * (iq4 * iq4);
-  u[c] = uc - F / dF;
+  u[c] = uc - omega * (F * recip(dF));
 }
 
 __global__ void __launch_bounds__(ID_THREADS) residual_kernel(int n, double L, double h, double ih2,
@@ -140,7 +163,7 @@ __global__ void __launch_bounds__(ID_THREADS) residual_kernel(int n, double L, d
     const double uc = u[c];
     double gw;
     const double s = neighbour_sum(n, L, h, u, i, j, k, uc, &gw);
-    const double iq = 1.0 / (psi[c] + uc);
+    const double iq = recip(psi[c] + uc);
     const double iq2 = iq * iq, iq4 = iq2 * iq2;
     const double F = (s - 6.0 * uc) * ih2 + 0.125 * aa[c] * (iq4 * iq2 * iq);
     if (res) res[c] = F;
@@ -169,6 +192,93 @@ __global__ void __launch_bounds__(ID_THREADS) max_kernel(const double *partial, 
   if (threadIdx.x == 0) *out = sh[0];
 }
 
+// Lagrange weights of the cubic through nodes 0..3 (unit spacing) at t.
+__device__ __forceinline__ void cubic_w(double t, double w[4]) {
+  const double t0 = t, t1 = t - 1.0, t2 = t - 2.0, t3 = t - 3.0;
+  w[0] = -(t1 * t2 * t3) / 6.0;
+  w[1] = (t0 * t2 * t3) / 2.0;
+  w[2] = -(t0 * t1 * t3) / 2.0;
+  w[3] = (t0 * t1 * t2) / 6.0;
+}
+
+__device__ __forceinline__ void cubic_stencil(int n, double L, double h, double x, int *k0, double *t) {
+  const double s = (x + L) / h - 0.5;
+  int k = (int)floor(s) - 1;
+  k = k < 0 ? 0 : (k > n - 4 ? n - 4 : k);
+  *k0 = k;
+  *t = s - k;
+}
+
+// State of the data at one point (see ccz4_id_assemble).
+__global__ void __launch_bounds__(ID_THREADS) assemble_kernel(ccz4::GridView g, int n, double L, double h,
+                                                               PunctureSet B, const double *__restrict__ u,
+                                                               double *state) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.n_points + g.n_ghost) return;
+  double X[3];
+  if (e < g.n_points) {
+    const int p = g.p;
+    const long long p3 = (long long)p * p * p;
+    const int pn = (int)(e / p3);
+    const int q = (int)(e - pn * p3);
+    const int loc[3] = {q % p, (q / p) % p, q / (p * p)};
+    const double dx = g.ldx[g.plev ? __ldg(g.plev + pn) : 0];
+    for (int d = 0; d < 3; ++d) X[d] = g.origin[d] + ((double)__ldg(g.ijk + 3 * pn + d) * p + loc[d] + 0.5) * dx;
+  } else {
+    const long long id = e - g.n_points;
+    for (int d = 0; d < 3; ++d) X[d] = g.origin[d] + (__ldg(g.gcoord + 3 * id + d) + 0.5) * g.dx;
+  }
+  // u by tricubic interpolation
+  int k[3];
+  double w[3][4];
+  for (int d = 0; d < 3; ++d) {
+    double t;
+    cubic_stencil(n, L, h, X[d], &k[d], &t);
+    cubic_w(t, w[d]);
+  }
+  double uz = 0.0;
+  for (int c = 0; c < 4; ++c) {
+    double uy = 0.0;
+    for (int b = 0; b < 4; ++b) {
+      const double *row = u + ((long long)(k[2] + c) * n + (k[1] + b)) * n + k[0];
+      const double ux = w[0][0] * row[0] + w[0][1] * row[1] + w[0][2] * row[2] + w[0][3] * row[3];
+      uy += w[1][b] * ux;
+    }
+    uz += w[2][c] * uy;
+  }
+  // curvature, Brill-Lindquist factor
+  double A[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+  double sbl = 0.0;
+  for (int p = 0; p < B.n; ++p) {
+    double dd[3], nv[3];
+    for (int q = 0; q < 3; ++q) dd[q] = X[q] - B.c[p][q];
+    const double r = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+    for (int q = 0; q < 3; ++q) nv[q] = dd[q] / r;
+    const double Pn = B.P[p][0] * nv[0] + B.P[p][1] * nv[1] + B.P[p][2] * nv[2];
+    const double wv[3] = {B.S[p][1] * nv[2] - B.S[p][2] * nv[1], B.S[p][2] * nv[0] - B.S[p][0] * nv[2],
+                          B.S[p][0] * nv[1] - B.S[p][1] * nv[0]};
+    const double cp = 1.5 / (r * r), cs = 3.0 / (r * r * r);
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const double dab = a == b ? 1.0 : 0.0;
+        A[a][b] += cp * (B.P[p][a] * nv[b] + B.P[p][b] * nv[a] - (dab - nv[a] * nv[b]) * Pn) +
+                   cs * (wv[a] * nv[b] + wv[b] * nv[a]);
+      }
+    sbl += B.m[p] / (2.0 * r);
+  }
+  const double psi = 1.0 + sbl + uz;
+  const double ip = 1.0 / psi, ip2 = ip * ip, ip6 = ip2 * ip2 * ip2;
+  const long long S = g.S;
+  for (int v = 0; v < ccz4::NV; ++v) state[v * S + e] = 0.0;
+  state[ccz4::GXX * S + e] = 1.0;
+  state[ccz4::GYY * S + e] = 1.0;
+  state[ccz4::GZZ * S + e] = 1.0;
+  state[ccz4::ALPHA * S + e] = 0.5 * ((1.0 - sbl) / (1.0 + sbl) + 1.0);
+  state[ccz4::PHI * S + e] = ip2;
+  const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+  for (int c = 0; c < 6; ++c) state[(ccz4::AXX + c) * S + e] = ip6 * A[ia[c]][ib[c]];
+}
+
 cudaError_t launch_sweeps(const ccz4_idsolver *s, int n_sweeps, cudaStream_t st) {
   const int n = s->n;
   const long long work = (long long)((n + 1) / 2) * n * n;
@@ -176,7 +286,7 @@ cudaError_t launch_sweeps(const ccz4_idsolver *s, int n_sweeps, cudaStream_t st)
   const double ih2 = 1.0 / (s->h * s->h);
   for (int k = 0; k < n_sweeps; ++k)
     for (int color = 0; color < 2; ++color) {
-      sweep_kernel<<<grid, ID_THREADS, 0, st>>>(n, s->L, s->h, ih2, color, s->aa, s->psi, s->u);
+      sweep_kernel<<<grid, ID_THREADS, 0, st>>>(n, s->L, s->h, ih2, color, s->omega, s->aa, s->psi, s->u);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
@@ -222,6 +332,7 @@ extern "C" ccz4_status ccz4_id_create(int n, double L, ccz4_idsolver **out) {
   s->n = n;
   s->L = L;
   s->h = 2.0 * L / n;
+  s->omega = 1.0;
   const size_t cells = (size_t)n * n * n;
   s->blocks = (int)((cells + ID_THREADS - 1) / ID_THREADS);
   bool ok = cudaMalloc(&s->u, sizeof(double) * cells) == cudaSuccess &&
@@ -284,6 +395,19 @@ extern "C" ccz4_status ccz4_id_u_ptr(ccz4_idsolver *s, double **dev_u) {
     return CCZ4_ERR_INVALID;
   }
   *dev_u = s->u;
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_id_set_relaxation(ccz4_idsolver *s, double omega) {
+  if (!s || !(omega > 0.0 && omega < 2.0)) {
+    set_error("id_set_relaxation: need a solver and 0 < omega < 2");
+    return CCZ4_ERR_INVALID;
+  }
+  if (omega != s->omega && s->exec) {
+    cudaGraphExecDestroy(s->exec);  // the captured sweeps carry the old factor
+    s->exec = nullptr;
+  }
+  s->omega = omega;
   return CCZ4_OK;
 }
 
@@ -367,5 +491,32 @@ extern "C" ccz4_status ccz4_id_solve(ccz4_idsolver *s, double tol, int max_sweep
   }
   if (sweeps) *sweeps = res < tol ? done : -1;
   if (final_res) *final_res = res;
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_id_assemble(ccz4_idsolver *s, const ccz4_punctures *B, ccz4_grid *g, int buf,
+                                        void *stream) {
+  if (!s || !B || !g || B->n < 1 || B->n > CCZ4_ID_MAX_PUNCTURES || s->n < 4 || buf < CCZ4_BUF_U ||
+      buf > CCZ4_BUF_INI || !g->buf[buf]) {
+    set_error("id_assemble: need a solver (n >= 4), 1..%d punctures, a grid and one of its state buffers",
+              CCZ4_ID_MAX_PUNCTURES);
+    return CCZ4_ERR_INVALID;
+  }
+  PunctureSet P;
+  memset(&P, 0, sizeof(P));
+  P.n = B->n;
+  for (int p = 0; p < B->n; ++p) {
+    P.m[p] = B->m[p];
+    for (int d = 0; d < 3; ++d) {
+      P.c[p][d] = B->c[p][d];
+      P.P[p][d] = B->P[p][d];
+      P.S[p][d] = B->S[p][d];
+    }
+  }
+  const long long total = g->v.n_points + g->v.n_ghost;
+  if (total == 0) return CCZ4_OK;
+  assemble_kernel<<<(unsigned)((total + ID_THREADS - 1) / ID_THREADS), ID_THREADS, 0, (cudaStream_t)stream>>>(
+      g->v, s->n, s->L, s->h, P, s->u, g->buf[buf]);
+  ID_TRY(cudaGetLastError());
   return CCZ4_OK;
 }

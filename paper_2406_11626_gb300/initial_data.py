@@ -48,8 +48,10 @@ def _sig():
         "ccz4_id_set_punctures": [vp, ctypes.POINTER(Punctures), vp],
         "ccz4_id_u_ptr": [vp, ctypes.POINTER(dp)],
         "ccz4_id_sweeps": [vp, ctypes.c_int, vp],
+        "ccz4_id_set_relaxation": [vp, ctypes.c_double],
         "ccz4_id_residual": [vp, dp, dp, vp],
         "ccz4_id_solve": [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, vp],
+        "ccz4_id_assemble": [vp, ctypes.POINTER(Punctures), vp, ctypes.c_int, vp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -88,6 +90,10 @@ class Solver:
         from .ccz4 import _wrap_device
         return _wrap_device(self.u_ptr, (self.n,) * 3, torch.float64)
 
+    def set_relaxation(self, omega):
+        """Relaxation factor of the point update (1: Gauss-Seidel)."""
+        _check(_sig().ccz4_id_set_relaxation(self._h, float(omega)))
+
     def set_punctures(self, B, stream=None):
         _check(_sig().ccz4_id_set_punctures(self._h, ctypes.byref(B), _stream(stream)))
 
@@ -118,6 +124,25 @@ class Solver:
         _check(_sig().ccz4_id_solve(self._h, float(tol), int(max_sweeps), int(check), ctypes.byref(k),
                                     ctypes.byref(r), _stream(stream)))
         return k.value, r.value
+
+    def assemble(self, B, grid, buf="U", stream=None):
+        """Writes the CCZ4 state of the solved data into a state buffer of a
+        ccz4.Grid (every interior point of every level and every ghost cell)."""
+        from .ccz4 import _buf
+        _check(_sig().ccz4_id_assemble(self._h, ctypes.byref(B), grid._h, _buf(buf), _stream(stream)))
+
+
+def solve_config(cfg, stream=None):
+    """The solver of a binary-puncture config after its plain solve from
+    u = 0 to the config's tolerance; returns (solver, punctures, sweeps)."""
+    e = cfg.extra
+    s = Solver(e["id_n"], e["id_L"])
+    B = binary(e["m1"], e["m2"], e["d"], e["P"], e["S"])
+    s.set_punctures(B, stream)
+    k, r = s.solve(tol=e["id_tol"], check=e.get("id_check", 200), stream=stream)
+    if k < 0:
+        raise RuntimeError("initial-data solve did not reach %g (residual %g)" % (e["id_tol"], r))
+    return s, B, k
 
 
 def _as_tensor(a):

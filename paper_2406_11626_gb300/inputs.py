@@ -318,6 +318,29 @@ def multilevel_puncture_config(p=9, n_side=16, half_width=8.0, boxes=None, steps
                       dict(PUNCTURE_PARAMS), cfl * h[-1], steps, None, dict(M=1.0), level, ijk)
 
 
+BINARY_PARAMS = dict(PUNCTURE_PARAMS, eta=1.0)
+
+
+def binary_puncture_config(p=9, steps=500, cfl=0.1, id_n=192, id_tol=1e-10):
+    """Two punctures of bare mass 0.487 at x = -3 and +3 with momenta
+    (0, -0.0934, 0) and (0, +0.0934, 0), no spin (Bowen-York data, u from the
+    plain relaxation solve on id_n^3 cells of [-32, 32]^3 to a max residual
+    of id_tol); [-32, 32]^3 with four ratio-3 levels of 9^3 patches: 16^3
+    level-0 patches (dx = 4/9), [-12, 12]^3 refined (5832 patches),
+    [-5.33, 5.33] x [-2.67, 2.67]^2 refined (3456), [-3.56, 3.56] x
+    [-0.89, 0.89]^2 refined (6912): 20296 patches, 14.8M points. 1+log,
+    Gamma-driver f = 0.75, eta = 1 (the paper's binary setup), KO 0.1,
+    Sommerfeld, RK4 with dt = cfl * finest dx."""
+    boxes = [((5, 5, 5), (11, 11, 11)), ((20, 22, 22), (28, 26, 26)), ((64, 70, 70), (80, 74, 74))]
+    level, ijk = refined_mesh((16, 16, 16), boxes)
+    dx = 64.0 / (16 * p)
+    h = level_spacing(dx, 4)
+    return MeshConfig("binary_puncture", p, (16, 16, 16), (-32.0, -32.0, -32.0), dx, "sommerfeld",
+                      dict(BINARY_PARAMS), cfl * h[-1], steps, None,
+                      dict(m1=0.487, m2=0.487, d=6.0, P=0.0934, S=0.0, id_n=id_n, id_L=32.0, id_tol=id_tol),
+                      level, ijk)
+
+
 def initial_state(cfg):
     """(U, G) at t = 0 for a config; G (the Sommerfeld ghost shell) is empty
     for other boundary kinds. For Sommerfeld, G also serves as Q_ini."""
@@ -332,6 +355,9 @@ def initial_state(cfg):
     if cfg.name == "gauge_wave":
         U = gauge_wave(x, 0.0, cfg.extra["A"], cfg.extra["k"])
         G = np.zeros((NV, 0)) if gx is None else gauge_wave(gx, 0.0, cfg.extra["A"], cfg.extra["k"])
+    elif cfg.name == "binary_puncture":
+        raise ValueError("the binary puncture's data come from the initial-data solve "
+                         "(initial_data.solve_config and Solver.assemble)")
     elif cfg.name == "single_puncture":
         U = brill_lindquist(x, y, z, (cfg.extra["M"],))
         G = np.zeros((NV, 0)) if gx is None else brill_lindquist(gx, gy, gz, (cfg.extra["M"],))

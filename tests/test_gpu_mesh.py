@@ -206,3 +206,73 @@ def test_three_level_puncture_full_size_sampled_parity():
     got = acc.reshape(I.NV, -1)[:, pts].T
     scale = np.maximum(np.abs(ref).max(axis=0), 1.0)
     assert (np.abs(got - ref) / scale).max() < TOL
+
+
+@pytest.mark.slow
+def test_binary_puncture_full_size_sampled_parity():
+    """The four-level binary puncture workload (20296 patches, Bowen-York
+    data from the GPU solve) in the bench's launch configuration: after one
+    fused RK stage, sampled points of every level (including those next to
+    interpolated halos and the punctures' patches) agree with the oracle
+    evaluated point by point on the same state."""
+    from paper_2406_11626_gb300 import ccz4 as C
+    from paper_2406_11626_gb300 import initial_data as ID
+    cfg = I.binary_puncture_config(id_n=96, id_tol=1e-8)
+    g = C.Grid.from_config(cfg)
+    s, B, k = ID.solve_config(cfg)
+    assert k > 0
+    s.assemble(B, g, "U")
+    s.assemble(B, g, "INI")
+    U, G = g.download("U")
+    og = O.Grid(cfg.p, cfg.np, cfg.ijk(), cfg.origin, cfg.dx, cfg.bc, level=cfg.level)
+    P = C.make_params(**cfg.params)
+    g.rk_stage(P, 0, cfg.dt)
+    acc, _ = g.download("ACC")
+    p3 = cfg.p ** 3
+    rng = np.random.default_rng(1)
+    pts = []
+    for l in range(4):
+        on = np.nonzero(np.repeat(cfg.level == l, p3))[0]
+        pts.append(rng.choice(on, 60, replace=False))
+        sl = cfg.ijk()[cfg.level == l]
+        lo, hi = sl.min(axis=0), sl.max(axis=0)
+        edge = np.nonzero((cfg.level == l) & ((cfg.ijk() == lo) | (cfg.ijk() == hi)).any(axis=1))[0]
+        pts.append(rng.choice(edge, 8, replace=False) * p3 + rng.integers(0, p3, 8))
+    x, y, z = I.mesh_point_coords(cfg.p, cfg.level, cfg.ijk(), cfg.origin, cfg.dx)
+    r = np.minimum(np.sqrt((x - 3) ** 2 + y ** 2 + z ** 2), np.sqrt((x + 3) ** 2 + y ** 2 + z ** 2)).ravel()
+    pts.append(np.argsort(r)[:20])
+    pts = np.concatenate(pts)
+    ref = og.rhs_points(O.make_params(**cfg.params), U, G, pts)
+    got = acc.reshape(I.NV, -1)[:, pts].T
+    scale = np.maximum(np.abs(ref).max(axis=0), 1.0)
+    assert (np.abs(got - ref) / scale).max() < TOL
+
+
+@pytest.mark.parametrize("mesh", [None, "three"])
+def test_queue_launch_is_bit_identical_to_flat(mesh):
+    """The persistent work-queue launch of the stage kernel computes every
+    point exactly as the flat launch (plain steps and graph replays)."""
+    from paper_2406_11626_gb300 import ccz4 as C
+    if mesh is None:
+        cfg = I.single_puncture_config(p=6, n_side=4, half_width=2.0)
+        make = lambda: C.Grid.from_config(cfg)
+        U, G = I.initial_state(cfg)
+        dt, P = cfg.dt, C.make_params(**cfg.params)
+    else:
+        dx = 0.3
+        gg, _, lev, ijk, origin = mesh_pair(mesh, "sommerfeld", dx=dx)
+        U, G = mesh_state(gg, lev, ijk, origin, dx, "sommerfeld", seed=2, base="puncture", amp=0.01)
+        make = lambda: C.Grid(6, (4, 4, 4), ijk, origin, dx, "sommerfeld", level=lev)
+        dt, P = 0.1 * I.level_spacing(dx, 3)[-1], C.make_params(**PUNC)
+    out = []
+    for launch in ("flat", "queue"):
+        for graph in (False, True):
+            g = make()
+            g.set_launch(launch)
+            g.upload(U, G)
+            g.upload(U, G, buf="INI")
+            (g.step_graph if graph else g.step)(P, dt, 2)
+            out.append(g.download("U"))
+    for o in out[1:]:
+        np.testing.assert_array_equal(o[0], out[0][0])
+        np.testing.assert_array_equal(o[1], out[0][1])

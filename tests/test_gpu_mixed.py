@@ -18,6 +18,7 @@ from paper_2406_11626_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 RHS_TOL = 2e-5
+PUNC = dict(I.PUNCTURE_PARAMS)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -71,3 +72,30 @@ def test_mixed_puncture_evolution_tracks_fp64():
     c64 = g64.constraints("U")
     c32 = g32.constraints("U")
     assert 0.5 < c32[0] / c64[0] < 2.0 and 0.5 < c32[1] / c64[1] < 2.0
+
+
+def test_mixed_fill_keeps_fp32_slots_for_the_fp32_algebra():
+    """For the mixed path the halo fill takes the mixed derivatives of g~ and
+    beta (used in FP32 by the mixed stage kernel) with FP64 differences and
+    FP32 weights and stores them as FP32 in the first 27 float slots of the
+    buffer; those of alpha and phi (used in FP64 next to 1/phi) stay FP64 and
+    equal the FP64 fill bit for bit; the tiles are the same."""
+    from paper_2406_11626_gb300 import ccz4 as C
+    p, npv, dx = 9, (2, 2, 2), 0.35
+    origin = (-3.15, -3.1, -3.2)
+    gg, og, ijk = make_pair(p, npv, origin, dx, "sommerfeld", permute_seed=3)
+    U, G = random_state(p, npv, origin, dx, ijk, seed=5, bc="sommerfeld", base="puncture")
+    gg.upload(U, G)
+    gg.fill_halos("U", P=C.make_params(**PUNC, precision="fp64"))
+    t64, m64 = gg.download("TILE"), gg.download("MIX")
+    gg.fill_halos("U", P=C.make_params(**PUNC, precision="mixed"))
+    t32, raw = gg.download("TILE"), gg.download("MIX")
+    np.testing.assert_array_equal(t32, t64)
+    n = gg.n_points
+    f32 = np.ascontiguousarray(raw).reshape(-1).view(np.float32)[:27 * n].reshape(27, n)
+    for s in list(range(18)) + list(range(21, 30)):
+        ref = m64[s]
+        got = f32[s if s < 18 else s - 3].astype(np.float64)
+        assert np.abs(got - ref).max() <= 1e-6 * max(np.abs(ref).max(), 1e-30), s
+    for s in (18, 19, 20, 30, 31, 32):
+        np.testing.assert_array_equal(raw[s], m64[s])
