@@ -11,7 +11,7 @@ Sommerfeld ghost-cell kernel). Metric: point-stages per second
 (interior points x 4 stages x steps / time).
 
 Prints one JSON line. --impl reference times the CPU oracle instead (the
-plain FP64 restatement of the paper used as the parity judge) on a bounded
+plain FP64 restatement of the paper that the parity tests use) on a bounded
 sample of the same physics.
 """
 import argparse
@@ -194,8 +194,8 @@ def workload_config(g, precision="fp64", K=None, workload="puncture144"):
     elif workload == "binary":
         cfg = I.binary_puncture_config()
         name = ("rotating binary puncture: bare masses 0.487 at x = -3, +3, momenta (0, -+0.0934, 0), no spin, "
-                "Bowen-York data (u by the plain relaxation solve on 192^3 cells of [-32,32]^3 to residual "
-                "1e-10); [-32,32]^3 on 4 ratio-3 levels of 9^3 patches (4096/5832/3456/6912, dx 4/9 .. 4/243); "
+                "Bowen-York data (u by the plain relaxation solve, over-relaxed by 1.98, on 192^3 cells of "
+                "[-32,32]^3 to residual 1e-10); [-32,32]^3 on 4 ratio-3 levels of 9^3 patches (4096/5832/3456/6912, dx 4/9 .. 4/243); "
                 "1+log, Gamma-driver f=0.75 eta=1, KO 0.1, Sommerfeld, RK4 dt=0.1 dx_finest")
     elif workload == "puncture3level":
         cfg = I.multilevel_puncture_config()
@@ -320,6 +320,21 @@ def time_path(C, I, cfg, precision, K, W, stream, dist, clocks_index=None):
     return g, P, ms, stage_ms, clocks
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over the ranks (the slowest rank sets the job time)."""
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, n_points, stages, seconds):
+    """Whole-job point-stages/s: the units all ranks processed (weak scaling,
+    each rank its own copy of the workload) over the job time."""
+    return world * n_points * stages / seconds
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -337,11 +352,8 @@ def run_gb300(args):
     stream = torch.cuda.current_stream()
     K = args.steps
     g, P, ms, stage_ms, clocks = time_path(C, I, cfg, args.precision, K, args.warmup, stream, dist, local)
-    ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    value = world * cfg.n_points * 4 * K / (ms * 1e-3)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = job_rate(world, cfg.n_points, 4 * K, ms * 1e-3)
     out = g.constraints("U", raise_nonfinite=False)
 
     # end to end through the C ABI from pinned host memory, one step per call
@@ -359,10 +371,7 @@ def run_gb300(args):
     for _ in range(E):
         g.evolve_host(P, cfg.dt, 1, Uh, Gh, Uh, Gh, stream)
     t_e2e = time.perf_counter() - t0
-    te = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * cfg.n_points * 4 * E / float(te.item())
+    e2e_value = job_rate(world, cfg.n_points, 4 * E, max_over_ranks(t_e2e, dist, "cuda"))
 
     mixed = None
     if not args.no_mixed and args.precision == "fp64":

@@ -7,7 +7,7 @@
  * separation d along x (punctures at -d/2 and +d/2), momenta (0, -+P, 0),
  * spins (0, 0, S) each -- to the correction u of the conformal factor
  * (ccz4_id.h). Its output seeds the plain relaxation solve, which stays the
- * judge of the residual.
+ * arbiter of the residual.
  *
  * Network: n_in inputs -> depth hidden layers of `width` units with SiLU,
  * silu(z) = z / (1 + exp(-z)) -> one linear output. Parameters: one flat

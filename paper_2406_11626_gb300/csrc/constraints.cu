@@ -211,9 +211,9 @@ __global__ void __launch_bounds__(RED_THREADS) constraints_kernel(GridView g, Co
   double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (i < g.n_points) {
     const int p = g.p, T = g.T;
-    const long long p3 = (long long)p * p * p;
-    const int n = (int)(i / p3);
-    const int r = (int)(i - n * p3);
+    const int p3 = p * p * p;  // 32-bit division: every state index is below 2^31
+    const int n = (int)i / p3;
+    const int r = (int)i - n * p3;
     const int z = r / (p * p), y = (r / p) % p, x = r % p;
     Nbhd N;
     N.c = tile + n * g.T3 + ((long long)(z + HALO) * T + (y + HALO)) * T + (x + HALO);

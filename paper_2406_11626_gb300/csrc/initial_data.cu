@@ -55,9 +55,10 @@ __device__ __forceinline__ double recip(double d) {
 
 __global__ void __launch_bounds__(ID_THREADS) setup_kernel(int n, double L, double h, PunctureSet B,
                                                             double *aa, double *psi) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= (long long)n * n * n) return;
-  const int i = (int)(c % n), j = (int)((c / n) % n), k = (int)(c / ((long long)n * n));
+  // n <= 1024: every cell index fits 32-bit arithmetic (no 64-bit division)
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n * n * n) return;
+  const int i = c % n, j = (c / n) % n, k = c / (n * n);
   const double X[3] = {cell_coord(L, h, i), cell_coord(L, h, j), cell_coord(L, h, k)};
   double A[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
   double s = 1.0;
@@ -133,9 +134,9 @@ __global__ void __launch_bounds__(ID_THREADS) sweep_kernel(int n, double L, doub
                                                             double omega, const double *__restrict__ aa,
                                                             const double *__restrict__ psi, double *u) {
   const int half = (n + 1) / 2;
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= (long long)half * n * n) return;
-  const int i2 = (int)(q % half), j = (int)((q / half) % n), k = (int)(q / ((long long)half * n));
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // 32-bit index arithmetic (n <= 1024)
+  if (q >= half * n * n) return;
+  const int i2 = q % half, j = (q / half) % n, k = q / (half * n);
   const int i = 2 * i2 + ((j + k + color) & 1);
   if (i >= n) return;
   const long long c = ((long long)k * n + j) * n + i;
@@ -156,10 +157,10 @@ __global__ void __launch_bounds__(ID_THREADS) residual_kernel(int n, double L, d
                                                                const double *__restrict__ u, double *res,
                                                                double *partial) {
   __shared__ double sh[ID_THREADS];
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
   double v = 0.0;
-  if (c < (long long)n * n * n) {
-    const int i = (int)(c % n), j = (int)((c / n) % n), k = (int)(c / ((long long)n * n));
+  if (c < n * n * n) {
+    const int i = c % n, j = (c / n) % n, k = c / (n * n);
     const double uc = u[c];
     double gw;
     const double s = neighbour_sum(n, L, h, u, i, j, k, uc, &gw);
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(ID_THREADS) assemble_kernel(ccz4::GridView g, 
   if (e < g.n_points) {
     const int p = g.p;
     const long long p3 = (long long)p * p * p;
-    const int pn = (int)(e / p3);
+    const int pn = (int)e / (int)p3;  // state indices are below 2^31
     const int q = (int)(e - pn * p3);
     const int loc[3] = {q % p, (q / p) % p, q / (p * p)};
     const double dx = g.ldx[g.plev ? __ldg(g.plev + pn) : 0];

@@ -287,11 +287,12 @@ namespace {
 __global__ void __launch_bounds__(128) restrict_kernel(GridView g, const int *__restrict__ par,
                                                        const int *__restrict__ kid, int n_par, double *U) {
   const int p = g.p;
-  const long long p3 = (long long)p * p * p;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)n_par * p3) return;
-  const int k = (int)(i / p3);
-  const int q = (int)(i - k * p3);
+  const int p3 = p * p * p;
+  // n_par * p^3 points of coarse patches: below 2^31 (32-bit division)
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_par * p3) return;
+  const int k = i / p3;
+  const int q = i - k * p3;
   const int cz = q / (p * p), cy = (q / p) % p, cx = q % p;
   const int *kk = kid + 27 * k;
   int idx[27];
@@ -303,9 +304,9 @@ __global__ void __launch_bounds__(128) restrict_kernel(GridView g, const int *__
       for (int a = 0; a < 3; ++a) {
         const int X = 3 * cx + a, Y = 3 * cy + b, Z = 3 * cz + c;
         const int child = __ldg(kk + ((Z / p) * 3 + Y / p) * 3 + X / p);
-        idx[(c * 3 + b) * 3 + a] = (int)(child * p3 + ((long long)(Z % p) * p + Y % p) * p + X % p);
+        idx[(c * 3 + b) * 3 + a] = child * p3 + ((Z % p) * p + Y % p) * p + X % p;
       }
-  const long long dst = (long long)__ldg(par + k) * p3 + q;
+  const long long dst = (long long)__ldg(par + k) * p3 + q;  // below 2^31 too
   const double third = 1.0 / 3.0;
   for (int v = 0; v < NV; ++v) {
     const double *f = U + v * g.S;

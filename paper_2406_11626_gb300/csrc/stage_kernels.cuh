@@ -140,8 +140,10 @@ __device__ __forceinline__ void stage_point(const GridView &g, const Phys<R> &P,
                                             const double *__restrict__ tile, const double *__restrict__ mix,
                                             const StageArgs &a, long long i) {
   const int p = g.p, T = g.T;
-  const long long p3 = (long long)p * p * p;
-  const int n = (int)(i / p3);
+  // 32-bit division (every state index is below 2^31): a 64-bit integer
+  // division is a long software sequence
+  const int p3 = p * p * p;
+  const int n = (int)i / p3;
   // a run-time index into the parameter array is only taken on a mesh (it
   // makes ptxas keep a local copy of the array)
   const int lev = MESH ? patch_level(g, n) : 0;

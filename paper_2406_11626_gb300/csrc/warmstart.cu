@@ -209,7 +209,8 @@ __global__ void adam_kernel(float *theta, float *m, float *v, const float *g, lo
 }
 
 __device__ __forceinline__ void features(int n, double L, long long c, const float *p5, float *x) {
-  const int i = (int)(c % n), j = (int)((c / n) % n), k = (int)(c / ((long long)n * n));
+  const int ci = (int)c;  // n <= 1024: 32-bit index arithmetic
+  const int i = ci % n, j = (ci / n) % n, k = ci / (n * n);
   const double h = 2.0 * L / n;
   x[0] = (float)((-L + (i + 0.5) * h) / L);
   x[1] = (float)((-L + (j + 0.5) * h) / L);

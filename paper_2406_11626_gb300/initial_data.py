@@ -137,6 +137,7 @@ def solve_config(cfg, stream=None):
     u = 0 to the config's tolerance; returns (solver, punctures, sweeps)."""
     e = cfg.extra
     s = Solver(e["id_n"], e["id_L"])
+    s.set_relaxation(e.get("id_omega", 1.0))
     B = binary(e["m1"], e["m2"], e["d"], e["P"], e["S"])
     s.set_punctures(B, stream)
     k, r = s.solve(tol=e["id_tol"], check=e.get("id_check", 200), stream=stream)

@@ -13,11 +13,11 @@ orchestration of the experiment:
 3. training: Adam on the mean squared error of the scaled correction at
    cells drawn uniformly (host-seeded) from the stored solutions;
 4. evaluation: on held-out draws, sweeps to the same tolerance from the
-   network's guess against sweeps from u = 0, with the same relaxation
-   (by default red-black Newton-SOR with the factor that needs the fewest
-   sweeps on three training draws; omega = 1 gives plain Gauss-Seidel). The plain solve stays the
-   judge: a guess is only a starting point, and a solve that does not reach
-   the tolerance reports -1.
+   network's guess against sweeps from u = 0, with the same relaxation (by
+   default red-black Newton-SOR with the factor that needs the fewest sweeps
+   on three training draws; omega = 1 gives plain Gauss-Seidel). The plain
+   solve stays the arbiter: a guess is only a starting point, and a solve
+   that does not reach the tolerance reports -1.
 """
 import ctypes
 import time

@@ -217,7 +217,7 @@ def test_binary_puncture_full_size_sampled_parity():
     evaluated point by point on the same state."""
     from paper_2406_11626_gb300 import ccz4 as C
     from paper_2406_11626_gb300 import initial_data as ID
-    cfg = I.binary_puncture_config(id_n=96, id_tol=1e-8)
+    cfg = I.binary_puncture_config(id_n=96, id_tol=1e-8, id_omega=1.97)
     g = C.Grid.from_config(cfg)
     s, B, k = ID.solve_config(cfg)
     assert k > 0

@@ -1,7 +1,7 @@
 """The learned warm start on the GPU (include/ccz4_mlp.h): forward pass,
 back-propagated gradients and Adam against the FP64 oracle, the feature
 kernels, and the gain of a trained network over the plain solve from u = 0
-on held-out draws (the plain solve judges both)."""
+on held-out draws (the plain solve decides both)."""
 import numpy as np
 import pytest
 
