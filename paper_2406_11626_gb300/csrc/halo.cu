@@ -21,8 +21,17 @@
 namespace ccz4 {
 namespace {
 
-constexpr int FILL_THREADS = 256;
-constexpr int GATHER_BATCH = 8;
+#ifndef CCZ4_FILL_THREADS
+#define CCZ4_FILL_THREADS 256
+#endif
+#ifndef CCZ4_FILL_GATHER_BATCH
+#define CCZ4_FILL_GATHER_BATCH 8
+#endif
+#ifndef CCZ4_FILL_MIN_BLOCKS
+#define CCZ4_FILL_MIN_BLOCKS 4
+#endif
+constexpr int FILL_THREADS = CCZ4_FILL_THREADS;
+constexpr int GATHER_BATCH = CCZ4_FILL_GATHER_BATCH;
 constexpr size_t FILL_SMEM_LIMIT = 227 * 1024;  // dynamic shared memory one block may use
 
 // Whether the d_z pass of the mixed derivatives fits on the region widened
@@ -90,7 +99,7 @@ __device__ __forceinline__ double interp_value(const InterpEntry *__restrict__ e
 // (and may be interpolations); otherwise they are resolved here. F32W: FP32
 // weights for the mixed derivatives (see mixed_out).
 template <bool MESH, bool F32W>
-__global__ void __launch_bounds__(FILL_THREADS, 4) fill_halos_kernel(GridView g, const double *__restrict__ src,
+__global__ void __launch_bounds__(FILL_THREADS, CCZ4_FILL_MIN_BLOCKS) fill_halos_kernel(GridView g, const double *__restrict__ src,
                                                                   double *__restrict__ tile,
                                                                   double *__restrict__ mix, LevelScale ls) {
   extern __shared__ double smem[];
