@@ -234,15 +234,22 @@ def _has_children(cfg, n):
 # ----------------------------------------------------------------------------
 # GB300 arm
 # ----------------------------------------------------------------------------
-def load_traffic():
+def load_traffic(n_points, precision="fp64", mesh=False):
+    """DRAM bytes of one stage-kernel launch over n_points, from the ncu
+    capture recorded in profiles/traffic.json (FP64, single-level instance),
+    scaled by points; None for another kernel instance (mixed precision, a
+    refined mesh) or once the kernel sources have changed."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
-    if d.get("kernel_hash") != kernel_hash():
+    if d.get("kernel_hash") != kernel_hash() or precision != "fp64" or mesh:
         return None
-    return d.get("bytes_per_launch")
+    cap = d.get("captured", {})
+    if not cap.get("points"):
+        return None
+    return (cap["dram_bytes_read"] + cap["dram_bytes_write"]) * n_points / cap["points"]
 
 
 def bench_config(args):
@@ -412,14 +419,14 @@ def run_gb300(args):
     f32 = fl["fp32"] * cfg.n_points
     if args.precision == "fp64" or f32 == 0:
         roof = {"bound": "alu", "achieved": f64 / t_stage / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": f64 / t_stage / 1e12 / FP64_PEAK_TFLOPS, "traffic": load_traffic(),
+                "frac": f64 / t_stage / 1e12 / FP64_PEAK_TFLOPS, "traffic": load_traffic(cfg.n_points, args.precision, g.n_levels > 1),
                 "kernel": "interior_kernel (fused RHS + RK stage) with the ghost-cell kernel of the same stage",
                 "flops_per_point_stage": fl["fp64"], "units_per_launch": cfg.n_points,
                 "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz"}
     else:
         t_roof = max(f64 / (FP64_PEAK_TFLOPS * 1e12), f32 / (FP32_PEAK_TFLOPS * 1e12))
         roof = {"bound": "alu", "achieved": f64 / t_stage / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": t_roof / t_stage, "traffic": load_traffic(),
+                "frac": t_roof / t_stage, "traffic": load_traffic(cfg.n_points, args.precision, g.n_levels > 1),
                 "fp64_flops_per_point_stage": fl["fp64"], "fp32_flops_per_point_stage": fl["fp32"],
                 "fp32_tflops": f32 / t_stage / 1e12,
                 "note": "frac = max(F64/P64, F32/P32) / kernel time"}

@@ -5,9 +5,10 @@
 //
 // One CTA per patch. It resolves the source of every tile point once
 // (neighbour patch, periodic wrap, clamped copy or Sommerfeld ghost cell;
-// on a refined mesh it reads the host-built table instead, whose entries
-// may also be coarse-to-fine interpolations) into an index table, then for each of the 25 fields gathers the field's
-// tile into shared memory and writes it out with coalesced stores. For g~,
+// on a refined mesh it reads the host-built table instead, and computes the
+// coarse-to-fine interpolations it lists for all fields in one pass) into
+// an index table, then for each of the 25 fields gathers the field's tile
+// into shared memory and writes it out with coalesced stores. For g~,
 // alpha, beta and phi it also forms the mixed derivatives d_x d_y, d_x d_z,
 // d_y d_z as the first-derivative stencil applied to first derivatives
 // shared through shared memory: d_y Q is taken once on the patch widened by
@@ -73,24 +74,25 @@ __device__ __forceinline__ double pw(int r, int k) {
   return r == 0 ? (k == 0 ? 1.0 : 0.0) : r == 1 ? (k == 0 ? 2.0 / 3.0 : 1.0 / 3.0) : (k == 0 ? 1.0 / 3.0 : 2.0 / 3.0);
 }
 
-// Value of an interpolated halo point of a refined mesh: the tensor product
+// Value of an interpolated halo point of a refined mesh from the corner
+// indices c[8] and remainders (rx, ry, rz) of its entry: the tensor product
 // of three linear maps, along x, then y, then z; every product and sum is
-// rounded on its own (no fused multiply-add), in that order.
-__device__ __forceinline__ double interp_value(const InterpEntry *__restrict__ e, const double *__restrict__ sv) {
-  const int r = __ldg(&e->r);
-  const int rx = r & 3, ry = (r >> 2) & 3, rz = (r >> 4) & 3;
+// rounded on its own (no fused multiply-add), in that order. A corner along
+// an axis with remainder 0 has weight zero and is not read.
+__device__ __forceinline__ double interp_value(const int (&c)[8], int rx, int ry, int rz,
+                                               const double *__restrict__ sv) {
   double t[2][2], u[2];
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    if (c == 1 && rz == 0) break;
+  for (int cz = 0; cz < 2; ++cz) {
+    if (cz == 1 && rz == 0) break;
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
       if (b == 1 && ry == 0) break;
-      const double q0 = __ldg(sv + __ldg(&e->src[(c * 2 + b) * 2]));
-      t[c][b] = rx ? __dadd_rn(__dmul_rn(pw(rx, 0), q0), __dmul_rn(pw(rx, 1), __ldg(sv + __ldg(&e->src[(c * 2 + b) * 2 + 1]))))
-                   : q0;
+      const double q0 = __ldg(sv + c[(cz * 2 + b) * 2]);
+      t[cz][b] = rx ? __dadd_rn(__dmul_rn(pw(rx, 0), q0), __dmul_rn(pw(rx, 1), __ldg(sv + c[(cz * 2 + b) * 2 + 1])))
+                    : q0;
     }
-    u[c] = ry ? __dadd_rn(__dmul_rn(pw(ry, 0), t[c][0]), __dmul_rn(pw(ry, 1), t[c][1])) : t[c][0];
+    u[cz] = ry ? __dadd_rn(__dmul_rn(pw(ry, 0), t[cz][0]), __dmul_rn(pw(ry, 1), t[cz][1])) : t[cz][0];
   }
   return rz ? __dadd_rn(__dmul_rn(pw(rz, 0), u[0]), __dmul_rn(pw(rz, 1), u[1])) : u[0];
 }
@@ -119,6 +121,22 @@ __global__ void __launch_bounds__(FILL_THREADS, CCZ4_FILL_MIN_BLOCKS) fill_halos
     // refined mesh: sources resolved once on the host
     const int *sp = g.src + (long long)n * T3;
     for (int t = threadIdx.x; t < T3; t += blockDim.x) idx[t] = __ldg(sp + t);
+    // The patch's interpolated halo points, one entry per thread, all fields
+    // at once: the entry is read once and the fields' corner loads are
+    // independent. The fields that need mixed derivatives read these values
+    // back from the tile after the barrier below.
+    const int e1 = __ldg(g.ibeg + n + 1);
+    for (int e = __ldg(g.ibeg + n) + threadIdx.x; e < e1; e += FILL_THREADS) {
+      const InterpEntry *ep = g.interp + e;
+      int c[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) c[k] = __ldg(&ep->src[k]);
+      const int r = __ldg(&ep->r), t = __ldg(&ep->t);
+      const int rx = r & 3, ry = (r >> 2) & 3, rz = (r >> 4) & 3;
+      double *tp = tile + (long long)n * g.T3 + t;
+#pragma unroll 5
+      for (int v = 0; v < NV; ++v) __stcs(tp + (long long)v * g.n_patches * g.T3, interp_value(c, rx, ry, rz, src + v * g.S));
+    }
   } else {
     for (int t = threadIdx.x; t < T3; t += blockDim.x) {
       const int lz = t / (T * T), ly = (t / T) % T, lx = t % T;
@@ -139,30 +157,22 @@ __global__ void __launch_bounds__(FILL_THREADS, CCZ4_FILL_MIN_BLOCKS) fill_halos
     // field costs a couple of memory latencies rather than one per point.
     for (int t0 = threadIdx.x; t0 < T3; t0 += GATHER_BATCH * FILL_THREADS) {
       double val[GATHER_BATCH];
+      int sx[GATHER_BATCH];
 #pragma unroll
       for (int u = 0; u < GATHER_BATCH; ++u) {
         const int t = t0 + u * FILL_THREADS;
-        const int s = t < T3 ? idx[t] : -1;
-        val[u] = s >= 0 ? __ldg(sv + s) : 0.0;
+        sx[u] = t < T3 ? idx[t] : -1;
+        // on a mesh, interpolated points (s <= -2) were written by the pass
+        // above: read back (through L2) only where the mixed derivatives need them
+        val[u] = sx[u] >= 0 ? __ldg(sv + sx[u]) : (MESH && slot >= 0 && sx[u] <= -2) ? __ldcg(tv + t) : 0.0;
       }
 #pragma unroll
       for (int u = 0; u < GATHER_BATCH; ++u) {
         const int t = t0 + u * FILL_THREADS;
-        // on a mesh, interpolated points (s <= -2) are written by the pass below
-        if (t < T3 && (!MESH || idx[t] > -2)) {
+        if (t < T3) {
           if (slot >= 0) ts[t] = val[u];
-          __stcs(tv + t, val[u]);  // read once, by the stage kernel
+          if (!MESH || sx[u] > -2) __stcs(tv + t, val[u]);  // read once, by the stage kernel
         }
-      }
-    }
-    if (MESH) {
-      // the patch's interpolated halo points, one entry per thread
-      const int e1 = __ldg(g.ibeg + n + 1);
-      for (int e = __ldg(g.ibeg + n) + threadIdx.x; e < e1; e += FILL_THREADS) {
-        const double val = interp_value(g.interp + e, sv);
-        const int t = __ldg(&g.interp[e].t);
-        if (slot >= 0) ts[t] = val;
-        __stcs(tv + t, val);
       }
     }
     if (slot < 0) continue;  // uniform across the block

@@ -130,15 +130,61 @@ __device__ __forceinline__ double neighbour_sum(int n, double L, double h, const
   return boundary_sum(n, L, h, u, i, j, k, uc, ghost_w);
 }
 
+// Threads of one half-sweep: the interior cells of the colour first, then
+// every cell of the boundary shell (those of the other colour return). The
+// split keeps the out-of-line ghost path off the warps of interior cells
+// (with rows of n/2 cells of a colour nearly every warp would otherwise
+// hold a boundary cell).
+__host__ __device__ inline int sweep_interior_threads(int n) {
+  const int m = n - 2;
+  return m > 0 ? ((m + 1) / 2) * m * m : 0;
+}
+__host__ __device__ inline int sweep_threads(int n) {
+  const int m = n - 2 > 0 ? n - 2 : 0;
+  return sweep_interior_threads(n) + (n * n * n - m * m * m);
+}
+
+// One half-sweep: the cells with i + j + k + color even take one Newton
+// step of the discrete Hamiltonian constraint, over-relaxed by omega.
 __global__ void __launch_bounds__(ID_THREADS) sweep_kernel(int n, double L, double h, double ih2, int color,
                                                             double omega, const double *__restrict__ aa,
                                                             const double *__restrict__ psi, double *u) {
-  const int half = (n + 1) / 2;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // 32-bit index arithmetic (n <= 1024)
-  if (q >= half * n * n) return;
-  const int i2 = q % half, j = (q / half) % n, k = q / (half * n);
-  const int i = 2 * i2 + ((j + k + color) & 1);
-  if (i >= n) return;
+  // 32-bit index arithmetic (n <= 1024)
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n_int = sweep_interior_threads(n);
+  const int m = n - 2;
+  int i, j, k;
+  if (q < n_int) {
+    const int half = (m + 1) / 2;
+    const int i2 = q % half;
+    j = (q / half) % m + 1;
+    k = q / (half * m) + 1;
+    i = 1 + 2 * i2 + ((1 + j + k + color) & 1);
+    if (i >= n - 1) return;
+  } else {
+    // boundary shell: the planes k = 0 and k = n-1, then per interior k the
+    // rows j = 0 and j = n-1, then the cells i = 0 and i = n-1 of the
+    // interior rows
+    const int b = q - n_int, n2 = n * n;
+    if (b < 2 * n2) {
+      k = b < n2 ? 0 : n - 1;
+      j = (b % n2) / n;
+      i = b % n;
+    } else {
+      const int per = 2 * n + 2 * m, b2 = b - 2 * n2;
+      k = 1 + b2 / per;
+      if (k >= n - 1) return;
+      const int r = b2 % per;
+      if (r < 2 * n) {
+        j = r < n ? 0 : n - 1;
+        i = r % n;
+      } else {
+        j = 1 + (r - 2 * n) / 2;
+        i = ((r - 2 * n) & 1) ? n - 1 : 0;
+      }
+    }
+    if ((i + j + k + color) & 1) return;
+  }
   const long long c = ((long long)k * n + j) * n + i;
   const double uc = u[c];
   double gw;
@@ -282,8 +328,7 @@ __global__ void __launch_bounds__(ID_THREADS) assemble_kernel(ccz4::GridView g, 
 
 cudaError_t launch_sweeps(const ccz4_idsolver *s, int n_sweeps, cudaStream_t st) {
   const int n = s->n;
-  const long long work = (long long)((n + 1) / 2) * n * n;
-  const unsigned grid = (unsigned)((work + ID_THREADS - 1) / ID_THREADS);
+  const unsigned grid = (unsigned)((sweep_threads(n) + ID_THREADS - 1) / ID_THREADS);
   const double ih2 = 1.0 / (s->h * s->h);
   for (int k = 0; k < n_sweeps; ++k)
     for (int color = 0; color < 2; ++color) {

@@ -20,6 +20,7 @@ orchestration of the experiment:
    that does not reach the tolerance reports -1.
 """
 import ctypes
+import math
 import time
 
 import numpy as np
@@ -204,8 +205,17 @@ def solve_draws(draws, n, L, tol=1e-10, check=100, max_sweeps=2000000, keep=True
     return store, np.array(sweeps), time.perf_counter() - t0
 
 
-def train(mlp, u_store, draws, n, L, steps, batch=16384, lr=1e-3, seed=1, log_every=0):
-    """Adam on uniformly drawn (solution, cell) rows; returns the loss history."""
+def lr_at(k, steps, lr, lr_final=None):
+    """Learning rate of step k: cosine decay from lr to lr_final over the
+    run (constant lr when lr_final is None)."""
+    if lr_final is None or steps <= 1:
+        return lr
+    return lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * k / (steps - 1)))
+
+
+def train(mlp, u_store, draws, n, L, steps, batch=16384, lr=1e-3, seed=1, log_every=0, lr_final=None):
+    """Adam on uniformly drawn (solution, cell) rows, learning rate from
+    lr_at; returns the loss history."""
     import torch
     rng = np.random.default_rng(seed)
     p5 = torch.as_tensor(np.asarray(draws, dtype=np.float32), device="cuda").contiguous()
@@ -215,7 +225,7 @@ def train(mlp, u_store, draws, n, L, steps, batch=16384, lr=1e-3, seed=1, log_ev
         idx = torch.as_tensor(rng.integers(0, len(draws) * n3, batch, dtype=np.int64), device="cuda")
         x, t = features_sample(n, L, p5, u_store, idx)
         loss = mlp.loss_grad(x, t)
-        mlp.adam(lr)
+        mlp.adam(lr_at(k, steps, lr, lr_final))
         if log_every and (k % log_every == 0 or k == steps - 1):
             hist.append((k, float(loss.item())))
     return hist
@@ -243,7 +253,7 @@ def evaluate(mlp, draws, n, L, tol=1e-10, check=100, max_sweeps=2000000, omega=1
 
 
 def run_experiment(n=96, L=16.0, n_train=2000, n_test=200, steps=20000, batch=65536, lr=1e-3, tol=1e-10,
-                   check=20, seed=0, omega=None, gs_draws=10, log=print):
+                   check=20, seed=0, omega=None, gs_draws=10, log=print, lr_final=1e-5):
     """The whole experiment; returns a JSON-ready report."""
     import torch
     draws = sobol_draws(n_train + n_test, seed=seed)
@@ -261,7 +271,7 @@ def run_experiment(n=96, L=16.0, n_train=2000, n_test=200, steps=20000, batch=65
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     hist = train(net, store, train_d, n, L, steps, batch=batch, lr=lr, seed=seed + 1,
-                 log_every=max(1, steps // 20))
+                 log_every=max(1, steps // 20), lr_final=lr_final)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
     log("training: %d steps of %d rows in %.1f s, loss %s" % (steps, batch, t_train, hist[-1]))
@@ -278,7 +288,7 @@ def run_experiment(n=96, L=16.0, n_train=2000, n_test=200, steps=20000, batch=65
         "draws": {"train": n_train, "test": n_test, "sobol_seed": seed, "ranges": dict(zip(
             ("m1", "m2", "d", "P", "S"), RANGES))},
         "network": {"layers": "8 -> 4 x 128 SiLU -> 1", "params": net.n_params, "steps": steps, "batch": batch,
-                    "lr": lr, "loss_history": hist},
+                    "lr": lr, "lr_final": lr_final, "loss_history": hist},
         "train_solves": {"seconds": t_solve, "sweeps_mean": float(sweeps.mean())},
         "train_seconds": t_train,
         "eval": {"seconds": t_eval, "all_converged": bool(ok.all()),
@@ -313,6 +323,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr-final", type=float, default=1e-5, help="end of the cosine learning-rate decay")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--omega", type=float, default=None,
                     help="relaxation factor (default: the fastest of a short scan; 1 = Gauss-Seidel)")
@@ -322,7 +333,7 @@ def main(argv=None):
     ap.add_argument("--out", default=None, help="write the report as JSON here")
     a = ap.parse_args(argv)
     rep = run_experiment(a.n, a.L, a.train, a.test, a.steps, a.batch, a.lr, a.tol, check=a.check, omega=a.omega,
-                         gs_draws=a.gs_draws, log=lambda s: print(s, flush=True))
+                         gs_draws=a.gs_draws, log=lambda s: print(s, flush=True), lr_final=a.lr_final)
     if a.out:
         with open(a.out, "w") as f:
             json.dump(rep, f, indent=1)

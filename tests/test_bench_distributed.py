@@ -58,3 +58,22 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_traffic_is_scaled_by_points_and_kept_to_the_captured_kernel(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    rec = {"kernel_hash": bench.kernel_hash(),
+           "captured": {"points": 1000, "dram_bytes_read": 3.0e6, "dram_bytes_write": 1.0e6}}
+    (prof / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    # kernel_hash reads the kernel sources under ROOT: keep the real ones
+    monkeypatch.setattr(bench, "kernel_hash", lambda h=rec["kernel_hash"]: h)
+    assert bench.load_traffic(5000) == 2.0e7                 # 4 kB per point x 5000
+    assert bench.load_traffic(5000, "mixed") is None         # another kernel instance
+    assert bench.load_traffic(5000, mesh=True) is None
+    rec["kernel_hash"] = "0" * 16                            # sources changed since the capture
+    (prof / "traffic.json").write_text(json.dumps(rec))
+    assert bench.load_traffic(5000) is None
