@@ -391,6 +391,9 @@ def run_gb300(args):
         a = a.reshape(I.NV, -1)
         b = b.reshape(I.NV, -1)
         err = np.abs(b - a).max(axis=1) / np.maximum(np.abs(a).max(axis=1), 1.0)
+        # root-mean-square difference over all interior points, same scaling
+        rms = lambda x: np.sqrt(np.mean(np.square(x), axis=1))
+        err2 = rms(b - a) / np.maximum(rms(a), 1.0)
         c64 = g64.constraints("U", raise_nonfinite=False)
         cmx = gmx.constraints("U", raise_nonfinite=False)
         flm = C.flops_per_point_stage("mixed")
@@ -403,6 +406,7 @@ def run_gb300(args):
                  "max_rel_state_error_vs_fp64": float(err.max()),
                  "worst_field": I.FIELDS[int(err.argmax())],
                  "rel_state_error_per_field": {f: float(e) for f, e in zip(I.FIELDS, err)},
+                 "rms_state_error_per_field": {f: float(e) for f, e in zip(I.FIELDS, err2)},
                  "after_steps": K + args.warmup,
                  "L2_H": cmx[0], "L2_H_fp64": c64[0], "L2_M": cmx[1], "L2_M_fp64": c64[1],
                  "roofline_frac": t_roof_mx / t_stage_mx,
