@@ -8,7 +8,8 @@ equations quadratic in eps, so the linear response of each right-hand side
 is a constant times the mode or times one of its FD4 derivatives. The
 constants below are read off the printed equations by hand: the 1+log or
 harmonic slicing, the Gamma-driver (f, eta, s), the Theta and Z damping
-(kappa1, kappa2, c, e), the Lie-derivative and Ricci parts. On a periodic
+(kappa1, kappa2, c, e), the relaxation of det g~ (tau), the Lie-derivative,
+Ricci and conformal-factor parts. On a periodic
 grid the FD4 stencils act on the mode exactly as their Fourier symbols
 (textbook): d1 sin = s1 cos with s1 = (8 sin(kh) - sin(2kh)) / (6h), d2 sin
 = -s2 sin with s2 = (30 - 32 cos(kh) + 2 cos(2kh)) / (12 h^2), and the
@@ -88,12 +89,22 @@ def _expected(field, slicing, s1, s2, ko):
                   "K": (0, s1), "Theta": (0, 0.5 * p["e"] ** 2 * s1), "bx": (-k1, 0)},
         # transverse metric: -1/2 g~^kl d_k d_l g~_ij, and Z_i = -G~_i / 2 damped by kappa1
         "gxy": {"gxy": (ko, 0), "Axy": (s2 / 2, 0), "Ghaty": (0, k1 * s1), "by": (0, k1 * s1)},
+        # diagonal metric: det g~ - 1 = eps sin relaxed on the time scale tau in every diagonal
+        # component; R_xx + 2 nabla_(x Z_x) = -1/2 d_x d_x g~_xx, its trace in K and Theta, its
+        # trace-free part in A~; G~^x = 1/2 d_x g~_xx feeds the Z damping
+        "gxx": {"gxx": (-1.0 / p["tau"] + ko, 0), "gyy": (-1.0 / p["tau"], 0), "gzz": (-1.0 / p["tau"], 0),
+                "Axx": (s2 / 3, 0), "Ayy": (-s2 / 6, 0), "Azz": (-s2 / 6, 0), "K": (s2 / 2, 0),
+                "Theta": (0.25 * p["e"] ** 2 * s2, 0), "Ghatx": (0, k1 * s1 / 2), "bx": (0, k1 * s1 / 2)},
+        # conformal factor: (1/phi)(nabla~_i nabla~_j phi + g~_ij g~^kl nabla~_k nabla~_l phi), trace 4 d^2 phi
+        "phi": {"phi": (ko, 0), "K": (-4 * s2, 0), "Theta": (-2 * p["e"] ** 2 * s2, 0), "Axx": (-2 * s2 / 3, 0),
+                "Ayy": (s2 / 3, 0), "Azz": (s2 / 3, 0)},
     }
     return table[field]
 
 
 @pytest.mark.parametrize("slicing", ["1+log", "harmonic"])
-@pytest.mark.parametrize("field", ["alpha", "K", "Theta", "betax", "betay", "by", "Ghaty", "Ghatx", "gxy"])
+@pytest.mark.parametrize("field", ["alpha", "K", "Theta", "betax", "betay", "by", "Ghaty", "Ghatx", "gxy", "gxx",
+                                   "phi"])
 def test_linear_response_about_flat_space(field, slicing):
     g, x, h = _grid()
     P = O.make_params(**dict(PARAMS, slicing=slicing))
