@@ -132,3 +132,37 @@ def test_zero_shift_freezes_beta_and_b():
             assert np.abs(r[I.IDX[name]] - want).max() <= 1e-7 * s2, (field, name)
     r, S, C = _response(g, x, P, "Ghaty")
     assert np.abs(r[I.IDX["Axy"]] - 0.5 * s1 * C).max() <= 1e-7 * s2
+
+
+def test_bilinear_response_pins_kappa3_and_shift_advection():
+    """The kappa3 terms 2 kappa3 (2/3 g~^ij Z_j B_k^k - g~^jk Z_j B_k^i) are
+    products of Z and d beta, so they show in the mixed second-order response
+    to a longitudinal Gamma-hat mode (Z_x = Gamma-hat^x / 2) and a shift mode
+    of another wavenumber: d_t Gamma-hat^x gains beta d_x Gamma-hat^x
+    (advection) - kappa3/3 Gamma-hat^x d_x beta^x; in d_t b^x the advection
+    cancels (d_t b - beta d b = d_t Gamma-hat - beta d Gamma-hat - eta b) and
+    only the kappa3 part stays; no other right-hand side has a product of
+    the two. Mixed central difference in (eps1, eps2)."""
+    g, x, h = _grid()
+    P = O.make_params(**dict(PARAMS, slicing="1+log"))
+    k = 2.0 * math.pi * M
+    e1 = e2 = 1e-4
+    r = {}
+    for a in (1.0, -1.0):
+        for b in (1.0, -1.0):
+            U = I.flat(g.ushape[1:])
+            U[I.IDX["Ghatx"]] += a * e1 * np.sin(k * x)
+            U[I.IDX["betax"]] += b * e2 * np.sin(2 * k * x)
+            r[a, b] = g.rhs(P, U)[0]
+    mixed = (r[1, 1] - r[1, -1] - r[-1, 1] + r[-1, -1]) / (4.0 * e1 * e2)
+
+    def d1(kk):  # FD4 symbol of d/dx on sin(kk x)
+        return (8.0 * math.sin(kk * h) - math.sin(2 * kk * h)) / (6.0 * h)
+
+    adv = np.sin(2 * k * x) * d1(k) * np.cos(k * x)                 # beta^x d_x Gamma-hat^x
+    k3 = -PARAMS["kappa3"] / 3.0 * np.sin(k * x) * d1(2 * k) * np.cos(2 * k * x)
+    want = {"Ghatx": adv + k3, "bx": k3}
+    scale = d1(2 * k)
+    for v, name in enumerate(I.FIELDS):
+        err = np.abs(mixed[v] - want.get(name, 0.0)).max()
+        assert err <= 1e-6 * scale, (name, err)
