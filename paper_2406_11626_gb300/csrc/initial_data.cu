@@ -27,6 +27,7 @@ struct ccz4_idsolver {
   cudaGraphExec_t exec; // `exec_check` sweeps, or NULL
   int exec_check;
   double omega;         // relaxation factor
+  double *gwt;          // [n_shell][6] 1/r ghost weights of the boundary-shell cells
 };
 
 namespace {
@@ -87,6 +88,14 @@ __global__ void __launch_bounds__(ID_THREADS) setup_kernel(int n, double L, doub
   psi[c] = s;
 }
 
+// Weight r_cell / r_ghost of the 1/r fall-off ghost at index o along axis d
+// of the cell at X (radius rc).
+__device__ __forceinline__ double ghost_weight(double L, double h, const double X[3], double rc, int d, int o) {
+  double g[3] = {X[0], X[1], X[2]};
+  g[d] = cell_coord(L, h, o);
+  return rc / sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+}
+
 // Laplacian neighbour sum of a cell on the boundary of the grid, where
 // one or more neighbours are 1/r ghosts; adds the ghosts' weights
 // r_cell / r_ghost to *ghost_w. Kept out of line so that the interior cells
@@ -106,9 +115,7 @@ __device__ __noinline__ double boundary_sum(int n, double L, double h, const dou
       if (o >= 0 && o < n) {
         s += u[c + side * st[d]];
       } else {
-        double g[3] = {X[0], X[1], X[2]};
-        g[d] = cell_coord(L, h, o);
-        const double w = rc / sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        const double w = ghost_weight(L, h, X, rc, d, o);
         s += uc * w;
         gw += w;
       }
@@ -132,63 +139,112 @@ __device__ __forceinline__ double neighbour_sum(int n, double L, double h, const
 
 // Threads of one half-sweep: the interior cells of the colour first, then
 // every cell of the boundary shell (those of the other colour return). The
-// split keeps the out-of-line ghost path off the warps of interior cells
-// (with rows of n/2 cells of a colour nearly every warp would otherwise
-// hold a boundary cell).
+// split keeps the boundary path off the warps of interior cells (with rows
+// of n/2 cells of a colour nearly every warp would otherwise hold a
+// boundary cell).
 __host__ __device__ inline int sweep_interior_threads(int n) {
   const int m = n - 2;
   return m > 0 ? ((m + 1) / 2) * m * m : 0;
 }
-__host__ __device__ inline int sweep_threads(int n) {
+__host__ __device__ inline int shell_cells(int n) {
   const int m = n - 2 > 0 ? n - 2 : 0;
-  return sweep_interior_threads(n) + (n * n * n - m * m * m);
+  return n * n * n - m * m * m;
+}
+__host__ __device__ inline int sweep_threads(int n) { return sweep_interior_threads(n) + shell_cells(n); }
+
+// Cell (i, j, k) of boundary-shell index b < shell_cells(n): the planes
+// k = 0 and k = n-1, then per interior k the rows j = 0 and j = n-1, then
+// the cells i = 0 and i = n-1 of the interior rows.
+__device__ __forceinline__ void shell_cell(int n, int b, int &i, int &j, int &k) {
+  const int n2 = n * n, m = n - 2;
+  if (b < 2 * n2) {
+    k = b < n2 ? 0 : n - 1;
+    j = (b % n2) / n;
+    i = b % n;
+    return;
+  }
+  const int per = 2 * n + 2 * m, b2 = b - 2 * n2;
+  k = 1 + b2 / per;
+  const int r = b2 % per;
+  if (r < 2 * n) {
+    j = r < n ? 0 : n - 1;
+    i = r % n;
+  } else {
+    j = 1 + (r - 2 * n) / 2;
+    i = ((r - 2 * n) & 1) ? n - 1 : 0;
+  }
+}
+
+// Ghost weights of the shell cells, w[6 b + 2 d + (side > 0)] for the
+// neighbour on axis d and side -1 / +1 (0 where that neighbour is a cell):
+// they depend on the grid only, so the sweeps read them instead of taking
+// roots and divisions.
+__global__ void __launch_bounds__(ID_THREADS) ghost_table_kernel(int n, double L, double h, double *w) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= shell_cells(n)) return;
+  int i, j, k;
+  shell_cell(n, b, i, j, k);
+  const int I[3] = {i, j, k};
+  const double X[3] = {cell_coord(L, h, i), cell_coord(L, h, j), cell_coord(L, h, k)};
+  const double rc = sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+  for (int d = 0; d < 3; ++d)
+    for (int side = 0; side < 2; ++side) {
+      const int o = I[d] + (side ? 1 : -1);
+      w[6 * b + 2 * d + side] = (o >= 0 && o < n) ? 0.0 : ghost_weight(L, h, X, rc, d, o);
+    }
 }
 
 // One half-sweep: the cells with i + j + k + color even take one Newton
 // step of the discrete Hamiltonian constraint, over-relaxed by omega.
-__global__ void __launch_bounds__(ID_THREADS) sweep_kernel(int n, double L, double h, double ih2, int color,
-                                                            double omega, const double *__restrict__ aa,
-                                                            const double *__restrict__ psi, double *u) {
+__global__ void __launch_bounds__(ID_THREADS) sweep_kernel(int n, double ih2, int color, double omega,
+                                                            const double *__restrict__ aa,
+                                                            const double *__restrict__ psi,
+                                                            const double *__restrict__ gwt, double *u) {
   // 32-bit index arithmetic (n <= 1024)
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int n_int = sweep_interior_threads(n);
-  const int m = n - 2;
-  int i, j, k;
+  const long long nn = (long long)n * n;
+  double uc, s, gw;
+  long long c;
   if (q < n_int) {
-    const int half = (m + 1) / 2;
+    const int m = n - 2, half = (m + 1) / 2;
     const int i2 = q % half;
-    j = (q / half) % m + 1;
-    k = q / (half * m) + 1;
-    i = 1 + 2 * i2 + ((1 + j + k + color) & 1);
+    const int j = (q / half) % m + 1;
+    const int k = q / (half * m) + 1;
+    const int i = 1 + 2 * i2 + ((1 + j + k + color) & 1);
     if (i >= n - 1) return;
+    c = ((long long)k * n + j) * n + i;
+    uc = u[c];
+    s = ((u[c - 1] + u[c + 1]) + (u[c - n] + u[c + n])) + (u[c - nn] + u[c + nn]);
+    gw = 0.0;
   } else {
-    // boundary shell: the planes k = 0 and k = n-1, then per interior k the
-    // rows j = 0 and j = n-1, then the cells i = 0 and i = n-1 of the
-    // interior rows
-    const int b = q - n_int, n2 = n * n;
-    if (b < 2 * n2) {
-      k = b < n2 ? 0 : n - 1;
-      j = (b % n2) / n;
-      i = b % n;
-    } else {
-      const int per = 2 * n + 2 * m, b2 = b - 2 * n2;
-      k = 1 + b2 / per;
-      if (k >= n - 1) return;
-      const int r = b2 % per;
-      if (r < 2 * n) {
-        j = r < n ? 0 : n - 1;
-        i = r % n;
-      } else {
-        j = 1 + (r - 2 * n) / 2;
-        i = ((r - 2 * n) & 1) ? n - 1 : 0;
-      }
-    }
+    const int b = q - n_int;
+    if (b >= shell_cells(n)) return;
+    int i, j, k;
+    shell_cell(n, b, i, j, k);
     if ((i + j + k + color) & 1) return;
+    c = ((long long)k * n + j) * n + i;
+    uc = u[c];
+    // the same terms in the same order as boundary_sum, the ghost weights
+    // from the table
+    const int I[3] = {i, j, k};
+    const long long st[3] = {1, n, nn};
+    s = 0.0;
+    gw = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int o = I[d] + (side ? 1 : -1);
+        if (o >= 0 && o < n) {
+          s += u[c + (side ? st[d] : -st[d])];
+        } else {
+          const double w = __ldg(gwt + 6 * b + 2 * d + side);
+          s += uc * w;
+          gw += w;
+        }
+      }
   }
-  const long long c = ((long long)k * n + j) * n + i;
-  const double uc = u[c];
-  double gw;
-  const double s = neighbour_sum(n, L, h, u, i, j, k, uc, &gw);
   const double a = __ldg(aa + c);
   const double iq = recip(__ldg(psi + c) + uc);
   const double iq2 = iq * iq, iq4 = iq2 * iq2;
@@ -332,7 +388,7 @@ cudaError_t launch_sweeps(const ccz4_idsolver *s, int n_sweeps, cudaStream_t st)
   const double ih2 = 1.0 / (s->h * s->h);
   for (int k = 0; k < n_sweeps; ++k)
     for (int color = 0; color < 2; ++color) {
-      sweep_kernel<<<grid, ID_THREADS, 0, st>>>(n, s->L, s->h, ih2, color, s->omega, s->aa, s->psi, s->u);
+      sweep_kernel<<<grid, ID_THREADS, 0, st>>>(n, ih2, color, s->omega, s->aa, s->psi, s->gwt, s->u);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
@@ -360,6 +416,7 @@ static void id_release(ccz4_idsolver *s) {
   cudaFree(s->psi);
   cudaFree(s->partial);
   cudaFree(s->dev_max);
+  cudaFree(s->gwt);
   cudaFreeHost(s->host_max);
   free(s);
 }
@@ -386,6 +443,7 @@ extern "C" ccz4_status ccz4_id_create(int n, double L, ccz4_idsolver **out) {
             cudaMalloc(&s->psi, sizeof(double) * cells) == cudaSuccess &&
             cudaMalloc(&s->partial, sizeof(double) * (size_t)s->blocks) == cudaSuccess &&
             cudaMalloc(&s->dev_max, sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&s->gwt, sizeof(double) * 6 * (size_t)shell_cells(n)) == cudaSuccess &&
             cudaMallocHost(&s->host_max, sizeof(double)) == cudaSuccess;
   if (!ok) {
     set_error("id_create: device allocation failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -395,7 +453,9 @@ extern "C" ccz4_status ccz4_id_create(int n, double L, ccz4_idsolver **out) {
   cudaMemset(s->u, 0, sizeof(double) * cells);
   cudaMemset(s->aa, 0, sizeof(double) * cells);
   cudaMemset(s->psi, 0, sizeof(double) * cells);
-  cudaError_t e = cudaDeviceSynchronize();
+  ghost_table_kernel<<<(shell_cells(n) + ID_THREADS - 1) / ID_THREADS, ID_THREADS>>>(n, L, s->h, s->gwt);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     set_error("id_create: %s", cudaGetErrorString(e));
     id_release(s);

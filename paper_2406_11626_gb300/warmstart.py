@@ -252,8 +252,8 @@ def evaluate(mlp, draws, n, L, tol=1e-10, check=100, max_sweeps=2000000, omega=1
     return np.array(out)
 
 
-def run_experiment(n=96, L=16.0, n_train=2000, n_test=200, steps=20000, batch=65536, lr=1e-3, tol=1e-10,
-                   check=20, seed=0, omega=None, gs_draws=10, log=print, lr_final=1e-5):
+def run_experiment(n=96, L=16.0, n_train=2000, n_test=200, steps=80000, batch=65536, lr=1e-3, tol=1e-10,
+                   check=20, seed=0, omega=None, gs_draws=10, log=print, lr_final=None):
     """The whole experiment; returns a JSON-ready report."""
     import torch
     draws = sobol_draws(n_train + n_test, seed=seed)
@@ -320,10 +320,11 @@ def main(argv=None):
     ap.add_argument("--L", type=float, default=16.0)
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--test", type=int, default=200)
-    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--steps", type=int, default=80000)
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--lr-final", type=float, default=1e-5, help="end of the cosine learning-rate decay")
+    ap.add_argument("--lr-final", type=float, default=None,
+                    help="end of a cosine learning-rate decay (default: constant rate)")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--omega", type=float, default=None,
                     help="relaxation factor (default: the fastest of a short scan; 1 = Gauss-Seidel)")

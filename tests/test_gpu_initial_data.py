@@ -25,11 +25,12 @@ BINARY = ([0.45, 0.55], [(-1.3, 0.05, 0.0), (1.3, -0.05, 0.02)], [(0.0, -0.15, 0
           [(0.0, 0.0, 0.2), (0.05, 0.0, 0.1)])
 
 
-@pytest.mark.parametrize("n,L,omega", [(16, 4.0, 1.0), (15, 3.5, 1.0), (16, 4.0, 1.7)])
+@pytest.mark.parametrize("n,L,omega", [(16, 4.0, 1.0), (15, 3.5, 1.0), (16, 4.0, 1.7), (2, 4.0, 1.0), (3, 3.5, 1.3)])
 def test_sweeps_and_residual_match_the_oracle(n, L, omega):
     """Odd and even n (the colour mapping of odd rows), plain and
-    over-relaxed; 40 sweeps from a non-zero guess, then the residual of
-    every cell."""
+    over-relaxed; grids with no interior cell (n = 2) and a single one
+    (n = 3), where the boundary-shell threads do all or nearly all of the
+    work; 40 sweeps from a non-zero guess, then the residual of every cell."""
     from paper_2406_11626_gb300 import initial_data as ID
     gB, oB = _pair(*BINARY)
     s = ID.Solver(n, L)
