@@ -53,8 +53,10 @@ def parse_args():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--workload", default="puncture144", choices=["puncture144", "puncture3level", "binary", "mid", "small"],
-                    help="the same physics on fewer points, for profiler captures: mid = 90^3 (10^3 patches), small = 54^3 (6^3 patches)")
+    ap.add_argument("--workload", default="puncture144",
+                    choices=["puncture144", "puncture3level", "binary", "mid", "small", "mesh-mid"],
+                    help="the same physics on fewer points, for profiler captures: mid = 90^3 (10^3 patches), "
+                         "small = 54^3 (6^3 patches), mesh-mid = two levels (2240 patches)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     return ap.parse_args()
 
@@ -120,7 +122,7 @@ def oracle_sample_config(workload="puncture144"):
     three-level workload, those 4^3 level-0 patches with the central 2^3
     refined once and one level-1 patch refined again (307 patches)."""
     from paper_2406_11626_gb300 import inputs as I
-    if workload in ("puncture3level", "binary"):
+    if workload in ("puncture3level", "binary", "mesh-mid"):
         # the binary uses the same multi-level sample: the oracle's rate per
         # point-stage does not depend on the data
         return I.multilevel_puncture_config(n_side=4, half_width=2.0,
@@ -191,6 +193,10 @@ def workload_config(g, precision="fp64", K=None, workload="puncture144"):
     elif workload == "mid":
         cfg = I.single_puncture_config(n_side=10, half_width=5.0)
         name = "single puncture M=1, [-5,5]^3, 10^3 patches of 9^3 (90^3 points), profiling case"
+    elif workload == "mesh-mid":
+        cfg = I.multilevel_puncture_config(n_side=8, half_width=4.0, boxes=[((2, 2, 2), (6, 6, 6))])
+        name = ("single puncture M=1 on 2 static ratio-3 levels: [-4,4]^3 as 8^3 patches of 9^3 (dx 1/9), "
+                "central 4^3 refined to 12^3 patches (dx 1/27): 2240 patches, profiling case")
     elif workload == "binary":
         cfg = I.binary_puncture_config()
         name = ("rotating binary puncture: bare masses 0.487 at x = -3, +3, momenta (0, -+0.0934, 0), no spin, "
@@ -258,6 +264,8 @@ def bench_config(args):
         return I.single_puncture_config(n_side=6, half_width=3.0)
     if args.workload == "mid":
         return I.single_puncture_config(n_side=10, half_width=5.0)
+    if args.workload == "mesh-mid":
+        return I.multilevel_puncture_config(n_side=8, half_width=4.0, boxes=[((2, 2, 2), (6, 6, 6))])
     if args.workload == "puncture3level":
         return I.multilevel_puncture_config()
     if args.workload == "binary":

@@ -189,8 +189,11 @@ __host__ __device__ __forceinline__ D fdkl(const Nbhd &N, int v, int k, int l, c
   return k == l ? fd2<D>(N, v, N.st[k], C.c2) : fd11<D, D>(N, v, N.st[k], N.st[l], C.c3);
 }
 
+// Kreiss-Oliger sum of field v over the three axes, without its factor
+// eps / (64 dx): the caller applies that factor in the fused multiply-add
+// that adds the dissipation to the right-hand side.
 template <class D>
-__host__ __device__ __forceinline__ D ko_sum(const Nbhd &N, int v, const D &cko) {
+__host__ __device__ __forceinline__ D ko_sum(const Nbhd &N, int v) {
   const int s0 = N.st[0], s1 = N.st[1], s2 = N.st[2];
   const D p1 = (ld<D>(N, v, s0) + ld<D>(N, v, -s0)) + (ld<D>(N, v, s1) + ld<D>(N, v, -s1)) +
                (ld<D>(N, v, s2) + ld<D>(N, v, -s2));
@@ -198,7 +201,7 @@ __host__ __device__ __forceinline__ D ko_sum(const Nbhd &N, int v, const D &cko)
                (ld<D>(N, v, 2 * s2) + ld<D>(N, v, -2 * s2));
   const D p3 = (ld<D>(N, v, 3 * s0) + ld<D>(N, v, -3 * s0)) + (ld<D>(N, v, 3 * s1) + ld<D>(N, v, -3 * s1)) +
                (ld<D>(N, v, 3 * s2) + ld<D>(N, v, -3 * s2));
-  return fmaT(D(-60.0), ld<D>(N, v, 0), fmaT(D(15.0), p1, fmaT(D(-6.0), p2, p3))) * cko;
+  return fmaT(D(-60.0), ld<D>(N, v, 0), fmaT(D(15.0), p1, fmaT(D(-6.0), p2, p3)));
 }
 
 // Pure second derivatives d_x d_x, d_y d_y, d_z d_z of field v and its
@@ -228,7 +231,7 @@ __host__ __device__ __forceinline__ void pure2_ko(const Nbhd &N, int v, const St
     }
   }
   const D p1 = s1[0] + s1[1] + s1[2], p2 = s2[0] + s2[1] + s2[2], p3 = s3[0] + s3[1] + s3[2];
-  ko = fmaT(D(-60.0), q0, fmaT(D(15.0), p1, fmaT(D(-6.0), p2, p3))) * C.cko;
+  ko = fmaT(D(-60.0), q0, fmaT(D(15.0), p1, fmaT(D(-6.0), p2, p3)));  // unscaled, as ko_sum
 }
 
 // All six second derivatives of field v, in the order xx, xy, xz, yy, yz, zz,
@@ -603,13 +606,13 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
 #pragma unroll
       for (int j = i; j < 3; ++j) {
         const int c = S6(i, j);
-        sink(GXX + c, cvt<D>((advg[c] + (Xg[i][j] + Xg[j][i])) + fmaT(g[c], sg, -al2 * A[c])) + kog[c]);
+        sink(GXX + c, fmaT(C.cko, kog[c], cvt<D>((advg[c] + (Xg[i][j] + Xg[j][i])) + fmaT(g[c], sg, -al2 * A[c]))));
         R advA = R(0.0);
 #pragma unroll
         for (int k = 0; k < 3; ++k) advA = fmaT(be[k], fd1o<D, R>(N, AXX + c, N.st[k], CR.c1), advA);
         const R rA = (advA + (XA[i][j] + XA[j][i])) +
                      fmaT(ph2al, RZ[c], fmaT(-ph2, DDa[c], fmaT(g[c], sA1, fmaT(A[c], sA2, -al2 * AgA[c]))));
-        sink(AXX + c, cvt<D>(rA) + ko_sum<D>(N, AXX + c, C.cko));
+        sink(AXX + c, fmaT(C.cko, ko_sum<D>(N, AXX + c), cvt<D>(rA)));
       }
   }
   CCZ4_MARK("rhs g A");
@@ -617,8 +620,8 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
   // ---- scalars ---------------------------------------------------------------------------------
   const R gK = (P.slicing == CCZ4_SLICING_ONE_PLUS_LOG) ? al2 : al * al;  // alpha^2 g(alpha)
   const R dP[3] = {cvt<R>(dPD[0]), cvt<R>(dPD[1]), cvt<R>(dPD[2])};
-  sink(ALPHA, cvt<D>(fmaT(be[0], da[0], fmaT(be[1], da[1], be[2] * da[2])) - gK * (Kc - P.K0)) + koA);
-  sink(PHI, cvt<D>(fmaT(be[0], dP[0], fmaT(be[1], dP[1], be[2] * dP[2])) + third * ph * fmaT(al, Kt, -trB)) + koP);
+  sink(ALPHA, fmaT(C.cko, koA, cvt<D>(fmaT(be[0], da[0], fmaT(be[1], da[1], be[2] * da[2])) - gK * (Kc - P.K0))));
+  sink(PHI, fmaT(C.cko, koP, cvt<D>(fmaT(be[0], dP[0], fmaT(be[1], dP[1], be[2] * dP[2])) + third * ph * fmaT(al, Kt, -trB))));
   R dK[3], dT[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -627,10 +630,10 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
   }
   const R advK = fmaT(be[0], dK[0], fmaT(be[1], dK[1], be[2] * dK[2]));
   const R advT = fmaT(be[0], dT[0], fmaT(be[1], dT[1], be[2] * dT[2]));
-  sink(KTR, cvt<D>(advK - lapal + al * (RpZ + fmaT(Kt, Kc, -P.k1a * Th))) + ko_sum<D>(N, KTR, C.cko));
+  sink(KTR, fmaT(C.cko, ko_sum<D>(N, KTR), cvt<D>(advK - lapal + al * (RpZ + fmaT(Kt, Kc, -P.k1a * Th)))));
   const R ZA = R(0.5) * ph2 * fmaT(dGam[0], da[0], fmaT(dGam[1], da[1], dGam[2] * da[2]));  // Z^i A_i
-  sink(THETA, cvt<D>(advT + al * fmaT(P.e2h, RpZ + fmaT(twothird * Kt, Kt, -AA), -Th * fmaT(Kt, P.c, P.k1b)) - ZA) +
-                  ko_sum<D>(N, THETA, C.cko));
+  sink(THETA, fmaT(C.cko, ko_sum<D>(N, THETA),
+                   cvt<D>(advT + al * fmaT(P.e2h, RpZ + fmaT(twothird * Kt, Kt, -AA), -Th * fmaT(Kt, P.c, P.k1b)) - ZA)));
   CCZ4_MARK("rhs scalars");
 
   // ---- d_t Gamma-hat^i, gauge --------------------------------------------------------------------
@@ -678,23 +681,23 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
     t = fmaT(zc, dGam[i], t);
     t = fmaT(k3h, ZB, t);
     dbK[i] = t - GB;  // d_t Gamma-hat^i - beta^k d_k Gamma-hat^i
-    sink(GHX + i, cvt<D>(advGh[i] + dbK[i]) + ko_sum<D>(N, GHX + i, C.cko));
+    sink(GHX + i, fmaT(C.cko, ko_sum<D>(N, GHX + i), cvt<D>(advGh[i] + dbK[i])));
   }
   if (P.shift == CCZ4_SHIFT_GAMMA_DRIVER) {
     const R bb[3] = {cvt<R>(ld<D>(N, BBX, 0)), cvt<R>(ld<D>(N, BBY, 0)), cvt<R>(ld<D>(N, BBZ, 0))};
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      sink(BETAX + i, cvt<D>(fmaT(be[0], dB[0][i], fmaT(be[1], dB[1][i], fmaT(be[2], dB[2][i], P.f * bb[i])))) + koB[i]);
+      sink(BETAX + i, fmaT(C.cko, koB[i], cvt<D>(fmaT(be[0], dB[0][i], fmaT(be[1], dB[1][i], fmaT(be[2], dB[2][i], P.f * bb[i]))))));
       R advb = fmaT(-P.eta, bb[i], dbK[i]);
 #pragma unroll
       for (int k = 0; k < 3; ++k) advb = fmaT(be[k], fd1o<D, R>(N, BBX + i, N.st[k], CR.c1), advb);
-      sink(BBX + i, cvt<D>(advb) + ko_sum<D>(N, BBX + i, C.cko));
+      sink(BBX + i, fmaT(C.cko, ko_sum<D>(N, BBX + i), cvt<D>(advb)));
     }
   } else {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      sink(BETAX + i, D(0.0) + koB[i]);
-      sink(BBX + i, D(0.0) + ko_sum<D>(N, BBX + i, C.cko));
+      sink(BETAX + i, C.cko * koB[i]);
+      sink(BBX + i, C.cko * ko_sum<D>(N, BBX + i));
     }
   }
   CCZ4_MARK("rhs gamma-hat gauge");

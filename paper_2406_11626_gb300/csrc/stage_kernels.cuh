@@ -33,6 +33,13 @@
 #ifndef CCZ4_INTERIOR_MIN_BLOCKS_MIXED
 #define CCZ4_INTERIOR_MIN_BLOCKS_MIXED 5
 #endif
+// Register spills of the stage kernel go to shared memory first (the
+// kernel uses none otherwise; ptxas places 104 bytes per thread there) and
+// only then to local memory. Measured on GB300: mixed path 1 % faster per
+// step, FP64 path unchanged. Set to 0 to spill to local memory only.
+#ifndef CCZ4_SMEM_SPILL
+#define CCZ4_SMEM_SPILL 1
+#endif
 
 namespace ccz4 {
 
@@ -183,6 +190,9 @@ template <int MODE, class R, bool MESH, bool QUEUE>
 __global__ void __launch_bounds__(128, StageBlocks<R>::value) interior_kernel(GridView g, Phys<R> P, LevelCoef<R> LC,
                                                           const double *__restrict__ tile,
                                                           const double *__restrict__ mix, StageArgs a) {
+#if CCZ4_SMEM_SPILL
+  asm volatile(".pragma \"enable_smem_spilling\";");
+#endif
   if (!QUEUE) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < g.n_points) stage_point<MODE, R, MESH>(g, P, LC, tile, mix, a, i);
