@@ -448,7 +448,8 @@ def run_gb300(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f64 state + f32 algebra",
-        "data": "synthetic (Brill-Lindquist puncture data generated in closed form)",
+        "data": ("synthetic (Bowen-York binary data from the initial-data solve)" if args.workload == "binary"
+                 else "synthetic (Brill-Lindquist puncture data generated in closed form)"),
         "config": workload_config(g, args.precision, K, args.workload),
         "stage_kernel_ms": sum(stage_ms) / len(stage_ms),
         "roofline": roof,
