@@ -317,7 +317,13 @@ typedef struct {
    level out of range, a level-0 slot missing or listed twice, a refined
    patch without its parent or with an incomplete set of siblings, or a
    halo point whose interpolation sources are not interior points of the
-   level below. */
+   level below. The halo fill evaluates each patch's coarse-to-fine
+   interpolations separably (the distinct x-interpolations of the patch,
+   then the distinct y-interpolations of their pairs, then one
+   z-interpolation per halo point, all in shared memory; the same products
+   and sums, so the same values); with the environment variable
+   CCZ4_MESH_INTERP_BY_ENTRY=1 set when the mesh is created it evaluates
+   them point by point instead. */
 ccz4_status ccz4_alloc_mesh(const ccz4_mesh_desc *desc, ccz4_grid **out);
 
 /* Number of levels and of points of leaf patches (the norm's point count). */

@@ -86,6 +86,11 @@ static void free_all(ccz4_grid *g) {
   cudaFree(g->d_src);
   cudaFree(g->d_interp);
   cudaFree(g->d_ibeg);
+  cudaFree(g->d_xjob);
+  cudaFree(g->d_yjob);
+  cudaFree(g->d_zjob);
+  cudaFree(g->d_xbeg);
+  cudaFree(g->d_ybeg);
   cudaFree(g->d_plev);
   cudaFree(g->d_leaf);
   for (int l = 0; l < CCZ4_MAX_LEVELS; ++l) {
@@ -158,6 +163,10 @@ extern "C" ccz4_status ccz4_alloc_mesh(const ccz4_mesh_desc *m, ccz4_grid **out)
   MeshPlan plan;
   ccz4_status st = plan_mesh(m, true, plan);
   if (st != CCZ4_OK) return st;
+  // separable coarse-to-fine interpolation unless CCZ4_MESH_INTERP_BY_ENTRY=1
+  const char *by_entry = getenv("CCZ4_MESH_INTERP_BY_ENTRY");
+  const long long T = m->p + 2 * HALO;
+  plan_separable(plan, (by_entry && by_entry[0] == '1') ? 0 : T * T * T);
   ccz4_grid_desc d;
   d.p = m->p;
   d.n_patches = m->n_patches;
@@ -273,6 +282,11 @@ static ccz4_status create_grid(const ccz4_grid_desc *d, const std::vector<int> &
     ok = upload_table(&g->d_src, mesh->src.data(), mesh->src.size()) &&
          upload_table(&g->d_interp, mesh->interp.data(), mesh->interp.size()) &&
          upload_table(&g->d_ibeg, mesh->ibeg.data(), mesh->ibeg.size()) &&
+         upload_table(&g->d_xjob, mesh->xjob.data(), mesh->xjob.size()) &&
+         upload_table(&g->d_yjob, mesh->yjob.data(), mesh->yjob.size()) &&
+         upload_table(&g->d_zjob, mesh->zjob.data(), mesh->zjob.size()) &&
+         upload_table(&g->d_xbeg, mesh->xbeg.data(), mesh->xbeg.size()) &&
+         upload_table(&g->d_ybeg, mesh->ybeg.data(), mesh->ybeg.size()) &&
          upload_table(&g->d_plev, mesh->level.data(), mesh->level.size()) &&
          upload_table(&g->d_leaf, mesh->leaf.data(), mesh->leaf.size());
     for (int l = 1; l < mesh->n_levels && ok; ++l) {
@@ -300,6 +314,11 @@ static ccz4_status create_grid(const ccz4_grid_desc *d, const std::vector<int> &
   v.src = g->d_src;
   v.interp = g->d_interp;
   v.ibeg = g->d_ibeg;
+  v.xjob = g->d_xjob;
+  v.yjob = g->d_yjob;
+  v.zjob = g->d_zjob;
+  v.xbeg = g->d_xbeg;
+  v.ybeg = g->d_ybeg;
   v.plev = g->d_plev;
   v.leaf = g->d_leaf;
   *out = g;

@@ -45,6 +45,24 @@ struct InterpEntry {
   int t;
 };
 
+// Separable form of a patch's interpolations (the same values, rounded the
+// same way): the distinct x-interpolations of the patch (value
+// rx ? (1-w) q(s0) + w q(s1) : q(s0), w = rx/3), then the distinct
+// y-interpolations of pairs of x results (packed: xa | xb << 14 | ry << 28,
+// indices into the patch's x results), then one z-interpolation per
+// interpolated tile point (packed: ya | yb << 14 | rz << 28, indices into
+// the y results, and the tile point). A patch whose x and y results do not
+// fit in its tile's shared memory has no jobs and is interpolated entry by
+// entry.
+struct XJob {
+  int s0, s1, rx;
+};
+constexpr int JOB_BITS = 14;  // local indices < 2^14 > (18 + 6)^3
+struct ZJob {
+  int yab;  // ya | yb << 14 | rz << 28
+  int t;
+};
+
 // The mixed path keeps the mixed derivatives it uses in FP32 -- those of
 // g~ (slots 0..17) and beta (slots 21..29) -- as FP32 in the first 27 float
 // slots of the mixed-derivative buffer: FP32 slot of slot s, or -1 for the
@@ -75,6 +93,10 @@ struct GridView {
   const int *src;              // [n_patches][T3] tile sources: >= 0 index, <= -2 entry -(s+2)
   const InterpEntry *interp;   // interpolated tile points
   const int *ibeg;             // [n_patches + 1] first entry of each patch in interp
+  const XJob *xjob;            // separable interpolation (see XJob): x jobs, patch after patch
+  const int *yjob;             //   y jobs
+  const ZJob *zjob;            //   z jobs, one per entry of interp
+  const int *xbeg, *ybeg;      //   [n_patches + 1] first x / y job of each patch
   const int *plev;             // [n_patches] level of each patch
   const unsigned char *leaf;   // [n_patches] 1 if the patch has no children
   double ldx[MAX_LEVELS];      // spacing of each level (ldx[0] = dx)
@@ -166,6 +188,10 @@ struct ccz4_grid {
   int *d_src;
   ccz4::InterpEntry *d_interp;
   int *d_ibeg;
+  ccz4::XJob *d_xjob;
+  int *d_yjob;
+  ccz4::ZJob *d_zjob;
+  int *d_xbeg, *d_ybeg;
   int *d_plev;
   unsigned char *d_leaf;
   int *d_rpar[CCZ4_MAX_LEVELS], *d_rkid[CCZ4_MAX_LEVELS];

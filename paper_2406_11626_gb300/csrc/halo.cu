@@ -97,6 +97,12 @@ __device__ __forceinline__ double interp_value(const int (&c)[8], int rx, int ry
   return rz ? __dadd_rn(__dmul_rn(pw(rz, 0), u[0]), __dmul_rn(pw(rz, 1), u[1])) : u[0];
 }
 
+// One linear map of the interpolation between a and b for remainder r, the
+// product and the sum each rounded on its own; r = 0: a.
+__device__ __forceinline__ double lerp3(int r, double a, double b) {
+  return r ? __dadd_rn(__dmul_rn(pw(r, 0), a), __dmul_rn(pw(r, 1), b)) : a;
+}
+
 // MESH: the tile sources come from the host-built table of a refined mesh
 // (and may be interpolations); otherwise they are resolved here. F32W: FP32
 // weights for the mixed derivatives (see mixed_out).
@@ -121,12 +127,14 @@ __global__ void __launch_bounds__(FILL_THREADS, CCZ4_FILL_MIN_BLOCKS) fill_halos
     // refined mesh: sources resolved once on the host
     const int *sp = g.src + (long long)n * T3;
     for (int t = threadIdx.x; t < T3; t += blockDim.x) idx[t] = __ldg(sp + t);
-    // The patch's interpolated halo points, one entry per thread, all fields
-    // at once: the entry is read once and the fields' corner loads are
-    // independent. The fields that need mixed derivatives read these values
-    // back from the tile after the barrier below.
+    // A patch without separable tables: its interpolated halo points, one
+    // entry per thread, all fields at once (the entry is read once and the
+    // fields' corner loads are independent). The fields that need mixed
+    // derivatives read these values back from the tile after the barrier
+    // below.
     const int e1 = __ldg(g.ibeg + n + 1);
-    for (int e = __ldg(g.ibeg + n) + threadIdx.x; e < e1; e += FILL_THREADS) {
+    const bool by_entry = __ldg(g.xbeg + n + 1) == __ldg(g.xbeg + n);
+    for (int e = by_entry ? __ldg(g.ibeg + n) + (int)threadIdx.x : e1; e < e1; e += FILL_THREADS) {
       const InterpEntry *ep = g.interp + e;
       int c[8];
 #pragma unroll
@@ -149,10 +157,43 @@ __global__ void __launch_bounds__(FILL_THREADS, CCZ4_FILL_MIN_BLOCKS) fill_halos
   __syncthreads();
   const long long p3 = (long long)p * p * p;
   const long long pbase = (long long)n * p3;
+  // separable interpolation of this patch's halo points (see XJob)
+  int e0 = 0, e1 = 0, xb0 = 0, nx = 0, yb0 = 0, ny = 0;
+  if (MESH) {
+    e0 = __ldg(g.ibeg + n);
+    e1 = __ldg(g.ibeg + n + 1);
+    xb0 = __ldg(g.xbeg + n);
+    nx = __ldg(g.xbeg + n + 1) - xb0;
+    yb0 = __ldg(g.ybeg + n);
+    ny = __ldg(g.ybeg + n + 1) - yb0;
+  }
+  constexpr int JM = (1 << JOB_BITS) - 1;
   for (int v = 0; v < NV; ++v) {
     const double *sv = src + v * g.S;
     double *tv = tile + ((long long)v * g.n_patches + n) * g.T3;
     const int slot = mix_slot(v);
+    if (MESH && nx > 0) {
+      // x, then y, then z: the x and y results of the patch in the tile's
+      // shared memory (host-checked to fit), the z results to the tile
+      double *xv = ts, *yv = ts + nx;
+      for (int j = threadIdx.x; j < nx; j += FILL_THREADS) {
+        const XJob *J = g.xjob + xb0 + j;
+        const int rx = __ldg(&J->rx);
+        const double q0 = __ldg(sv + __ldg(&J->s0));
+        xv[j] = rx ? lerp3(rx, q0, __ldg(sv + __ldg(&J->s1))) : q0;
+      }
+      __syncthreads();
+      for (int j = threadIdx.x; j < ny; j += FILL_THREADS) {
+        const int k = __ldg(g.yjob + yb0 + j);
+        yv[j] = lerp3((k >> (2 * JOB_BITS)) & 3, xv[k & JM], xv[(k >> JOB_BITS) & JM]);
+      }
+      __syncthreads();
+      for (int e = e0 + threadIdx.x; e < e1; e += FILL_THREADS) {
+        const int k = __ldg(&g.zjob[e].yab);
+        __stcs(tv + __ldg(&g.zjob[e].t), lerp3((k >> (2 * JOB_BITS)) & 3, yv[k & JM], yv[(k >> JOB_BITS) & JM]));
+      }
+      __syncthreads();  // the gather below overwrites the tile's shared memory
+    }
     // Gather in batches of GATHER_BATCH independent loads per thread, so a
     // field costs a couple of memory latencies rather than one per point.
     for (int t0 = threadIdx.x; t0 < T3; t0 += GATHER_BATCH * FILL_THREADS) {

@@ -337,6 +337,69 @@ cudaError_t launch_restrict(const GridView &g, const int *par, const int *kid, i
   return cudaGetLastError();
 }
 
+// The x jobs of an entry are its (up to four) x-pairs, the y jobs its (up
+// to two) pairs of x results, in the order of the per-entry evaluation, so
+// every job computes the same products and sums as the entry itself.
+void plan_separable(MeshPlan &out, long long T3) {
+  const int n = (int)out.ibeg.size() - 1;
+  out.xjob.clear();
+  out.yjob.clear();
+  out.zjob.assign(out.interp.size(), ZJob{0, 0});
+  out.xbeg.assign((size_t)n + 1, 0);
+  out.ybeg.assign((size_t)n + 1, 0);
+  std::unordered_map<unsigned long long, int> xs;
+  std::unordered_map<int, int> ys;
+  std::vector<XJob> px;
+  std::vector<int> py;
+  for (int m = 0; m < n; ++m) {
+    out.xbeg[m] = (int)out.xjob.size();
+    out.ybeg[m] = (int)out.yjob.size();
+    const int e0 = out.ibeg[m], e1 = out.ibeg[m + 1];
+    if (e1 == e0) continue;
+    xs.clear();
+    ys.clear();
+    px.clear();
+    py.clear();
+    bool fits = true;
+    for (int e = e0; e < e1 && fits; ++e) {
+      const InterpEntry &E = out.interp[e];
+      const int rx = E.r & 3, ry = (E.r >> 2) & 3, rz = (E.r >> 4) & 3;
+      int yi[2] = {0, 0};
+      for (int c = 0; c < (rz ? 2 : 1); ++c) {
+        int xi[2] = {0, 0};
+        for (int b = 0; b < (ry ? 2 : 1); ++b) {
+          const int s0 = E.src[(c * 2 + b) * 2], s1 = rx ? E.src[(c * 2 + b) * 2 + 1] : s0;
+          const unsigned long long key =
+              ((unsigned long long)(unsigned)s0 << 33) | ((unsigned long long)(unsigned)s1 << 2) | (unsigned)rx;
+          auto it = xs.find(key);
+          if (it == xs.end()) {
+            it = xs.emplace(key, (int)px.size()).first;
+            px.push_back(XJob{s0, s1, rx});
+          }
+          xi[b] = it->second;
+        }
+        if (!ry) xi[1] = xi[0];
+        const int key = xi[0] | (xi[1] << JOB_BITS) | (ry << (2 * JOB_BITS));
+        auto it = ys.find(key);
+        if (it == ys.end()) {
+          it = ys.emplace(key, (int)py.size()).first;
+          py.push_back(key);
+        }
+        yi[c] = it->second;
+      }
+      if (!rz) yi[1] = yi[0];
+      out.zjob[e] = ZJob{yi[0] | (yi[1] << JOB_BITS) | (rz << (2 * JOB_BITS)), E.t};
+      fits = (long long)(px.size() + py.size()) <= T3 && px.size() < (1u << JOB_BITS) &&
+             py.size() < (1u << JOB_BITS);
+    }
+    if (!fits) continue;  // interpolated entry by entry
+    out.xjob.insert(out.xjob.end(), px.begin(), px.end());
+    out.yjob.insert(out.yjob.end(), py.begin(), py.end());
+  }
+  out.xbeg[n] = (int)out.xjob.size();
+  out.ybeg[n] = (int)out.yjob.size();
+}
+
 }  // namespace ccz4
 
 using namespace ccz4;

@@ -16,6 +16,10 @@ struct MeshPlan {
   std::vector<int> src;                    // [n_patches][T3] tile sources (if requested)
   std::vector<InterpEntry> interp;         // [n_interp] (if requested), patch after patch
   std::vector<int> ibeg;                   // [n_patches + 1] first entry of each patch (if requested)
+  std::vector<XJob> xjob;                  // separable interpolation tables (if requested)
+  std::vector<int> yjob;
+  std::vector<ZJob> zjob;                  // [n_interp]
+  std::vector<int> xbeg, ybeg;             // [n_patches + 1]
   std::vector<unsigned char> leaf;         // [n_patches]
   std::vector<int> owner0;                 // level-0 slot -> patch
   std::vector<int> rpar[MAX_LEVELS];       // level l >= 1: parents on level l-1
@@ -24,5 +28,9 @@ struct MeshPlan {
 
 // Validates the descriptor and, with want_tables, resolves every tile point.
 ccz4_status plan_mesh(const ccz4_mesh_desc *d, bool want_tables, MeshPlan &out);
+
+// Builds the separable interpolation tables of a plan with tables, for
+// tiles of T3 points.
+void plan_separable(MeshPlan &out, long long T3);
 
 }  // namespace ccz4

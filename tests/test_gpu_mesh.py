@@ -248,6 +248,33 @@ def test_binary_puncture_full_size_sampled_parity():
     assert (np.abs(got - ref) / scale).max() < TOL
 
 
+@pytest.mark.parametrize("name,bc", [("three", "sommerfeld"), ("two", "periodic")])
+def test_separable_interpolation_equals_entry_by_entry(name, bc, monkeypatch):
+    """The halo fill's separable evaluation of the coarse-to-fine
+    interpolations (x, y, z passes sharing their results) gives the same
+    tiles, bit for bit, as the point-by-point evaluation, and so the same
+    states after RK4 steps."""
+    from paper_2406_11626_gb300 import ccz4 as C
+    dx = 0.3
+    gg, _, lev, ijk, origin = mesh_pair(name, bc, dx=dx, shuffle=5)
+    U, G = mesh_state(gg, lev, ijk, origin, dx, bc, seed=4, base="puncture", amp=0.01)
+    dt, P = 0.1 * I.level_spacing(dx, int(np.max(lev)) + 1)[-1], C.make_params(**PUNC)
+    out = []
+    for by_entry in ("0", "1"):
+        monkeypatch.setenv("CCZ4_MESH_INTERP_BY_ENTRY", by_entry)
+        g = C.Grid(gg.p, gg.np, ijk, origin, dx, bc, level=lev)
+        g.upload(U, G)
+        if bc == "sommerfeld":
+            g.upload(U, G, buf="INI")
+        g.fill_halos("U")
+        tiles = g.download("TILE")
+        g.step(P, dt, 2)
+        out.append((tiles, g.download("U")))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1][0], out[1][1][0])
+    np.testing.assert_array_equal(out[0][1][1], out[1][1][1])
+
+
 @pytest.mark.parametrize("mesh", [None, "three"])
 def test_queue_launch_is_bit_identical_to_flat(mesh):
     """The persistent work-queue launch of the stage kernel computes every
