@@ -161,6 +161,15 @@ __host__ __device__ __forceinline__ O fd1o(const Nbhd &N, int v, int s, const O 
   return fmaT(O(8.0), cvt<O>(a), -cvt<O>(b)) * c1;
 }
 
+// The same without the factor 1 / (12 dx), for callers that fold it into
+// a coefficient they apply anyway.
+template <class D, class O>
+__host__ __device__ __forceinline__ O fd1u(const Nbhd &N, int v, int s) {
+  const D a = ld<D>(N, v, s) - ld<D>(N, v, -s);
+  const D b = ld<D>(N, v, 2 * s) - ld<D>(N, v, -2 * s);
+  return fmaT(O(8.0), cvt<O>(a), -cvt<O>(b));
+}
+
 template <class D>
 __host__ __device__ __forceinline__ D fd2(const Nbhd &N, int v, int s, const D &c2) {
   const D s1 = ld<D>(N, v, s) + ld<D>(N, v, -s);
@@ -258,6 +267,19 @@ __host__ __device__ __forceinline__ void second_ko(const Nbhd &N, int v, const S
     dd[1] = cvt<O>(D(N.mixed(m)));
     dd[2] = cvt<O>(D(N.mixed(m + 1)));
     dd[4] = cvt<O>(D(N.mixed(m + 2)));
+  }
+}
+
+// A right-hand side (algebra type R) plus the dissipation eps/(64 dx) times
+// the Kreiss-Oliger sum ko (taken in D): the sum is the differencing and
+// stays in D; its factor and the addition are algebra, done in R.
+template <class D, class R>
+__host__ __device__ __forceinline__ D with_ko(const R &rhs, const D &ko, const StencilCoef<D> &C,
+                                              const StencilCoef<R> &CR) {
+  if constexpr (std::is_same<D, R>::value) {
+    return fmaT(C.cko, ko, rhs);
+  } else {
+    return cvt<D>(fmaT(CR.cko, cvt<R>(ko), rhs));
   }
 }
 
@@ -365,22 +387,28 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
   R Gd[3][6], Gu[3][6], Gc[3];
   R advg[6], Ghdg[6];  // beta^k d_k g~_ij and Gamma-hat^k d_k g~_ij
   {
+    // half the derivatives, so that the 1/2 of G~_kij costs nothing; the
+    // contractions with beta and Gamma-hat take them doubled (all exact
+    // powers of two: the same values as with full derivatives)
+    const R c1h = R(0.5) * CR.c1;
+    const R be2[3] = {be[0] + be[0], be[1] + be[1], be[2] + be[2]};
+    const R Gh2[3] = {Gh[0] + Gh[0], Gh[1] + Gh[1], Gh[2] + Gh[2]};
     R dg[3][6];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int c = 0; c < 6; ++c) dg[k][c] = fd1o<D, R>(N, GXX + c, N.st[k], CR.c1);
+      for (int c = 0; c < 6; ++c) dg[k][c] = fd1o<D, R>(N, GXX + c, N.st[k], c1h);  // (1/2) d_k g~_ij
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j)
-          Gd[k][S6(i, j)] = R(0.5) * (dg[i][S6(j, k)] + dg[j][S6(i, k)] - dg[k][S6(i, j)]);
+          Gd[k][S6(i, j)] = dg[i][S6(j, k)] + dg[j][S6(i, k)] - dg[k][S6(i, j)];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      advg[c] = fmaT(be[0], dg[0][c], fmaT(be[1], dg[1][c], be[2] * dg[2][c]));
-      Ghdg[c] = fmaT(Gh[0], dg[0][c], fmaT(Gh[1], dg[1][c], Gh[2] * dg[2][c]));
+      advg[c] = fmaT(be2[0], dg[0][c], fmaT(be2[1], dg[1][c], be2[2] * dg[2][c]));
+      Ghdg[c] = fmaT(Gh2[0], dg[0][c], fmaT(Gh2[1], dg[1][c], Gh2[2] * dg[2][c]));
     }
   }
 #pragma unroll
@@ -575,6 +603,8 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
   CCZ4_MARK("A contractions");
 
   // ---- d_t g~_ij, d_t A~_ij ---------------------------------------------------------------
+  // beta / (12 dx): the advection of A~ and b takes unscaled first differences
+  const R bec1[3] = {be[0] * CR.c1, be[1] * CR.c1, be[2] * CR.c1};
   R dB[3][3];  // B_k^i = d_k beta^i
 #pragma unroll
   for (int k = 0; k < 3; ++k)
@@ -606,13 +636,13 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
 #pragma unroll
       for (int j = i; j < 3; ++j) {
         const int c = S6(i, j);
-        sink(GXX + c, fmaT(C.cko, kog[c], cvt<D>((advg[c] + (Xg[i][j] + Xg[j][i])) + fmaT(g[c], sg, -al2 * A[c]))));
+        sink(GXX + c, with_ko<D, R>((advg[c] + (Xg[i][j] + Xg[j][i])) + fmaT(g[c], sg, -al2 * A[c]), kog[c], C, CR));
         R advA = R(0.0);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) advA = fmaT(be[k], fd1o<D, R>(N, AXX + c, N.st[k], CR.c1), advA);
+        for (int k = 0; k < 3; ++k) advA = fmaT(bec1[k], fd1u<D, R>(N, AXX + c, N.st[k]), advA);
         const R rA = (advA + (XA[i][j] + XA[j][i])) +
                      fmaT(ph2al, RZ[c], fmaT(-ph2, DDa[c], fmaT(g[c], sA1, fmaT(A[c], sA2, -al2 * AgA[c]))));
-        sink(AXX + c, fmaT(C.cko, ko_sum<D>(N, AXX + c), cvt<D>(rA)));
+        sink(AXX + c, with_ko<D, R>(rA, ko_sum<D>(N, AXX + c), C, CR));
       }
   }
   CCZ4_MARK("rhs g A");
@@ -620,8 +650,9 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
   // ---- scalars ---------------------------------------------------------------------------------
   const R gK = (P.slicing == CCZ4_SLICING_ONE_PLUS_LOG) ? al2 : al * al;  // alpha^2 g(alpha)
   const R dP[3] = {cvt<R>(dPD[0]), cvt<R>(dPD[1]), cvt<R>(dPD[2])};
-  sink(ALPHA, fmaT(C.cko, koA, cvt<D>(fmaT(be[0], da[0], fmaT(be[1], da[1], be[2] * da[2])) - gK * (Kc - P.K0))));
-  sink(PHI, fmaT(C.cko, koP, cvt<D>(fmaT(be[0], dP[0], fmaT(be[1], dP[1], be[2] * dP[2])) + third * ph * fmaT(al, Kt, -trB))));
+  sink(ALPHA, with_ko<D, R>(fmaT(be[0], da[0], fmaT(be[1], da[1], be[2] * da[2])) - gK * (Kc - P.K0), koA, C, CR));
+  sink(PHI, with_ko<D, R>(fmaT(be[0], dP[0], fmaT(be[1], dP[1], be[2] * dP[2])) + third * ph * fmaT(al, Kt, -trB), koP, C,
+                          CR));
   R dK[3], dT[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -630,10 +661,10 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
   }
   const R advK = fmaT(be[0], dK[0], fmaT(be[1], dK[1], be[2] * dK[2]));
   const R advT = fmaT(be[0], dT[0], fmaT(be[1], dT[1], be[2] * dT[2]));
-  sink(KTR, fmaT(C.cko, ko_sum<D>(N, KTR), cvt<D>(advK - lapal + al * (RpZ + fmaT(Kt, Kc, -P.k1a * Th)))));
+  sink(KTR, with_ko<D, R>(advK - lapal + al * (RpZ + fmaT(Kt, Kc, -P.k1a * Th)), ko_sum<D>(N, KTR), C, CR));
   const R ZA = R(0.5) * ph2 * fmaT(dGam[0], da[0], fmaT(dGam[1], da[1], dGam[2] * da[2]));  // Z^i A_i
-  sink(THETA, fmaT(C.cko, ko_sum<D>(N, THETA),
-                   cvt<D>(advT + al * fmaT(P.e2h, RpZ + fmaT(twothird * Kt, Kt, -AA), -Th * fmaT(Kt, P.c, P.k1b)) - ZA)));
+  sink(THETA, with_ko<D, R>(advT + al * fmaT(P.e2h, RpZ + fmaT(twothird * Kt, Kt, -AA), -Th * fmaT(Kt, P.c, P.k1b)) - ZA,
+                            ko_sum<D>(N, THETA), C, CR));
   CCZ4_MARK("rhs scalars");
 
   // ---- d_t Gamma-hat^i, gauge --------------------------------------------------------------------
@@ -681,23 +712,24 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
     t = fmaT(zc, dGam[i], t);
     t = fmaT(k3h, ZB, t);
     dbK[i] = t - GB;  // d_t Gamma-hat^i - beta^k d_k Gamma-hat^i
-    sink(GHX + i, fmaT(C.cko, ko_sum<D>(N, GHX + i), cvt<D>(advGh[i] + dbK[i])));
+    sink(GHX + i, with_ko<D, R>(advGh[i] + dbK[i], ko_sum<D>(N, GHX + i), C, CR));
   }
   if (P.shift == CCZ4_SHIFT_GAMMA_DRIVER) {
     const R bb[3] = {cvt<R>(ld<D>(N, BBX, 0)), cvt<R>(ld<D>(N, BBY, 0)), cvt<R>(ld<D>(N, BBZ, 0))};
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      sink(BETAX + i, fmaT(C.cko, koB[i], cvt<D>(fmaT(be[0], dB[0][i], fmaT(be[1], dB[1][i], fmaT(be[2], dB[2][i], P.f * bb[i]))))));
+      sink(BETAX + i, with_ko<D, R>(fmaT(be[0], dB[0][i], fmaT(be[1], dB[1][i], fmaT(be[2], dB[2][i], P.f * bb[i]))), koB[i],
+                                C, CR));
       R advb = fmaT(-P.eta, bb[i], dbK[i]);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) advb = fmaT(be[k], fd1o<D, R>(N, BBX + i, N.st[k], CR.c1), advb);
-      sink(BBX + i, fmaT(C.cko, ko_sum<D>(N, BBX + i), cvt<D>(advb)));
+      for (int k = 0; k < 3; ++k) advb = fmaT(bec1[k], fd1u<D, R>(N, BBX + i, N.st[k]), advb);
+      sink(BBX + i, with_ko<D, R>(advb, ko_sum<D>(N, BBX + i), C, CR));
     }
   } else {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      sink(BETAX + i, C.cko * koB[i]);
-      sink(BBX + i, C.cko * ko_sum<D>(N, BBX + i));
+      sink(BETAX + i, with_ko<D, R>(R(0.0), koB[i], C, CR));
+      sink(BBX + i, with_ko<D, R>(R(0.0), ko_sum<D>(N, BBX + i), C, CR));
     }
   }
   CCZ4_MARK("rhs gamma-hat gauge");
