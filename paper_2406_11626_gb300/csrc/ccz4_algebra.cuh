@@ -458,10 +458,10 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = i; j < 3; ++j) {
-        R q3 = Cm[0][i][0] * Gd[0][S6(0, j)];
+        R q3 = X[i][j] + X[j][i];
 #pragma unroll
-        for (int q = 1; q < 9; ++q) q3 = fmaT(Cm[q / 3][i][q % 3], Gd[q / 3][S6(q % 3, j)], q3);
-        Q6[S6(i, j)] = X[i][j] + X[j][i] + q3;
+        for (int q = 0; q < 9; ++q) q3 = fmaT(Cm[q / 3][i][q % 3], Gd[q / 3][S6(q % 3, j)], q3);
+        Q6[S6(i, j)] = q3;
       }
   }
   CCZ4_MARK("ricci quadratic");
@@ -505,12 +505,15 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
       second_ko<D, D>(N, PHI, C, C, ddP, koP);
 #pragma unroll
       for (int c = 0; c < 6; ++c)
-        cdph[c] = ddP[c] - fmaT(cvt<D>(Gu[0][c]), dPD[0], fmaT(cvt<D>(Gu[1][c]), dPD[1], cvt<D>(Gu[2][c]) * dPD[2]));
+        cdph[c] = fmaT(-cvt<D>(Gu[0][c]), dPD[0], fmaT(-cvt<D>(Gu[1][c]), dPD[1], fmaT(-cvt<D>(Gu[2][c]), dPD[2], ddP[c])));
     }
     D trcdph = igwD[0] * cdph[0];
 #pragma unroll
     for (int c = 1; c < 6; ++c) trcdph = fmaT(igwD[c], cdph[c], trcdph);
-    const D two_iph2PP = D(2.0) * (iph * iph) * PP;
+    // (1/phi)(cdph_ij + g~_ij (trcdph - dGP - 2 PP / phi) + 2 Z_i P_j + 2 Z_j P_i): the
+    // g~_ij terms of the Ricci part share one coefficient
+    const D iphPP = iph * PP;
+    const D gco = (trcdph - dGP) - (iphPP + iphPP);
     D ddA[6];
     second_ko<D, D>(N, ALPHA, C, C, ddA, koA);
 #pragma unroll
@@ -518,11 +521,11 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
 #pragma unroll
       for (int j = i; j < 3; ++j) {
         const int c = S6(i, j);
-        const D zt = fmaT(Z2D[i], dPD[j], fmaT(Z2D[j], dPD[i], -gD[c] * dGP));
-        phiRZ[c] = cvt<R>(fmaT(iph, cdph[c] + fmaT(gD[c], trcdph, zt), -two_iph2PP * gD[c]));
-        const D phiDDa = iph * fmaT(dPD[i], daD[j], fmaT(dPD[j], daD[i], -gD[c] * PA));
+        const D zt = fmaT(Z2D[i], dPD[j], Z2D[j] * dPD[i]);
+        phiRZ[c] = cvt<R>(iph * (cdph[c] + fmaT(gD[c], gco, zt)));
         // nabla_i nabla_j alpha with the physical Christoffel symbols
-        DDa[c] = cvt<R>(ddA[c] + phiDDa) - fmaT(Gu[0][c], da[0], fmaT(Gu[1][c], da[1], Gu[2][c] * da[2]));
+        const D DDaD = fmaT(iph, fmaT(dPD[i], daD[j], fmaT(dPD[j], daD[i], -gD[c] * PA)), ddA[c]);
+        DDa[c] = fmaT(-Gu[0][c], da[0], fmaT(-Gu[1][c], da[1], fmaT(-Gu[2][c], da[2], cvt<R>(DDaD))));
       }
   }
   R trDDa = igw[0] * DDa[0];
@@ -636,12 +639,11 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
 #pragma unroll
       for (int j = i; j < 3; ++j) {
         const int c = S6(i, j);
-        sink(GXX + c, with_ko<D, R>((advg[c] + (Xg[i][j] + Xg[j][i])) + fmaT(g[c], sg, -al2 * A[c]), kog[c], C, CR));
-        R advA = R(0.0);
+        sink(GXX + c, with_ko<D, R>(fmaT(g[c], sg, fmaT(-al2, A[c], advg[c] + (Xg[i][j] + Xg[j][i]))), kog[c], C, CR));
+        R advA = XA[i][j] + XA[j][i];  // the advection and Lie-derivative terms
 #pragma unroll
         for (int k = 0; k < 3; ++k) advA = fmaT(bec1[k], fd1u<D, R>(N, AXX + c, N.st[k]), advA);
-        const R rA = (advA + (XA[i][j] + XA[j][i])) +
-                     fmaT(ph2al, RZ[c], fmaT(-ph2, DDa[c], fmaT(g[c], sA1, fmaT(A[c], sA2, -al2 * AgA[c]))));
+        const R rA = fmaT(ph2al, RZ[c], fmaT(-ph2, DDa[c], fmaT(g[c], sA1, fmaT(A[c], sA2, fmaT(-al2, AgA[c], advA)))));
         sink(AXX + c, with_ko<D, R>(rA, ko_sum<D>(N, AXX + c), C, CR));
       }
   }
@@ -650,20 +652,21 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
   // ---- scalars ---------------------------------------------------------------------------------
   const R gK = (P.slicing == CCZ4_SLICING_ONE_PLUS_LOG) ? al2 : al * al;  // alpha^2 g(alpha)
   const R dP[3] = {cvt<R>(dPD[0]), cvt<R>(dPD[1]), cvt<R>(dPD[2])};
-  sink(ALPHA, with_ko<D, R>(fmaT(be[0], da[0], fmaT(be[1], da[1], be[2] * da[2])) - gK * (Kc - P.K0), koA, C, CR));
-  sink(PHI, with_ko<D, R>(fmaT(be[0], dP[0], fmaT(be[1], dP[1], be[2] * dP[2])) + third * ph * fmaT(al, Kt, -trB), koP, C,
-                          CR));
+  sink(ALPHA, with_ko<D, R>(fmaT(be[0], da[0], fmaT(be[1], da[1], fmaT(be[2], da[2], -gK * (Kc - P.K0)))), koA, C, CR));
+  sink(PHI, with_ko<D, R>(fmaT(be[0], dP[0], fmaT(be[1], dP[1], fmaT(be[2], dP[2], third * ph * fmaT(al, Kt, -trB)))), koP,
+                          C, CR));
   R dK[3], dT[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     dK[k] = fd1o<D, R>(N, KTR, N.st[k], CR.c1);
     dT[k] = fd1o<D, R>(N, THETA, N.st[k], CR.c1);
   }
-  const R advK = fmaT(be[0], dK[0], fmaT(be[1], dK[1], be[2] * dK[2]));
-  const R advT = fmaT(be[0], dT[0], fmaT(be[1], dT[1], be[2] * dT[2]));
-  sink(KTR, with_ko<D, R>(advK - lapal + al * (RpZ + fmaT(Kt, Kc, -P.k1a * Th)), ko_sum<D>(N, KTR), C, CR));
+  // the advection terms seeded with the other terms outside the factor alpha
+  const R advK = fmaT(be[0], dK[0], fmaT(be[1], dK[1], fmaT(be[2], dK[2], -lapal)));
+  sink(KTR, with_ko<D, R>(fmaT(al, RpZ + fmaT(Kt, Kc, -P.k1a * Th), advK), ko_sum<D>(N, KTR), C, CR));
   const R ZA = R(0.5) * ph2 * fmaT(dGam[0], da[0], fmaT(dGam[1], da[1], dGam[2] * da[2]));  // Z^i A_i
-  sink(THETA, with_ko<D, R>(advT + al * fmaT(P.e2h, RpZ + fmaT(twothird * Kt, Kt, -AA), -Th * fmaT(Kt, P.c, P.k1b)) - ZA,
+  const R advT = fmaT(be[0], dT[0], fmaT(be[1], dT[1], fmaT(be[2], dT[2], -ZA)));
+  sink(THETA, with_ko<D, R>(fmaT(al, fmaT(P.e2h, RpZ + fmaT(twothird * Kt, Kt, -AA), -Th * fmaT(Kt, P.c, P.k1b)), advT),
                             ko_sum<D>(N, THETA), C, CR));
   CCZ4_MARK("rhs scalars");
 
@@ -696,7 +699,6 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
     const R gKk = fmaT(ig[S6(i, 0)], dK[0], fmaT(ig[S6(i, 1)], dK[1], ig[S6(i, 2)] * dK[2]));
     const R gdv = fmaT(ig[S6(i, 0)], gdivB[0], fmaT(ig[S6(i, 1)], gdivB[1], ig[S6(i, 2)] * gdivB[2]));
     const R gA = fmaT(ig[S6(i, 0)], da[0], fmaT(ig[S6(i, 1)], da[1], ig[S6(i, 2)] * da[2]));
-    const R GB = fmaT(Gc[0], dB[0][i], fmaT(Gc[1], dB[1][i], Gc[2] * dB[2][i]));
     const R AuA = fmaT(Au[S6(i, 0)], da[0], fmaT(Au[S6(i, 1)], da[1], Au[S6(i, 2)] * da[2]));
     const R ZB = fmaT(dGam[0], dB[0][i], fmaT(dGam[1], dB[1][i], dGam[2] * dB[2][i]));
     // the 3 A~^ij P_j / phi term, in D
@@ -711,7 +713,8 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
     t = fmaT(R(-2.0), AuA, t);
     t = fmaT(zc, dGam[i], t);
     t = fmaT(k3h, ZB, t);
-    dbK[i] = t - GB;  // d_t Gamma-hat^i - beta^k d_k Gamma-hat^i
+    // - G~^k B_k^i; d_t Gamma-hat^i - beta^k d_k Gamma-hat^i
+    dbK[i] = fmaT(-Gc[0], dB[0][i], fmaT(-Gc[1], dB[1][i], fmaT(-Gc[2], dB[2][i], t)));
     sink(GHX + i, with_ko<D, R>(advGh[i] + dbK[i], ko_sum<D>(N, GHX + i), C, CR));
   }
   if (P.shift == CCZ4_SHIFT_GAMMA_DRIVER) {
