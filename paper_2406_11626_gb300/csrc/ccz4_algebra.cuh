@@ -218,7 +218,7 @@ __host__ __device__ __forceinline__ D ko_sum(const Nbhd &N, int v) {
 // sums Q+ + Q- and Q++ + Q--. The second derivatives come out in O: for
 // O != D the second differences Q+ + Q- - 2Q and Q++ + Q-- - 2Q are taken
 // in D and only their weighted combination is done in O.
-template <class D, class O>
+template <class D, class O, bool SCALED = true>
 __host__ __device__ __forceinline__ void pure2_ko(const Nbhd &N, int v, const StencilCoef<D> &C, const O &c2o,
                                                   O d2[3], D &ko) {
   const D q0 = ld<D>(N, v, 0);
@@ -233,10 +233,12 @@ __host__ __device__ __forceinline__ void pure2_ko(const Nbhd &N, int v, const St
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     if constexpr (std::is_same<D, O>::value) {
-      d2[k] = fmaT(D(-30.0), q0, fmaT(D(16.0), s1[k], -s2[k])) * C.c2;
+      d2[k] = fmaT(D(-30.0), q0, fmaT(D(16.0), s1[k], -s2[k]));
+      if constexpr (SCALED) d2[k] = d2[k] * C.c2;
     } else {
       const D t1 = fmaT(D(-2.0), q0, s1[k]), t2 = fmaT(D(-2.0), q0, s2[k]);
-      d2[k] = fmaT(O(16.0), cvt<O>(t1), -cvt<O>(t2)) * c2o;
+      d2[k] = fmaT(O(16.0), cvt<O>(t1), -cvt<O>(t2));
+      if constexpr (SCALED) d2[k] = d2[k] * c2o;
     }
   }
   const D p1 = s1[0] + s1[1] + s1[2], p2 = s2[0] + s2[1] + s2[2], p3 = s3[0] + s3[1] + s3[2];
@@ -247,11 +249,13 @@ __host__ __device__ __forceinline__ void pure2_ko(const Nbhd &N, int v, const St
 // in O, and its Kreiss-Oliger sum in D. The pure ones are taken here; the
 // mixed ones were formed by the halo fill while the tile was in shared
 // memory, sharing first derivatives between neighbouring points.
-template <class D, class O>
+// SCALED false: the pure ones without their factor 1 / (12 dx^2), for a
+// caller that folds it into its own coefficients.
+template <class D, class O, bool SCALED = true>
 __host__ __device__ __forceinline__ void second_ko(const Nbhd &N, int v, const StencilCoef<D> &C,
                                                    const StencilCoef<O> &CO, O dd[6], D &ko) {
   O d2[3];
-  pure2_ko<D, O>(N, v, C, CO.c2, d2, ko);
+  pure2_ko<D, O, SCALED>(N, v, C, CO.c2, d2, ko);
   dd[0] = d2[0];
   dd[3] = d2[1];
   dd[5] = d2[2];
@@ -421,13 +425,13 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
     for (int c = 1; c < 6; ++c) s = fmaT(igw[c], Gu[k][c], s);
     Gc[k] = s;  // G~^k = g~^ij G~^k_ij
   }
-  // Gamma-hat - G~ and Z_i = g~_ij (Gamma-hat^j - G~^j) / 2
-  R dGam[3], Zd[3];
+  // Gamma-hat - G~ and 2 Z_i = g~_ij (Gamma-hat^j - G~^j) (Z only enters doubled)
+  R dGam[3], Z2[3];  // Gamma-hat - G~ and 2 Z_i
 #pragma unroll
   for (int i = 0; i < 3; ++i) dGam[i] = Gh[i] - Gc[i];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
-    Zd[i] = R(0.5) * fmaT(g[S6(i, 0)], dGam[0], fmaT(g[S6(i, 1)], dGam[1], g[S6(i, 2)] * dGam[2]));
+    Z2[i] = fmaT(g[S6(i, 0)], dGam[0], fmaT(g[S6(i, 1)], dGam[1], g[S6(i, 2)] * dGam[2]));
   CCZ4_MARK("christoffel");
 
   // ---- quadratic Christoffel part of the Ricci tensor -------------------------
@@ -495,8 +499,7 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       dGamD[i] = cvt<D>(dGam[i]);
-      const D z = cvt<D>(Zd[i]);
-      Z2D[i] = z + z;  // 2 Z_i
+      Z2D[i] = cvt<D>(Z2[i]);  // 2 Z_i
     }
     const D dGP = fmaT(dGamD[0], dPD[0], fmaT(dGamD[1], dPD[1], dGamD[2] * dPD[2]));
     D cdph[6];  // nabla~_i nabla~_j phi
@@ -535,6 +538,23 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
 
   // ---- R_ij + 2 nabla_(i Z_j) -----------------------------------------------------
   // -1/2 g~^kl d_k d_l g~_ij + g~_k(i d_j) Gamma-hat^k + 1/2 Gamma-hat^k d_k g~_ij + Q6_ij + phi terms
+  // FP64 path: g~^kl with the factor 1 / (12 dx^2) of the pure second
+  // differences on its diagonal, for the Laplacians of g~ and beta (taken
+  // from unscaled pure ones: fewer FP64 multiplies). Mixed path: g~^kl and
+  // scaled pure ones (the saving would be FP32 work, and the six weights
+  // would stay live across the kernel).
+  R igwc[6];
+  if constexpr (SAME) {
+    igwc[0] = igw[0] * CR.c2;
+    igwc[1] = igw[1];
+    igwc[2] = igw[2];
+    igwc[3] = igw[3] * CR.c2;
+    igwc[4] = igw[4];
+    igwc[5] = igw[5] * CR.c2;
+  } else {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) igwc[c] = igw[c];
+  }
   R RZ[6], advGh[3];
   D kog[6];
   {
@@ -551,10 +571,10 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
       for (int j = i; j < 3; ++j) {
         const int c = S6(i, j);
         R dd[6];
-        second_ko<D, R>(N, GXX + c, C, CR, dd, kog[c]);
-        R lap = igw[0] * dd[0];
+        second_ko<D, R, !SAME>(N, GXX + c, C, CR, dd, kog[c]);  // FP64 path: pure ones unscaled
+        R lap = igwc[0] * dd[0];
 #pragma unroll
-        for (int q = 1; q < 6; ++q) lap = fmaT(igw[q], dd[q], lap);
+        for (int q = 1; q < 6; ++q) lap = fmaT(igwc[q], dd[q], lap);
         R u = Ghdg[c];
 #pragma unroll
         for (int k = 0; k < 3; ++k) u = fmaT(g[S6(k, i)], dG[j][k], fmaT(g[S6(k, j)], dG[i][k], u));
@@ -677,14 +697,21 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
     R ddB[3][6];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      second_ko<D, R>(N, BETAX + i, C, CR, ddB[i], koB[i]);
-      R s = igw[0] * ddB[i][0];
+      second_ko<D, R, !SAME>(N, BETAX + i, C, CR, ddB[i], koB[i]);  // FP64 path: pure ones unscaled
+      R s = igwc[0] * ddB[i][0];
 #pragma unroll
-      for (int q = 1; q < 6; ++q) s = fmaT(igw[q], ddB[i][q], s);
+      for (int q = 1; q < 6; ++q) s = fmaT(igwc[q], ddB[i][q], s);
       lapB[i] = s;
     }
+    // d_k d_l beta^l (FP64 path: the l = k term is the unscaled pure one)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) gdivB[k] = ddB[0][S6(k, 0)] + ddB[1][S6(k, 1)] + ddB[2][S6(k, 2)];
+    for (int k = 0; k < 3; ++k) {
+      if constexpr (SAME)
+        gdivB[k] = fmaT(CR.c2, ddB[k][S6(k, k)],
+                        ddB[(k + 1) % 3][S6(k, (k + 1) % 3)] + ddB[(k + 2) % 3][S6(k, (k + 2) % 3)]);
+      else
+        gdivB[k] = ddB[0][S6(k, 0)] + ddB[1][S6(k, 1)] + ddB[2][S6(k, 2)];
+    }
   }
   const R al43 = R(4.0 / 3.0) * al;
   const R al6 = R(6.0) * al;
