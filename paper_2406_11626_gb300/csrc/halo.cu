@@ -50,19 +50,36 @@ struct LevelScale {
   float cmixf[MAX_LEVELS];
 };
 
-// Second stage of a mixed derivative: d_a of the first derivatives e[] at
-// stride s, stored to mixed-derivative slot `slot` of this patch's point q.
-// FP64 weights and an FP64 slot; or, for the fields whose mixed derivatives
-// the mixed path's stage kernel uses in FP32 (g~ and beta, f32 set), the
-// differences in FP64, the weights in FP32 (the split the stage kernel
-// applies to its own stencils) and an FP32 slot (half the traffic).
-__device__ __forceinline__ void mixed_out(const double *e, int s, double cmix, float cmixf, bool f32, double *mix,
-                                          long long n_points, long long pbase, int slot, int q) {
-  const double d1 = e[s] - e[-s], d2 = e[2 * s] - e[-2 * s];
+// First stage of a mixed derivative at point e of the widened region: the
+// (unscaled) first derivative of the tile along stride si. FP64 differences
+// of the FP64 tile; the weights in FP64, or, for the fields whose mixed
+// derivatives the mixed path's stage kernel uses in FP32 (g~ and beta, f32
+// set), in FP32 with the result kept as FP32 (the split the stage kernel
+// applies to its own first derivatives).
+__device__ __forceinline__ void mixed_in(double *ext, int e, const double *ts, int c0, int si, bool f32) {
+  const double a = ts[c0 + si] - ts[c0 - si], b = ts[c0 + 2 * si] - ts[c0 - 2 * si];
+  if (f32)
+    reinterpret_cast<float *>(ext)[e] = fmaf(8.0f, d2f_bits(a), -d2f_bits(b));
+  else
+    ext[e] = fma(8.0, a, -b);
+}
+
+// Second stage: d_a of the first derivatives at ext[e] along stride s, stored
+// to mixed-derivative slot `slot` of this patch's point q. FP64 differences
+// and weights and an FP64 slot; or (f32) the differences of the FP32 first
+// derivatives in FP32 (a subtraction of two FP32 numbers is exact when it
+// cancels and otherwise within half an ulp of its result), the weights in
+// FP32 and an FP32 slot (half the traffic).
+__device__ __forceinline__ void mixed_out(const double *ext, int e, int s, double cmix, float cmixf, bool f32,
+                                          double *mix, long long n_points, long long pbase, int slot, int q) {
   if (f32) {
+    const float *ef = reinterpret_cast<const float *>(ext) + e;
+    const float d1 = ef[s] - ef[-s], d2 = ef[2 * s] - ef[-2 * s];
     float *mf = reinterpret_cast<float *>(mix) + (long long)mix_fslot(slot) * n_points + pbase;
-    __stcs(mf + q, fmaf(8.0f, d2f_bits(d1), -d2f_bits(d2)) * cmixf);
+    __stcs(mf + q, fmaf(8.0f, d1, -d2) * cmixf);
   } else {
+    const double *ed = ext + e;
+    const double d1 = ed[s] - ed[-s], d2 = ed[2 * s] - ed[-2 * s];
     __stcs(mix + (long long)slot * n_points + pbase + q, fma(8.0, d1, -d2) * cmix);
   }
 }
@@ -232,14 +249,14 @@ __global__ void __launch_bounds__(FILL_THREADS, CCZ4_FILL_MIN_BLOCKS) fill_halos
         // a runs along the widened axis (x for passes 0, 1; y for pass 2)
         const int x = pass == 2 ? b : a, y = pass == 2 ? a : b, z = c;
         const int c0 = ((z + HALO) * T + (y + HALO)) * T + (x + HALO);
-        ext[e] = fma(8.0, ts[c0 + si] - ts[c0 - si], -(ts[c0 + 2 * si] - ts[c0 - 2 * si]));
+        mixed_in(ext, e, ts, c0, si, f32);
       }
       __syncthreads();
       for (int q = threadIdx.x; q < p3; q += blockDim.x) {
         const int x = q % p, y = (q / p) % p, z = q / (p * p);
         const int a = pass == 2 ? y : x, b = pass == 2 ? x : y;
         const int e = (z * p + b) * pe + (a + 2);
-        mixed_out(ext + e, 1, cmix, cmixf, f32, mix, g.n_points, pbase, slot + pass, q);
+        mixed_out(ext, e, 1, cmix, cmixf, f32, mix, g.n_points, pbase, slot + pass, q);
       }
       __syncthreads();
     }
@@ -249,14 +266,14 @@ __global__ void __launch_bounds__(FILL_THREADS, CCZ4_FILL_MIN_BLOCKS) fill_halos
       const int a = e % pe - 2, b = (e / pe) % pe - 2, c = e / (pe * pe);
       if ((a < 0 || a >= p) && (b < 0 || b >= p)) continue;  // corner: not needed
       const int c0 = ((c + HALO) * T + (b + HALO)) * T + (a + HALO);
-      ext[e] = fma(8.0, ts[c0 + T2] - ts[c0 - T2], -(ts[c0 + 2 * T2] - ts[c0 - 2 * T2]));
+      mixed_in(ext, e, ts, c0, T2, f32);
     }
     __syncthreads();
     for (int q = threadIdx.x; q < p3; q += blockDim.x) {
       const int x = q % p, y = (q / p) % p, z = q / (p * p);
       const int e = (z * pe + (y + 2)) * pe + (x + 2);
-      mixed_out(ext + e, 1, cmix, cmixf, f32, mix, g.n_points, pbase, slot + 1, q);
-      mixed_out(ext + e, pe, cmix, cmixf, f32, mix, g.n_points, pbase, slot + 2, q);
+      mixed_out(ext, e, 1, cmix, cmixf, f32, mix, g.n_points, pbase, slot + 1, q);
+      mixed_out(ext, e, pe, cmix, cmixf, f32, mix, g.n_points, pbase, slot + 2, q);
     }
     __syncthreads();
   }
