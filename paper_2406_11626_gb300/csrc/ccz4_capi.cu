@@ -352,25 +352,75 @@ extern "C" ccz4_status ccz4_field_ptr(ccz4_grid *g, int buf, double **dev, long 
   return CCZ4_OK;
 }
 
+// Rows of doubles between a device buffer and host memory that the device
+// can address (pinned, mapped): one thread per element, a warp per 32
+// consecutive elements of a row, so both sides are read and written in
+// full lines. Faster than a copy engine over the CPU-GPU link of a
+// Grace-Blackwell node.
+__global__ void __launch_bounds__(256) strided_copy_kernel(double *__restrict__ dst, long long dst_stride,
+                                                            const double *__restrict__ src, long long src_stride,
+                                                            long long row_len, int rows) {
+  const long long total = row_len * rows;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long r = k / row_len, c = k - r * row_len;
+    dst[r * dst_stride + c] = src[r * src_stride + c];
+  }
+}
+
+// The device address of host memory that the device can access directly
+// (pinned and mapped), or NULL.
+static void *mapped_host(const void *h) {
+  if (!h) return nullptr;
+  const char *mode = getenv("CCZ4_HOST_COPY");
+  if (mode && strcmp(mode, "dma") == 0) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+    cudaGetLastError();  // not a CUDA allocation: clear the error
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// rows x row_len doubles from src (stride src_stride) to dst (stride
+// dst_stride), one side on the host: by the copy kernel when that side is
+// mapped pinned memory, else by the copy engine.
+static cudaError_t copy_rows(double *dst, long long dst_stride, const double *src, long long src_stride,
+                             long long row_len, int rows, bool to_device, cudaStream_t s) {
+  if (row_len <= 0 || rows <= 0) return cudaSuccess;
+  void *mh = mapped_host(to_device ? (const void *)src : (const void *)dst);
+  if (mh) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long blocks_needed = (row_len * rows + 255) / 256;
+    const long long blocks = blocks_needed < 8LL * sms ? blocks_needed : 8LL * sms;
+    if (to_device)
+      strided_copy_kernel<<<(unsigned)blocks, 256, 0, s>>>(dst, dst_stride, (const double *)mh, src_stride, row_len,
+                                                            rows);
+    else
+      strided_copy_kernel<<<(unsigned)blocks, 256, 0, s>>>((double *)mh, dst_stride, src, src_stride, row_len, rows);
+    return cudaGetLastError();
+  }
+  return cudaMemcpy2DAsync(dst, sizeof(double) * dst_stride, src, sizeof(double) * src_stride,
+                           sizeof(double) * row_len, rows, to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost,
+                           s);
+}
+
 static ccz4_status copy_state(ccz4_grid *g, int buf, double *U, double *G, bool to_device, cudaStream_t s) {
   const GridView &v = g->v;
   double *d = g->buf[buf];
-  const cudaMemcpyKind kind = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
   if (v.n_points > 0) {
     if (to_device)
-      CUDA_TRY(cudaMemcpy2DAsync(d, sizeof(double) * v.S, U, sizeof(double) * v.n_points,
-                                 sizeof(double) * v.n_points, NV, kind, s));
+      CUDA_TRY(copy_rows(d, v.S, U, v.n_points, v.n_points, NV, true, s));
     else
-      CUDA_TRY(cudaMemcpy2DAsync(U, sizeof(double) * v.n_points, d, sizeof(double) * v.S,
-                                 sizeof(double) * v.n_points, NV, kind, s));
+      CUDA_TRY(copy_rows(U, v.n_points, d, v.S, v.n_points, NV, false, s));
   }
   if (v.n_ghost > 0 && G) {
     if (to_device)
-      CUDA_TRY(cudaMemcpy2DAsync(d + v.n_points, sizeof(double) * v.S, G, sizeof(double) * v.n_ghost,
-                                 sizeof(double) * v.n_ghost, NV, kind, s));
+      CUDA_TRY(copy_rows(d + v.n_points, v.S, G, v.n_ghost, v.n_ghost, NV, true, s));
     else
-      CUDA_TRY(cudaMemcpy2DAsync(G, sizeof(double) * v.n_ghost, d + v.n_points, sizeof(double) * v.S,
-                                 sizeof(double) * v.n_ghost, NV, kind, s));
+      CUDA_TRY(copy_rows(G, v.n_ghost, d + v.n_points, v.S, v.n_ghost, NV, false, s));
   }
   CUDA_TRY(cudaStreamSynchronize(s));
   return CCZ4_OK;
