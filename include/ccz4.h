@@ -144,7 +144,10 @@ ccz4_status ccz4_field_ptr(ccz4_grid *g, int buf, double **dev, long long *n_dou
 /* Copies host arrays U[25][n_points] and (Sommerfeld only, may be NULL
    otherwise) G[25][n_ghost] into a state-shaped buffer, or back. Both
    synchronise the stream before returning (the host arrays may be reused
-   at once). */
+   at once). Host arrays in pinned memory that the device can address are
+   moved by a copy kernel over the CPU-GPU link, any other host memory by
+   the copy engine; the environment variable CCZ4_HOST_COPY=dma selects the
+   copy engine always. */
 ccz4_status ccz4_upload(ccz4_grid *g, int buf, const double *U, const double *G, void *stream);
 ccz4_status ccz4_download(ccz4_grid *g, int buf, double *U, double *G, void *stream);
 
