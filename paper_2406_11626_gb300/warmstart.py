@@ -252,7 +252,7 @@ def evaluate(mlp, draws, n, L, tol=1e-10, check=100, max_sweeps=2000000, omega=1
     return np.array(out)
 
 
-def run_experiment(n=96, L=16.0, n_train=2000, n_test=200, steps=80000, batch=65536, lr=1e-3, tol=1e-10,
+def run_experiment(n=96, L=16.0, n_train=2000, n_test=200, steps=160000, batch=65536, lr=1e-3, tol=1e-10,
                    check=20, seed=0, omega=None, gs_draws=10, log=print, lr_final=None):
     """The whole experiment; returns a JSON-ready report."""
     import torch
@@ -320,7 +320,7 @@ def main(argv=None):
     ap.add_argument("--L", type=float, default=16.0)
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--test", type=int, default=200)
-    ap.add_argument("--steps", type=int, default=80000)
+    ap.add_argument("--steps", type=int, default=160000)
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--lr-final", type=float, default=None,
