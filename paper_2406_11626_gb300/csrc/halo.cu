@@ -5,10 +5,14 @@
 //
 // One CTA per patch. It resolves the source of every tile point once
 // (neighbour patch, periodic wrap, clamped copy or Sommerfeld ghost cell;
-// on a refined mesh it reads the host-built table instead, and computes the
-// coarse-to-fine interpolations it lists for all fields in one pass) into
-// an index table, then for each of the 25 fields gathers the field's tile
-// into shared memory and writes it out with coalesced stores. For g~,
+// on a refined mesh it reads the host-built table instead) into an index
+// table, then for each of the 25 fields gathers the field's tile into
+// shared memory and writes it out with coalesced stores. On a refined mesh
+// the coarse-to-fine interpolations of the halo are evaluated separably per
+// field (the patch's distinct x-interpolations, then the distinct
+// y-interpolations of their pairs, then one z-interpolation per halo point,
+// in shared memory), or point by point for all fields at once where the
+// host planned no separable tables. For g~,
 // alpha, beta and phi it also forms the mixed derivatives d_x d_y, d_x d_z,
 // d_y d_z as the first-derivative stencil applied to first derivatives
 // shared through shared memory: d_y Q is taken once on the patch widened by
