@@ -79,6 +79,7 @@ static void free_all(ccz4_grid *g) {
   cudaFree(g->d_ijk);
   cudaFree(g->d_owner);
   cudaFree(g->d_gcoord);
+  cudaFree(g->d_ghost_geo);
   cudaFree(g->d_status);
   cudaFree(g->red_partial);
   cudaFree(g->red_out);
@@ -321,6 +322,22 @@ static ccz4_status create_grid(const ccz4_grid_desc *d, const std::vector<int> &
   v.ybeg = g->d_ybeg;
   v.plev = g->d_plev;
   v.leaf = g->d_leaf;
+  if (v.n_ghost > 0) {
+    // the static geometry of the Sommerfeld ghost cells, once
+    if (cudaMalloc(&g->d_ghost_geo, sizeof(GhostGeo) * (size_t)v.n_ghost) != cudaSuccess) {
+      set_error("device allocation of the ghost-cell geometry failed: %s", cudaGetErrorString(cudaGetLastError()));
+      free_all(g);
+      return CCZ4_ERR_NOMEM;
+    }
+    v.ghost_geo = g->d_ghost_geo;
+    cudaError_t eg = launch_ghost_setup(v, g->d_ghost_geo, 0);
+    if (eg == cudaSuccess) eg = cudaDeviceSynchronize();
+    if (eg != cudaSuccess) {
+      set_error("ghost-cell geometry set-up failed: %s", cudaGetErrorString(eg));
+      free_all(g);
+      return CCZ4_ERR_CUDA;
+    }
+  }
   *out = g;
   return CCZ4_OK;
 }

@@ -45,6 +45,14 @@ struct InterpEntry {
   int t;
 };
 
+// Static geometry of an evolved Sommerfeld ghost cell: the index of its
+// neighbour one cell inward along the normal of its face (-1: none), the
+// factor (r / x_d) sign / dx of the normal derivative and 1 / r.
+struct GhostGeo {
+  long long sn;
+  double geo, ir;
+};
+
 // Separable form of a patch's interpolations (the same values, rounded the
 // same way): the distinct x-interpolations of the patch (value
 // rx ? (1-w) q(s0) + w q(s1) : q(s0), w = rx/3), then the distinct
@@ -86,6 +94,7 @@ struct GridView {
   const int *ijk;              // [n_patches][3]
   const int *owner;            // [np2][np1][np0] -> patch id
   const int *gcoord;           // [n_ghost][3] global coordinates of the ghost cells
+  const GhostGeo *ghost_geo;   // [n_ghost] their static geometry
   unsigned *status;            // device status word
   // refined meshes only (src == nullptr on a single level)
   int n_levels;
@@ -197,10 +206,13 @@ struct ccz4_grid {
   int *d_rpar[CCZ4_MAX_LEVELS], *d_rkid[CCZ4_MAX_LEVELS];
   int n_rpar[CCZ4_MAX_LEVELS];
   unsigned long long *d_queue;  // work counter of the queue launch (allocated on first use)
+  ccz4::GhostGeo *d_ghost_geo;  // [n_ghost] static geometry of the Sommerfeld ghost cells
 };
 
 // Kernel launchers (one translation unit each).
 namespace ccz4 {
+// Fills the static geometry of the Sommerfeld ghost cells (rhs.cu).
+cudaError_t launch_ghost_setup(const GridView &g, GhostGeo *out, cudaStream_t s);
 // fp32_weights: mixed derivatives with FP32 weights (for the mixed-precision stage kernel)
 cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile, double *mix, cudaStream_t s,
                               bool fp32_weights = false);

@@ -205,39 +205,37 @@ __global__ void __launch_bounds__(128, StageBlocks<R>::value) interior_kernel(Gr
   }
 }
 
+// One thread per (evolved Sommerfeld ghost cell, field): the ghost-cell
+// ODE (Eq. exa_sommerfeld_inter) with the cell's static geometry from
+// g.ghost_geo, and the same stage update, no enforcement, FP64.
 template <int MODE>
-__global__ void __launch_bounds__(128) ghost_kernel(GridView g, ccz4_params P, const double *__restrict__ in,
+__global__ void __launch_bounds__(256) ghost_kernel(GridView g, ccz4_params P, const double *__restrict__ in,
                                                     const double *__restrict__ ini, StageArgs a) {
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
   if (id >= g.n_ghost) return;
-  int c[3] = {__ldg(g.gcoord + 3 * id), __ldg(g.gcoord + 3 * id + 1), __ldg(g.gcoord + 3 * id + 2)};
-  // the face a ghost cell belongs to: its highest outside axis
-  int d = 0, side = 0;
+  const GhostGeo *gg = g.ghost_geo + id;
+  const long long sn = __ldg(&gg->sn);
+  if (sn < 0) return;
+  const double geo = __ldg(&gg->geo), ir = __ldg(&gg->ir);
+  // the field's speed, selected with static indices (a run-time index into
+  // the parameter array would copy it to local memory)
+  double cv = P.somm_speed[0];
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    if (c[q] < 0) { d = q; side = -1; }
-    if (c[q] >= g.N[q]) { d = q; side = 1; }
+  for (int q = 1; q < NV; ++q)
+    if (q == v) cv = P.somm_speed[q];
+  const long long o = v * g.S + g.n_points + id;
+  const double qg = __ldg(in + o);
+  const double qn = __ldg(in + v * g.S + sn);
+  const double k = -cv * geo * (qg - qn) - cv * ir * (qg - __ldg(ini + o));
+  if (MODE < 0) {
+    a.out[o] = k;
+    return;
   }
-  int nb[3] = {c[0], c[1], c[2]};
-  nb[d] -= side;
-  const long long sn = locate(g, nb[0], nb[1], nb[2]);
-  if (sn < 0 || side == 0) return;
-  double xs[3];
-#pragma unroll
-  for (int q = 0; q < 3; ++q) xs[q] = g.origin[q] + (c[q] + 0.5) * g.dx;
-  const double rr = sqrt(xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2]);
-  const double ir = 1.0 / rr;
-  const double geo = rr / xs[d] * (side > 0 ? 1.0 : -1.0) / g.dx;  // (r / x_d) * sign / dx
-  const long long self = g.n_points + id;
-  double k[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const double qg = __ldg(in + v * g.S + self);
-    const double qn = __ldg(in + v * g.S + sn);
-    const double cv = P.somm_speed[v];
-    k[v] = -cv * geo * (qg - qn) - cv * ir * (qg - __ldg(ini + v * g.S + self));
-  }
-  finish_point<MODE>(g, self, k, a, false);
+  double acc = MODE == 0 ? 0.0 : a.acc[o];
+  const double un = rk_combine<(MODE < 0 ? 0 : MODE), double>(a.U[o], acc, k, a.dt);
+  if (MODE < 3) a.acc[o] = acc;
+  a.out[o] = un;
 }
 
 StencilCoef<double> coefs(double dx, const ccz4_params &P) {
@@ -285,8 +283,8 @@ cudaError_t launch_mode(const GridView &g, const ccz4_params &P, const double *t
     if (e != cudaSuccess) return e;
   }
   if (g.n_ghost > 0) {
-    const long long blocks = (g.n_ghost + 127) / 128;
-    ghost_kernel<MODE><<<(unsigned)blocks, 128, 0, s>>>(g, P, in, ini, a);
+    const dim3 grid((unsigned)((g.n_ghost + 255) / 256), NV);
+    ghost_kernel<MODE><<<grid, 256, 0, s>>>(g, P, in, ini, a);
     return cudaGetLastError();
   }
   return cudaSuccess;
