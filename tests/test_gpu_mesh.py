@@ -20,6 +20,9 @@ MESHES = {
     "three": (6, (4, 4, 4), [((1, 1, 1), (3, 3, 3)), ((5, 5, 5), (7, 7, 7))]),
     "small_p": (3, (5, 4, 4), [((1, 1, 1), (4, 3, 3)), ((4, 4, 4), (6, 5, 5))]),
     "p9": (9, (3, 3, 3), [((1, 1, 1), (2, 2, 2))]),
+    # the largest patch edge the fill takes: 24^3 tiles, up to 4044 separable
+    # x and y interpolations per patch in its shared memory
+    "p18": (18, (3, 3, 3), [((1, 1, 1), (2, 2, 2))]),
 }
 
 
@@ -60,7 +63,7 @@ def mesh_state(gg, lev, ijk, origin, dx, bc, seed, base, amp=0.02):
 
 
 @pytest.mark.parametrize("name,bc", [("two", "periodic"), ("two", "copy"), ("three", "sommerfeld"),
-                                     ("small_p", "periodic"), ("p9", "sommerfeld")])
+                                     ("small_p", "periodic"), ("p9", "sommerfeld"), ("p18", "sommerfeld")])
 def test_mesh_halo_fill_is_bit_exact(name, bc):
     """Same-level copies, level-0 boundary rules and the interpolated halo
     of refined patches all equal the oracle bit for bit (the kernel rounds
