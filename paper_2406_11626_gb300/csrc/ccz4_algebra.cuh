@@ -675,17 +675,19 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
   sink(ALPHA, with_ko<D, R>(fmaT(be[0], da[0], fmaT(be[1], da[1], fmaT(be[2], da[2], -gK * (Kc - P.K0)))), koA, C, CR));
   sink(PHI, with_ko<D, R>(fmaT(be[0], dP[0], fmaT(be[1], dP[1], fmaT(be[2], dP[2], third * ph * fmaT(al, Kt, -trB)))), koP,
                           C, CR));
+  // first differences of K and Theta without 1 / (12 dx): their advection
+  // takes beta / (12 dx), the Gamma-hat equation coefficients with the factor
   R dK[3], dT[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    dK[k] = fd1o<D, R>(N, KTR, N.st[k], CR.c1);
-    dT[k] = fd1o<D, R>(N, THETA, N.st[k], CR.c1);
+    dK[k] = fd1u<D, R>(N, KTR, N.st[k]);
+    dT[k] = fd1u<D, R>(N, THETA, N.st[k]);
   }
   // the advection terms seeded with the other terms outside the factor alpha
-  const R advK = fmaT(be[0], dK[0], fmaT(be[1], dK[1], fmaT(be[2], dK[2], -lapal)));
+  const R advK = fmaT(bec1[0], dK[0], fmaT(bec1[1], dK[1], fmaT(bec1[2], dK[2], -lapal)));
   sink(KTR, with_ko<D, R>(fmaT(al, RpZ + fmaT(Kt, Kc, -P.k1a * Th), advK), ko_sum<D>(N, KTR), C, CR));
   const R ZA = R(0.5) * ph2 * fmaT(dGam[0], da[0], fmaT(dGam[1], da[1], dGam[2] * da[2]));  // Z^i A_i
-  const R advT = fmaT(be[0], dT[0], fmaT(be[1], dT[1], fmaT(be[2], dT[2], -ZA)));
+  const R advT = fmaT(bec1[0], dT[0], fmaT(bec1[1], dT[1], fmaT(bec1[2], dT[2], -ZA)));
   sink(THETA, with_ko<D, R>(fmaT(al, fmaT(P.e2h, RpZ + fmaT(twothird * Kt, Kt, -AA), -Th * fmaT(Kt, P.c, P.k1b)), advT),
                             ko_sum<D>(N, THETA), C, CR));
   CCZ4_MARK("rhs scalars");
@@ -719,24 +721,24 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
   // coefficient of Gamma-hat^i - G~^i: (1/2)(-(4/3) alpha K - 2 alpha kappa1 + 2 kappa3 (2/3) tr B)
   const R zc = R(0.5) * fmaT(-al43, Kt, fmaT(-al2, P.kappa1, P.k3x2 * trB23));
   const R k3h = R(-0.5) * P.k3x2;
+  // the terms g~^ik (2 alpha d_k Theta - (4/3) alpha d_k K + (s/3) d_k d_l beta^l
+  // - 2 Theta d_k alpha) contract one vector with g~^ik
+  const R al2c = al2 * CR.c1, al43c = al43 * CR.c1;
+  R wv[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) wv[k] = fmaT(al2c, dT[k], fmaT(-al43c, dK[k], fmaT(P.s3, gdivB[k], -Th2 * da[k])));
   R dbK[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const R gT = fmaT(ig[S6(i, 0)], dT[0], fmaT(ig[S6(i, 1)], dT[1], ig[S6(i, 2)] * dT[2]));
-    const R gKk = fmaT(ig[S6(i, 0)], dK[0], fmaT(ig[S6(i, 1)], dK[1], ig[S6(i, 2)] * dK[2]));
-    const R gdv = fmaT(ig[S6(i, 0)], gdivB[0], fmaT(ig[S6(i, 1)], gdivB[1], ig[S6(i, 2)] * gdivB[2]));
-    const R gA = fmaT(ig[S6(i, 0)], da[0], fmaT(ig[S6(i, 1)], da[1], ig[S6(i, 2)] * da[2]));
     const R AuA = fmaT(Au[S6(i, 0)], da[0], fmaT(Au[S6(i, 1)], da[1], Au[S6(i, 2)] * da[2]));
     const R ZB = fmaT(dGam[0], dB[0][i], fmaT(dGam[1], dB[1][i], dGam[2] * dB[2][i]));
     // the 3 A~^ij P_j / phi term, in D
     const D AuP = fmaT(cvt<D>(Au[S6(i, 0)]), dPD[0], fmaT(cvt<D>(Au[S6(i, 1)]), dPD[1], cvt<D>(Au[S6(i, 2)]) * dPD[2]));
     const R AuPphi = cvt<R>(AuP * iph);
-    R t = fmaT(P.s3, gdv, lapB[i]);
-    t = fmaT(al2, gT + GA[i], t);
-    t = fmaT(-al43, gKk, t);
+    R t = fmaT(ig[S6(i, 0)], wv[0], fmaT(ig[S6(i, 1)], wv[1], fmaT(ig[S6(i, 2)], wv[2], lapB[i])));
+    t = fmaT(al2, GA[i], t);
     t = fmaT(trB23, Gc[i], t);
     t = fmaT(-al6, AuPphi, t);
-    t = fmaT(-Th2, gA, t);
     t = fmaT(R(-2.0), AuA, t);
     t = fmaT(zc, dGam[i], t);
     t = fmaT(k3h, ZB, t);
