@@ -40,7 +40,11 @@
  *    same order without padding: U[25][n_points] and G[25][n_ghost].
  *  - Halo tiles (CCZ4_BUF_TILE): [25][n_patches][(p+6)^3], each patch with
  *    its width-3 halo, [z][y][x] with x fastest, local index l = patch
- *    point index + 3.
+ *    point index + 3. 8 bytes per entry: the FP64 value, except after a
+ *    mixed-precision fill (ccz4_fill_halos_for), where every field but
+ *    alpha and phi holds the split pair {hi, lo} of the value as two FP32
+ *    numbers (hi first): hi = the value rounded to FP32, lo = the value
+ *    minus hi rounded to FP32.
  */
 #ifndef CCZ4_H
 #define CCZ4_H
@@ -162,13 +166,15 @@ ccz4_status ccz4_download(ccz4_grid *g, int buf, double *U, double *G, void *str
    first-derivative stencils) into CCZ4_BUF_MIX. */
 ccz4_status ccz4_fill_halos(ccz4_grid *g, int buf, void *stream);
 
-/* The halo fill as the stage kernel for parameters P needs it: the same
-   tiles; for P->precision == CCZ4_PREC_MIXED, the mixed derivatives that
+/* The halo fill as the stage kernel for parameters P needs it: for
+   P->precision == CCZ4_PREC_MIXED the tiles of every field but alpha and
+   phi hold split FP32 pairs (see the TILE layout above), on which the
+   mixed stage kernel takes its stencil differences, and the mixed derivatives that
    the mixed stage kernel uses in FP32 -- those of g~ and beta -- take their
    differences in FP64 and their weights in FP32 and are stored as FP32 in
    the first 27 x n_points floats of CCZ4_BUF_MIX (g~'s 18 slots, then
-   beta's 9), while those of alpha and phi stay FP64 in their slots;
-   otherwise the buffers equal ccz4_fill_halos'. A mixed-precision
+   beta's 9), while those of alpha and phi stay FP64 in their slots
+   (and their tiles FP64); otherwise the buffers equal ccz4_fill_halos'. A mixed-precision
    ccz4_rk_stage must follow this fill (ccz4_rhs, ccz4_step and
    ccz4_step_graph fill this way). */
 ccz4_status ccz4_fill_halos_for(ccz4_grid *g, int buf, const ccz4_params *P, void *stream);

@@ -14,12 +14,14 @@
 // the primaries, closed by the listed relations and the modified Ricci
 // tensor of Eq. NR_foccz4_modified_ricci.
 //
-// Two scalar types: D carries the state, every finite difference, the
-// contractions of second derivatives, the terms with inverse powers of the
-// conformal factor phi (which grow without bound at a puncture) and the
-// time update; R carries the rest of the pointwise algebra. D = R = double
-// is the FP64 path; D = double, R = float the mixed path. Constants are
-// written in the type they are used in, so no expression silently widens.
+// Two scalar types: D carries the state, the differences of alpha and phi,
+// the terms with inverse powers of the conformal factor phi (which grow
+// without bound at a puncture) and the time update; R carries the rest of
+// the pointwise algebra. D = R = double is the FP64 path, where D also
+// takes every difference; D = double, R = float the mixed path, where the
+// differences of the other fields are taken with FP64 accuracy on split
+// FP32 pairs (sp_second and its neighbours below). Constants are written in
+// the type they are used in, so no expression silently widens.
 //
 // Arithmetic is arranged for the FP64 pipe: reciprocals are taken once,
 // symmetric tensors are stored as six components, contractions use the
@@ -76,6 +78,33 @@ __device__ __forceinline__ double f2d_bits(float v) {
   hi = e == 255u ? (sgn | 0x7FF00000u | ((u & 0x7FFFFFu) >> 3)) : hi;
   return __hiloint2double((int)hi, (int)lo);
 }
+// The split pair of the mixed path's tiles: hi = d2f_bits(x) and lo = the
+// FP32 rounding (to nearest even) of x - hi, returned as the 8 bytes of a
+// float2 {hi, lo} (the bit pattern of a double, for a store in place of x).
+// x - hi is read off the 29 mantissa bits that hi drops: with r the rounding
+// bit (the highest of them), x - hi = sign(x) (low29 - r 2^29) 2^(e - 52);
+// its magnitude (below 2^28 units) is made an FP32 number from two exact
+// 14-bit halves and one fused multiply-add (a single rounding), then scaled
+// by the power of two. Integer and FP32 operations only. Where hi is zero
+// (x below the FP32 normal range) or infinite, or the power of two leaves
+// the FP32 normal range, lo is zero.
+__device__ __forceinline__ double split_pair(double x) {
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const float h = d2f_bits(x);
+  const unsigned E = (hw >> 20) & 0x7FFu;
+  const unsigned r = (lw >> 28) & 1u;
+  const unsigned low = lw & 0x1FFFFFFFu;
+  const unsigned mag = r ? (0x20000000u - low) : low;  // |x - hi| in units of 2^(e - 52), at most 2^28
+  const float a = __uint_as_float(0x4B000000u | (mag >> 14)) - 8388608.0f;     // exact: below 2^15
+  const float b = __uint_as_float(0x4B000000u | (mag & 0x3FFFu)) - 8388608.0f;  // exact: below 2^14
+  const float m = fmaf(a, 16384.0f, b);
+  const int se = (int)E - 948;  // FP32 exponent field of 2^(e - 52)
+  const float scale = (se >= 1 && se <= 254 && E >= 897u && E <= 1150u) ? __uint_as_float((unsigned)se << 23) : 0.0f;
+  float l = m * scale;
+  // sign: x - hi has the sign of x when hi was rounded down in magnitude
+  l = ((hw >> 31) ^ r) ? -l : l;
+  return __hiloint2double((int)__float_as_uint(l), (int)__float_as_uint(h));
+}
 template <class To, class From>
 __host__ __device__ __forceinline__ To cvt(const From &x) { return To(x); }
 template <>
@@ -128,6 +157,15 @@ struct Nbhd {
     return __ldg(mixf + fslot * msf);
 #else
     return mixf[fslot * msf];
+#endif
+  }
+  // mixed path: the split pair (hi, lo) stored in place of the FP64 value
+  __host__ __device__ __forceinline__ float2 at2(int v, int off) const {
+    const float2 *q = reinterpret_cast<const float2 *>(c) + (v * fs + off);
+#ifdef __CUDA_ARCH__
+    return __ldg(q);
+#else
+    return *q;
 #endif
   }
 };
@@ -287,6 +325,161 @@ __host__ __device__ __forceinline__ D with_ko(const R &rhs, const D &ko, const S
   }
 }
 
+// ---- mixed path: differences on split pairs ----------------------------------------
+// In the mixed path the halo fill stores every field but alpha and phi as
+// a pair of FP32 numbers per tile point: hi = u rounded to FP32 and lo =
+// u - hi (exact in FP64) rounded to FP32, so hi + lo = u to within
+// 2^-48 |u| (split_pair below). The stencil differences are taken on the
+// pairs with FP32 operations, whose pipe is 64 times wider than the FP64
+// one on this GPU, and carry the accuracy of FP64 differences rounded once
+// to FP32:
+//  - a difference of two neighbours, u(+o) - u(-o) = (hi+ - hi-) + (lo+ -
+//    lo-): the FP32 subtraction of the high parts is exact when they are
+//    within a factor of two (Sterbenz) and otherwise within half an ulp of
+//    a result that does not cancel further in the first-derivative
+//    stencil;
+//  - a second difference u(+o) + u(-o) - 2 u(0), which cancels to O(dx^2 u''),
+//    from error-free differences of the high parts (Knuth's two-sum, sp_two_diff):
+//    (d+ + d-) + ((e+ + e-) + (lo+ + lo- - 2 lo0)), where d+ + d- is exact
+//    whenever it cancels (Sterbenz) and every other term is of order
+//    2^-24 |u|, so the result is the exact second difference up to its own
+//    rounding and 2^-48 |u|.
+// The FD4 stencil weights and the Kreiss-Oliger combination are then applied
+// in FP32 to these differences, as the mixed path applied them to the FP64
+// differences before.
+template <class R>
+__host__ __device__ __forceinline__ void ld2(const Nbhd &N, int v, int off, R &h, R &l) {
+  const float2 q = N.at2(v, off);
+  h = R(q.x);
+  l = R(q.y);
+}
+
+// a - b = s + e exactly (Knuth's two-sum applied to a and -b); returns s
+template <class R>
+__host__ __device__ __forceinline__ R sp_two_diff(const R &a, const R &b, R &e) {
+  const R s = a - b;
+  const R bv = s - a;
+  e = (a - (s - bv)) - (b + bv);
+  return s;
+}
+
+// u(+o) - u(-o)
+template <class R>
+__host__ __device__ __forceinline__ R sp_diff(const Nbhd &N, int v, int o) {
+  R hp, lp, hm, lm;
+  ld2<R>(N, v, o, hp, lp);
+  ld2<R>(N, v, -o, hm, lm);
+  return (hp - hm) + (lp - lm);
+}
+
+// u(+o) + u(-o) - 2 u(0), the centre pair (h0, l0) given
+template <class R>
+__host__ __device__ __forceinline__ R sp_second(const Nbhd &N, int v, int o, const R &h0, const R &l0) {
+  R hp, lp, hm, lm, ep, em;
+  ld2<R>(N, v, o, hp, lp);
+  ld2<R>(N, v, -o, hm, lm);
+  const R dp = sp_two_diff<R>(hp, h0, ep), dm = sp_two_diff<R>(hm, h0, em);
+  return (dp + dm) + ((ep + em) + fmaT(R(-2.0), l0, lp + lm));
+}
+
+// first derivative along stride s without the factor 1 / (12 dx)
+template <class R>
+__host__ __device__ __forceinline__ R sp_fd1u(const Nbhd &N, int v, int s) {
+  return fmaT(R(8.0), sp_diff<R>(N, v, s), -sp_diff<R>(N, v, 2 * s));
+}
+
+// Pure second derivatives along x, y, z (unscaled unless SCALED, which
+// applies c2 = 1 / (12 dx^2)) and the Kreiss-Oliger sum over the three
+// axes without its factor: sum over axes of b3 - 6 b2 + 15 b1, b_j the
+// second difference at distance j (the -20 u(0) of each axis is inside the
+// b_j). KO only: d2 == nullptr.
+template <class R, bool SCALED>
+__host__ __device__ __forceinline__ void sp_pure2_ko(const Nbhd &N, int v, const R &c2, R *d2, R &ko) {
+  R h0, l0;
+  ld2<R>(N, v, 0, h0, l0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int s = N.st[k];
+    const R b1 = sp_second<R>(N, v, s, h0, l0), b2 = sp_second<R>(N, v, 2 * s, h0, l0);
+    const R b3 = sp_second<R>(N, v, 3 * s, h0, l0);
+    if (d2) {
+      d2[k] = fmaT(R(16.0), b1, -b2);
+      if constexpr (SCALED) d2[k] = d2[k] * c2;
+    }
+    const R t = fmaT(R(15.0), b1, fmaT(R(-6.0), b2, b3));
+    ko = k == 0 ? t : ko + t;
+  }
+}
+
+// The mixed path's counterparts of fd1u, fd1o, ko_sum, second_ko and of
+// the centre value, dispatched on the precision split: D == R reads FP64
+// tiles, D != R split pairs (every field but alpha and phi).
+template <class D, class R>
+__host__ __device__ __forceinline__ R centre(const Nbhd &N, int v) {
+  if constexpr (std::is_same<D, R>::value) {
+    return ld<D>(N, v, 0);
+  } else {
+    R h, l;
+    ld2<R>(N, v, 0, h, l);
+    return h;
+  }
+}
+template <class D, class R>
+__host__ __device__ __forceinline__ R d1u(const Nbhd &N, int v, int s) {
+  if constexpr (std::is_same<D, R>::value) return fd1u<D, R>(N, v, s);
+  else return sp_fd1u<R>(N, v, s);
+}
+template <class D, class R>
+__host__ __device__ __forceinline__ R d1o(const Nbhd &N, int v, int s, const R &c1) {
+  if constexpr (std::is_same<D, R>::value) return fd1o<D, R>(N, v, s, c1);
+  else return sp_fd1u<R>(N, v, s) * c1;
+}
+template <class D, class R>
+__host__ __device__ __forceinline__ R kosum(const Nbhd &N, int v) {
+  if constexpr (std::is_same<D, R>::value) {
+    return ko_sum<D>(N, v);
+  } else {
+    R ko;
+    sp_pure2_ko<R, false>(N, v, R(0.0), nullptr, ko);
+    return ko;
+  }
+}
+template <class D, class R, bool SCALED>
+__host__ __device__ __forceinline__ void second_sp(const Nbhd &N, int v, const StencilCoef<D> &C,
+                                                   const StencilCoef<R> &CR, R dd[6], R &ko) {
+  if constexpr (std::is_same<D, R>::value) {
+    second_ko<D, R, SCALED>(N, v, C, CR, dd, ko);
+  } else {
+    R d2[3];
+    sp_pure2_ko<R, SCALED>(N, v, CR.c2, d2, ko);
+    dd[0] = d2[0];
+    dd[3] = d2[1];
+    dd[5] = d2[2];
+    const int m = mix_slot(v);
+    if constexpr (std::is_same<R, float>::value) {
+      const int fm = mix_fslot(m);
+      dd[1] = N.mixedf(fm);
+      dd[2] = N.mixedf(fm + 1);
+      dd[4] = N.mixedf(fm + 2);
+    } else {  // the counting types read the FP64 slots
+      dd[1] = R(N.mixed(m));
+      dd[2] = R(N.mixed(m + 1));
+      dd[4] = R(N.mixed(m + 2));
+    }
+  }
+}
+
+// A right-hand side plus the dissipation of a Kreiss-Oliger sum ko taken
+// in D (alpha, phi, and every field of the FP64 path) or in R (the other
+// fields of the mixed path).
+template <class D, class R, class K>
+__host__ __device__ __forceinline__ D add_ko(const R &rhs, const K &ko, const StencilCoef<D> &C,
+                                             const StencilCoef<R> &CR) {
+  if constexpr (std::is_same<D, R>::value) return fmaT(C.cko, ko, rhs);
+  else if constexpr (std::is_same<K, R>::value) return cvt<D>(fmaT(CR.cko, ko, rhs));
+  else return cvt<D>(fmaT(CR.cko, cvt<R>(ko), rhs));
+}
+
 // Parameters of the equations, combined on the host and stored in the
 // algebra type R (no per-point division or widening).
 template <class R>
@@ -354,8 +547,15 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
   R g[6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
-    gD[c] = ld<D>(N, GXX + c, 0);
-    g[c] = cvt<R>(gD[c]);
+    if constexpr (SAME) {
+      gD[c] = ld<D>(N, GXX + c, 0);
+      g[c] = cvt<R>(gD[c]);
+    } else {
+      // the FP64 metric (for the conformal-factor terms) from the split pair
+      R l;
+      ld2<R>(N, GXX + c, 0, g[c], l);
+      gD[c] = cvt<D>(g[c]) + cvt<D>(l);
+    }
   }
   // igw: the inverse with the off-diagonal entries doubled, for contractions
   // with a symmetric pair stored as six components
@@ -381,8 +581,8 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
   R be[3], Gh[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    be[i] = cvt<R>(ld<D>(N, BETAX + i, 0));
-    Gh[i] = cvt<R>(ld<D>(N, GHX + i, 0));
+    be[i] = centre<D, R>(N, BETAX + i);
+    Gh[i] = centre<D, R>(N, GHX + i);
   }
   CCZ4_MARK("inverse metric");
 
@@ -401,7 +601,7 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int c = 0; c < 6; ++c) dg[k][c] = fd1o<D, R>(N, GXX + c, N.st[k], c1h);  // (1/2) d_k g~_ij
+      for (int c = 0; c < 6; ++c) dg[k][c] = d1o<D, R>(N, GXX + c, N.st[k], c1h);  // (1/2) d_k g~_ij
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
@@ -556,13 +756,13 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
     for (int c = 0; c < 6; ++c) igwc[c] = igw[c];
   }
   R RZ[6], advGh[3];
-  D kog[6];
+  R kog[6];
   {
     R dG[3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) dG[k][i] = fd1o<D, R>(N, GHX + i, N.st[k], CR.c1);  // d_k Gamma-hat^i
+      for (int i = 0; i < 3; ++i) dG[k][i] = d1o<D, R>(N, GHX + i, N.st[k], CR.c1);  // d_k Gamma-hat^i
 #pragma unroll
     for (int i = 0; i < 3; ++i) advGh[i] = fmaT(be[0], dG[0][i], fmaT(be[1], dG[1][i], be[2] * dG[2][i]));
 #pragma unroll
@@ -571,7 +771,7 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
       for (int j = i; j < 3; ++j) {
         const int c = S6(i, j);
         R dd[6];
-        second_ko<D, R, !SAME>(N, GXX + c, C, CR, dd, kog[c]);  // FP64 path: pure ones unscaled
+        second_sp<D, R, !SAME>(N, GXX + c, C, CR, dd, kog[c]);  // FP64 path: pure ones unscaled
         R lap = igwc[0] * dd[0];
 #pragma unroll
         for (int q = 1; q < 6; ++q) lap = fmaT(igwc[q], dd[q], lap);
@@ -592,7 +792,7 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
   // ---- A~ contractions ---------------------------------------------------------------
   R A[6];
 #pragma unroll
-  for (int c = 0; c < 6; ++c) A[c] = cvt<R>(ld<D>(N, AXX + c, 0));
+  for (int c = 0; c < 6; ++c) A[c] = centre<D, R>(N, AXX + c);
   R Au[6], AgA[6];
   {
     R Am[3][3];  // A~_i^m = A~_il g~^lm
@@ -632,11 +832,11 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
-    for (int i = 0; i < 3; ++i) dB[k][i] = fd1o<D, R>(N, BETAX + i, N.st[k], CR.c1);
+    for (int i = 0; i < 3; ++i) dB[k][i] = d1o<D, R>(N, BETAX + i, N.st[k], CR.c1);
   const R third = R(1.0 / 3.0), twothird = R(2.0 / 3.0);
   const R trB = dB[0][0] + dB[1][1] + dB[2][2];
   const R trB23 = twothird * trB;
-  const R Th = cvt<R>(ld<D>(N, THETA, 0)), Kt = cvt<R>(ld<D>(N, KTR, 0));
+  const R Th = centre<D, R>(N, THETA), Kt = centre<D, R>(N, KTR);
   const R Kc = fmaT(-P.c2, Th, Kt);  // K - 2 c Theta
   const R al2 = al + al;
   {
@@ -659,12 +859,12 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
 #pragma unroll
       for (int j = i; j < 3; ++j) {
         const int c = S6(i, j);
-        sink(GXX + c, with_ko<D, R>(fmaT(g[c], sg, fmaT(-al2, A[c], advg[c] + (Xg[i][j] + Xg[j][i]))), kog[c], C, CR));
+        sink(GXX + c, add_ko<D, R>(fmaT(g[c], sg, fmaT(-al2, A[c], advg[c] + (Xg[i][j] + Xg[j][i]))), kog[c], C, CR));
         R advA = XA[i][j] + XA[j][i];  // the advection and Lie-derivative terms
 #pragma unroll
-        for (int k = 0; k < 3; ++k) advA = fmaT(bec1[k], fd1u<D, R>(N, AXX + c, N.st[k]), advA);
+        for (int k = 0; k < 3; ++k) advA = fmaT(bec1[k], d1u<D, R>(N, AXX + c, N.st[k]), advA);
         const R rA = fmaT(ph2al, RZ[c], fmaT(-ph2, DDa[c], fmaT(g[c], sA1, fmaT(A[c], sA2, fmaT(-al2, AgA[c], advA)))));
-        sink(AXX + c, with_ko<D, R>(rA, ko_sum<D>(N, AXX + c), C, CR));
+        sink(AXX + c, add_ko<D, R>(rA, kosum<D, R>(N, AXX + c), C, CR));
       }
   }
   CCZ4_MARK("rhs g A");
@@ -672,34 +872,34 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
   // ---- scalars ---------------------------------------------------------------------------------
   const R gK = (P.slicing == CCZ4_SLICING_ONE_PLUS_LOG) ? al2 : al * al;  // alpha^2 g(alpha)
   const R dP[3] = {cvt<R>(dPD[0]), cvt<R>(dPD[1]), cvt<R>(dPD[2])};
-  sink(ALPHA, with_ko<D, R>(fmaT(be[0], da[0], fmaT(be[1], da[1], fmaT(be[2], da[2], -gK * (Kc - P.K0)))), koA, C, CR));
-  sink(PHI, with_ko<D, R>(fmaT(be[0], dP[0], fmaT(be[1], dP[1], fmaT(be[2], dP[2], third * ph * fmaT(al, Kt, -trB)))), koP,
+  sink(ALPHA, add_ko<D, R>(fmaT(be[0], da[0], fmaT(be[1], da[1], fmaT(be[2], da[2], -gK * (Kc - P.K0)))), koA, C, CR));
+  sink(PHI, add_ko<D, R>(fmaT(be[0], dP[0], fmaT(be[1], dP[1], fmaT(be[2], dP[2], third * ph * fmaT(al, Kt, -trB)))), koP,
                           C, CR));
   // first differences of K and Theta without 1 / (12 dx): their advection
   // takes beta / (12 dx), the Gamma-hat equation coefficients with the factor
   R dK[3], dT[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    dK[k] = fd1u<D, R>(N, KTR, N.st[k]);
-    dT[k] = fd1u<D, R>(N, THETA, N.st[k]);
+    dK[k] = d1u<D, R>(N, KTR, N.st[k]);
+    dT[k] = d1u<D, R>(N, THETA, N.st[k]);
   }
   // the advection terms seeded with the other terms outside the factor alpha
   const R advK = fmaT(bec1[0], dK[0], fmaT(bec1[1], dK[1], fmaT(bec1[2], dK[2], -lapal)));
-  sink(KTR, with_ko<D, R>(fmaT(al, RpZ + fmaT(Kt, Kc, -P.k1a * Th), advK), ko_sum<D>(N, KTR), C, CR));
+  sink(KTR, add_ko<D, R>(fmaT(al, RpZ + fmaT(Kt, Kc, -P.k1a * Th), advK), kosum<D, R>(N, KTR), C, CR));
   const R ZA = R(0.5) * ph2 * fmaT(dGam[0], da[0], fmaT(dGam[1], da[1], dGam[2] * da[2]));  // Z^i A_i
   const R advT = fmaT(bec1[0], dT[0], fmaT(bec1[1], dT[1], fmaT(bec1[2], dT[2], -ZA)));
-  sink(THETA, with_ko<D, R>(fmaT(al, fmaT(P.e2h, RpZ + fmaT(twothird * Kt, Kt, -AA), -Th * fmaT(Kt, P.c, P.k1b)), advT),
-                            ko_sum<D>(N, THETA), C, CR));
+  sink(THETA, add_ko<D, R>(fmaT(al, fmaT(P.e2h, RpZ + fmaT(twothird * Kt, Kt, -AA), -Th * fmaT(Kt, P.c, P.k1b)), advT),
+                            kosum<D, R>(N, THETA), C, CR));
   CCZ4_MARK("rhs scalars");
 
   // ---- d_t Gamma-hat^i, gauge --------------------------------------------------------------------
   R lapB[3], gdivB[3];  // g~^kl d_k d_l beta^i and d_k (d_l beta^l)
-  D koB[3];
+  R koB[3];
   {
     R ddB[3][6];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      second_ko<D, R, !SAME>(N, BETAX + i, C, CR, ddB[i], koB[i]);  // FP64 path: pure ones unscaled
+      second_sp<D, R, !SAME>(N, BETAX + i, C, CR, ddB[i], koB[i]);  // FP64 path: pure ones unscaled
       R s = igwc[0] * ddB[i][0];
 #pragma unroll
       for (int q = 1; q < 6; ++q) s = fmaT(igwc[q], ddB[i][q], s);
@@ -744,24 +944,24 @@ __host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const 
     t = fmaT(k3h, ZB, t);
     // - G~^k B_k^i; d_t Gamma-hat^i - beta^k d_k Gamma-hat^i
     dbK[i] = fmaT(-Gc[0], dB[0][i], fmaT(-Gc[1], dB[1][i], fmaT(-Gc[2], dB[2][i], t)));
-    sink(GHX + i, with_ko<D, R>(advGh[i] + dbK[i], ko_sum<D>(N, GHX + i), C, CR));
+    sink(GHX + i, add_ko<D, R>(advGh[i] + dbK[i], kosum<D, R>(N, GHX + i), C, CR));
   }
   if (P.shift == CCZ4_SHIFT_GAMMA_DRIVER) {
-    const R bb[3] = {cvt<R>(ld<D>(N, BBX, 0)), cvt<R>(ld<D>(N, BBY, 0)), cvt<R>(ld<D>(N, BBZ, 0))};
+    const R bb[3] = {centre<D, R>(N, BBX), centre<D, R>(N, BBY), centre<D, R>(N, BBZ)};
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      sink(BETAX + i, with_ko<D, R>(fmaT(be[0], dB[0][i], fmaT(be[1], dB[1][i], fmaT(be[2], dB[2][i], P.f * bb[i]))), koB[i],
+      sink(BETAX + i, add_ko<D, R>(fmaT(be[0], dB[0][i], fmaT(be[1], dB[1][i], fmaT(be[2], dB[2][i], P.f * bb[i]))), koB[i],
                                 C, CR));
       R advb = fmaT(-P.eta, bb[i], dbK[i]);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) advb = fmaT(bec1[k], fd1u<D, R>(N, BBX + i, N.st[k]), advb);
-      sink(BBX + i, with_ko<D, R>(advb, ko_sum<D>(N, BBX + i), C, CR));
+      for (int k = 0; k < 3; ++k) advb = fmaT(bec1[k], d1u<D, R>(N, BBX + i, N.st[k]), advb);
+      sink(BBX + i, add_ko<D, R>(advb, kosum<D, R>(N, BBX + i), C, CR));
     }
   } else {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      sink(BETAX + i, with_ko<D, R>(R(0.0), koB[i], C, CR));
-      sink(BBX + i, with_ko<D, R>(R(0.0), ko_sum<D>(N, BBX + i), C, CR));
+      sink(BETAX + i, add_ko<D, R>(R(0.0), koB[i], C, CR));
+      sink(BBX + i, add_ko<D, R>(R(0.0), kosum<D, R>(N, BBX + i), C, CR));
     }
   }
   CCZ4_MARK("rhs gamma-hat gauge");

@@ -118,6 +118,21 @@ __device__ __forceinline__ double interp_value(const int (&c)[8], int rx, int ry
   return rz ? __dadd_rn(__dmul_rn(pw(rz, 0), u[0]), __dmul_rn(pw(rz, 1), u[1])) : u[0];
 }
 
+// Whether field v's tile holds split pairs: in the mixed path (F32W) every
+// field but alpha and phi, whose differences the mixed stage kernel takes
+// in FP64 (see split_pair).
+__device__ __forceinline__ bool split_field(bool f32w, int v) { return f32w && v != ALPHA && v != PHI; }
+
+// A tile value as the stage kernel reads it (the FP64 value or its split
+// pair), and the FP64 value back from the tile (hi + lo, within 2^-48 of
+// the value for a split pair).
+__device__ __forceinline__ double tile_enc(double u, bool split) { return split ? split_pair(u) : u; }
+__device__ __forceinline__ double tile_dec(const double *q, bool split) {
+  const double t = __ldcg(q);
+  if (!split) return t;
+  return f2d_bits(__uint_as_float((unsigned)__double2loint(t))) + f2d_bits(__uint_as_float((unsigned)__double2hiint(t)));
+}
+
 // One linear map of the interpolation between a and b for remainder r, the
 // product and the sum each rounded on its own; r = 0: a.
 __device__ __forceinline__ double lerp3(int r, double a, double b) {
@@ -164,7 +179,8 @@ __global__ void __launch_bounds__(FILL_THREADS, CCZ4_FILL_MIN_BLOCKS) fill_halos
       const int rx = r & 3, ry = (r >> 2) & 3, rz = (r >> 4) & 3;
       double *tp = tile + (long long)n * g.T3 + t;
 #pragma unroll 5
-      for (int v = 0; v < NV; ++v) __stcs(tp + (long long)v * g.n_patches * g.T3, interp_value(c, rx, ry, rz, src + v * g.S));
+      for (int v = 0; v < NV; ++v)
+        __stcs(tp + (long long)v * g.n_patches * g.T3, tile_enc(interp_value(c, rx, ry, rz, src + v * g.S), split_field(F32W, v)));
     }
   } else {
     for (int t = threadIdx.x; t < T3; t += blockDim.x) {
@@ -193,6 +209,7 @@ __global__ void __launch_bounds__(FILL_THREADS, CCZ4_FILL_MIN_BLOCKS) fill_halos
     const double *sv = src + v * g.S;
     double *tv = tile + ((long long)v * g.n_patches + n) * g.T3;
     const int slot = mix_slot(v);
+    const bool sp = split_field(F32W, v);
     if (MESH && nx > 0) {
       // x, then y, then z: the x and y results of the patch in the tile's
       // shared memory (host-checked to fit), the z results to the tile
@@ -211,7 +228,7 @@ __global__ void __launch_bounds__(FILL_THREADS, CCZ4_FILL_MIN_BLOCKS) fill_halos
       __syncthreads();
       for (int e = e0 + threadIdx.x; e < e1; e += FILL_THREADS) {
         const int k = __ldg(&g.zjob[e].yab);
-        __stcs(tv + __ldg(&g.zjob[e].t), lerp3((k >> (2 * JOB_BITS)) & 3, yv[k & JM], yv[(k >> JOB_BITS) & JM]));
+        __stcs(tv + __ldg(&g.zjob[e].t), tile_enc(lerp3((k >> (2 * JOB_BITS)) & 3, yv[k & JM], yv[(k >> JOB_BITS) & JM]), sp));
       }
       __syncthreads();  // the gather below overwrites the tile's shared memory
     }
@@ -226,14 +243,14 @@ __global__ void __launch_bounds__(FILL_THREADS, CCZ4_FILL_MIN_BLOCKS) fill_halos
         sx[u] = t < T3 ? idx[t] : -1;
         // on a mesh, interpolated points (s <= -2) were written by the pass
         // above: read back (through L2) only where the mixed derivatives need them
-        val[u] = sx[u] >= 0 ? __ldg(sv + sx[u]) : (MESH && slot >= 0 && sx[u] <= -2) ? __ldcg(tv + t) : 0.0;
+        val[u] = sx[u] >= 0 ? __ldg(sv + sx[u]) : (MESH && slot >= 0 && sx[u] <= -2) ? tile_dec(tv + t, sp) : 0.0;
       }
 #pragma unroll
       for (int u = 0; u < GATHER_BATCH; ++u) {
         const int t = t0 + u * FILL_THREADS;
         if (t < T3) {
           if (slot >= 0) ts[t] = val[u];
-          if (!MESH || sx[u] > -2) __stcs(tv + t, val[u]);  // read once, by the stage kernel
+          if (!MESH || sx[u] > -2) __stcs(tv + t, tile_enc(val[u], sp));  // read once, by the stage kernel
         }
       }
     }

@@ -251,17 +251,20 @@ def test_binary_puncture_full_size_sampled_parity():
     assert (np.abs(got - ref) / scale).max() < TOL
 
 
-@pytest.mark.parametrize("name,bc", [("three", "sommerfeld"), ("two", "periodic")])
-def test_separable_interpolation_equals_entry_by_entry(name, bc, monkeypatch):
+@pytest.mark.parametrize("name,bc,prec", [("three", "sommerfeld", "fp64"), ("two", "periodic", "fp64"),
+                                          ("three", "sommerfeld", "mixed")])
+def test_separable_interpolation_equals_entry_by_entry(name, bc, prec, monkeypatch):
     """The halo fill's separable evaluation of the coarse-to-fine
     interpolations (x, y, z passes sharing their results) gives the same
     tiles, bit for bit, as the point-by-point evaluation, and so the same
-    states after RK4 steps."""
+    states after RK4 steps (in the mixed path the tiles of split pairs and
+    the FP32 mixed derivatives taken from interpolated points read back
+    from them)."""
     from paper_2406_11626_gb300 import ccz4 as C
     dx = 0.3
     gg, _, lev, ijk, origin = mesh_pair(name, bc, dx=dx, shuffle=5)
     U, G = mesh_state(gg, lev, ijk, origin, dx, bc, seed=4, base="puncture", amp=0.01)
-    dt, P = 0.1 * I.level_spacing(dx, int(np.max(lev)) + 1)[-1], C.make_params(**PUNC)
+    dt, P = 0.1 * I.level_spacing(dx, int(np.max(lev)) + 1)[-1], C.make_params(**dict(PUNC, precision=prec))
     out = []
     for by_entry in ("0", "1"):
         monkeypatch.setenv("CCZ4_MESH_INTERP_BY_ENTRY", by_entry)
@@ -269,7 +272,7 @@ def test_separable_interpolation_equals_entry_by_entry(name, bc, monkeypatch):
         g.upload(U, G)
         if bc == "sommerfeld":
             g.upload(U, G, buf="INI")
-        g.fill_halos("U")
+        g.fill_halos("U", P=P)
         tiles = g.download("TILE")
         g.step(P, dt, 2)
         out.append((tiles, g.download("U")))
