@@ -20,6 +20,10 @@
 // costs about half the FP64 operations of evaluating each point's 16-point
 // tensor-product stencil on its own. The result is the same FD4 mixed
 // derivative (the tensor product of two first-derivative stencils).
+// For the mixed-precision stage kernel (F32W) the tiles of every field but
+// alpha and phi are written as split FP32 pairs (split_pair), and the
+// shared-memory tile of such a field holds the same pairs, from which the
+// inner first derivatives of g~ and beta are taken in FP32.
 #include "ccz4_algebra.cuh"
 #include "ccz4_internal.cuh"
 
@@ -56,16 +60,21 @@ struct LevelScale {
 
 // First stage of a mixed derivative at point e of the widened region: the
 // (unscaled) first derivative of the tile along stride si. FP64 differences
-// of the FP64 tile; the weights in FP64, or, for the fields whose mixed
+// of the FP64 tile and FP64 weights; or, for the fields whose mixed
 // derivatives the mixed path's stage kernel uses in FP32 (g~ and beta, f32
-// set), in FP32 with the result kept as FP32 (the split the stage kernel
-// applies to its own first derivatives).
+// set; their shared-memory tile holds the split pairs), the differences of
+// the pairs, (hi+ - hi-) + (lo+ - lo-), and the weights in FP32, with the
+// result kept as FP32 (as the stage kernel takes its own first derivatives).
 __device__ __forceinline__ void mixed_in(double *ext, int e, const double *ts, int c0, int si, bool f32) {
-  const double a = ts[c0 + si] - ts[c0 - si], b = ts[c0 + 2 * si] - ts[c0 - 2 * si];
-  if (f32)
-    reinterpret_cast<float *>(ext)[e] = fmaf(8.0f, d2f_bits(a), -d2f_bits(b));
-  else
+  if (f32) {
+    const float2 *tf = reinterpret_cast<const float2 *>(ts);
+    const float2 p1 = tf[c0 + si], m1 = tf[c0 - si], p2 = tf[c0 + 2 * si], m2 = tf[c0 - 2 * si];
+    const float a = (p1.x - m1.x) + (p1.y - m1.y), b = (p2.x - m2.x) + (p2.y - m2.y);
+    reinterpret_cast<float *>(ext)[e] = fmaf(8.0f, a, -b);
+  } else {
+    const double a = ts[c0 + si] - ts[c0 - si], b = ts[c0 + 2 * si] - ts[c0 - 2 * si];
     ext[e] = fma(8.0, a, -b);
+  }
 }
 
 // Second stage: d_a of the first derivatives at ext[e] along stride s, stored
@@ -123,15 +132,9 @@ __device__ __forceinline__ double interp_value(const int (&c)[8], int rx, int ry
 // in FP64 (see split_pair).
 __device__ __forceinline__ bool split_field(bool f32w, int v) { return f32w && v != ALPHA && v != PHI; }
 
-// A tile value as the stage kernel reads it (the FP64 value or its split
-// pair), and the FP64 value back from the tile (hi + lo, within 2^-48 of
-// the value for a split pair).
+// A tile value as the stage kernel reads it: the FP64 value or its split
+// pair. The fill's shared-memory tile of a field holds the same encoding.
 __device__ __forceinline__ double tile_enc(double u, bool split) { return split ? split_pair(u) : u; }
-__device__ __forceinline__ double tile_dec(const double *q, bool split) {
-  const double t = __ldcg(q);
-  if (!split) return t;
-  return f2d_bits(__uint_as_float((unsigned)__double2loint(t))) + f2d_bits(__uint_as_float((unsigned)__double2hiint(t)));
-}
 
 // One linear map of the interpolation between a and b for remainder r, the
 // product and the sum each rounded on its own; r = 0: a.
@@ -242,15 +245,18 @@ __global__ void __launch_bounds__(FILL_THREADS, CCZ4_FILL_MIN_BLOCKS) fill_halos
         const int t = t0 + u * FILL_THREADS;
         sx[u] = t < T3 ? idx[t] : -1;
         // on a mesh, interpolated points (s <= -2) were written by the pass
-        // above: read back (through L2) only where the mixed derivatives need them
-        val[u] = sx[u] >= 0 ? __ldg(sv + sx[u]) : (MESH && slot >= 0 && sx[u] <= -2) ? tile_dec(tv + t, sp) : 0.0;
+        // above: read back (through L2, already encoded) only where the mixed
+        // derivatives need them
+        val[u] = sx[u] >= 0 ? __ldg(sv + sx[u]) : (MESH && slot >= 0 && sx[u] <= -2) ? __ldcg(tv + t) : 0.0;
       }
 #pragma unroll
       for (int u = 0; u < GATHER_BATCH; ++u) {
         const int t = t0 + u * FILL_THREADS;
         if (t < T3) {
-          if (slot >= 0) ts[t] = val[u];
-          if (!MESH || sx[u] > -2) __stcs(tv + t, tile_enc(val[u], sp));  // read once, by the stage kernel
+          // encoded after all the batch's loads are in flight
+          const double w = (sp && sx[u] >= 0) ? split_pair(val[u]) : val[u];
+          if (slot >= 0) ts[t] = w;
+          if (!MESH || sx[u] > -2) __stcs(tv + t, w);  // read once, by the stage kernel
         }
       }
     }

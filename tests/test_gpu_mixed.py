@@ -117,3 +117,65 @@ def test_mixed_fill_keeps_fp32_slots_for_the_fp32_algebra():
         assert np.abs(got - ref).max() <= 1e-6 * max(np.abs(ref).max(), 1e-30), s
     for s in (18, 19, 20, 30, 31, 32):
         np.testing.assert_array_equal(raw[s], m64[s])
+
+
+def _ko_pieces(tiles, v, p):
+    """From an FP64 tile of field v: the largest first second difference
+    |u(x+h) + u(x-h) - 2u(x)| over the interior points and the three axes,
+    and the Kreiss-Oliger sum evaluated naively in FP32 (every value
+    rounded to FP32 first, the sum in FP32), shaped like the interior."""
+    t = tiles[v]
+    n = t.shape[0]
+    inner = (slice(None),) + (slice(3, 3 + p),) * 3
+
+    def shift(a, axis, k):
+        sl = [slice(None), slice(3, 3 + p), slice(3, 3 + p), slice(3, 3 + p)]
+        sl[axis] = slice(3 + k, 3 + k + p)
+        return a[tuple(sl)]
+
+    b1 = max(np.abs(shift(t, ax, 1) + shift(t, ax, -1) - 2.0 * t[inner]).max() for ax in (1, 2, 3))
+    t32 = t.astype(np.float32)
+    ko = np.zeros((n, p, p, p), np.float32)
+    for ax in (1, 2, 3):
+        s1 = shift(t32, ax, 1) + shift(t32, ax, -1)
+        s2 = shift(t32, ax, 2) + shift(t32, ax, -2)
+        s3 = shift(t32, ax, 3) + shift(t32, ax, -3)
+        ko += s3 - np.float32(6.0) * s2 + np.float32(15.0) * s1 - np.float32(20.0) * t32[inner]
+    return b1, ko
+
+
+def test_split_pair_differences_keep_fp64_accuracy_on_a_large_offset():
+    """The mixed path takes stencil differences on split FP32 pairs with the
+    accuracy of FP64 differences. With the zero-shift option the right-hand
+    sides of beta and b are their Kreiss-Oliger dissipation alone, and
+    dissipation is blind to a constant: on beta = 1000 + s and b = -500 + s
+    (s a smooth perturbation of size 1e-3) the mixed path must match the
+    FP64 oracle to within the FP32 rounding of the combination of the
+    second differences, about 4 x 2^-24 x 144 x eps/(64 dx) x max |second
+    difference|. Differences of values rounded to FP32 would miss that bar
+    by orders of magnitude (checked below on the same tiles in numpy)."""
+    p, npv, dx = 6, (3, 2, 2), 1.0 / 18
+    origin = (-0.5 * npv[0] * p * dx, -0.5 * npv[1] * p * dx, -0.5 * npv[2] * p * dx)
+    gg, og, ijk = make_pair(p, npv, origin, dx, "periodic", permute_seed=6)
+    U, G = random_state(p, npv, origin, dx, ijk, seed=9, bc="periodic")
+    offset = {"betax": 1000.0, "betay": 1000.0, "betaz": 1000.0, "bx": -500.0, "by": -500.0, "bz": -500.0}
+    for name, c in offset.items():
+        U[I.IDX[name]] = c + 0.05 * (U[I.IDX[name]] + U[I.IDX["gxx"]] - 1.0)
+    kw = dict(PUNC, shift="zero", ko_eps=0.3)
+    cp, op = both_params(**dict(kw, precision="mixed"))
+    gg.upload(U, G)
+    gg.rhs(cp, "U", "RHS")
+    rU, _ = gg.download("RHS")
+    oU, _ = og.rhs(op, U, G, G)
+    tiles = og.fill_tiles(U, G)
+    cko = kw["ko_eps"] / (64.0 * dx)
+    eps32 = 2.0 ** -24
+    for name in offset:
+        v = I.IDX[name]
+        b1, ko_naive = _ko_pieces(tiles, v, p)
+        bar = 4.0 * eps32 * 144.0 * cko * b1
+        err = np.abs(rU[v] - oU[v]).max()
+        assert np.abs(oU[v]).max() > 100.0 * bar, name      # the dissipation itself is resolved
+        assert err <= bar, (name, err, bar)
+        naive = np.abs(cko * ko_naive.astype(np.float64) - oU[v]).max()
+        assert naive > 100.0 * bar, (name, naive, bar)      # rounding the values first fails
