@@ -129,6 +129,18 @@ __host__ __device__ constexpr int S6(int i, int j) {
   return i > j ? S6(j, i) : (i == 0 ? j : (i == 1 ? 2 + j : 5));
 }
 
+// Tile loads of the stage kernel: the streaming (evict-first) hint, which
+// leaves L2 to the kernel's register spills (a tile is reused within a
+// block, through L1); 0 for the read-only path.
+#ifndef CCZ4_TILE_LOAD_CS
+#define CCZ4_TILE_LOAD_CS 1
+#endif
+#if CCZ4_TILE_LOAD_CS
+#define CCZ4_TLD __ldcs
+#else
+#define CCZ4_TLD __ldg
+#endif
+
 // Read-only view of the halo'd neighbourhood of one point.
 struct Nbhd {
   const double *__restrict__ c;    // field 0 at the centre point
@@ -140,7 +152,7 @@ struct Nbhd {
   long long msf;                   // distance between FP32 slots
   __host__ __device__ __forceinline__ double at(int v, int off) const {
 #ifdef __CUDA_ARCH__
-    return __ldg(c + v * fs + off);
+    return CCZ4_TLD(c + v * fs + off);
 #else
     return c[v * fs + off];
 #endif
@@ -163,7 +175,7 @@ struct Nbhd {
   __host__ __device__ __forceinline__ float2 at2(int v, int off) const {
     const float2 *q = reinterpret_cast<const float2 *>(c) + (v * fs + off);
 #ifdef __CUDA_ARCH__
-    return __ldg(q);
+    return CCZ4_TLD(q);
 #else
     return *q;
 #endif

@@ -27,11 +27,15 @@
 #ifndef CCZ4_INTERIOR_MIN_BLOCKS
 #define CCZ4_INTERIOR_MIN_BLOCKS 4
 #endif
-// The same for the mixed-precision instances (R = float): 5 blocks (102
-// registers) measured best (33.31 ms per step at 144^3 against 33.56 with 4
-// and 34.59 with 6).
+// The same for the mixed-precision instances (R = float): 3 blocks (168
+// registers). The mixed kernel is held by its register spills rather than
+// by the FP64 pipe; with 3 blocks their footprint (resident threads times
+// stack) fits in L2, and with the streaming hints below the tiles and the
+// state do not push it out (measured on GB300, ms per RK4 step at 144^3:
+// 26.16 against 28.30 with 5 blocks and plain loads, 28.21 with 5 blocks
+// and streaming, 29.88 with 3 blocks and plain loads).
 #ifndef CCZ4_INTERIOR_MIN_BLOCKS_MIXED
-#define CCZ4_INTERIOR_MIN_BLOCKS_MIXED 5
+#define CCZ4_INTERIOR_MIN_BLOCKS_MIXED 3
 #endif
 // Register spills of the stage kernel go to shared memory first (the
 // kernel uses none otherwise; ptxas places 104 bytes per thread there) and
@@ -41,7 +45,29 @@
 #define CCZ4_SMEM_SPILL 1
 #endif
 
+// State, accumulator and output of the stage update: streaming
+// (evict-first) loads and stores, each value is touched once, which leaves
+// L2 to the kernel's register spills; 0 for plain ones.
+#ifndef CCZ4_STAGE_STREAM
+#define CCZ4_STAGE_STREAM 1
+#endif
+
 namespace ccz4 {
+
+__device__ __forceinline__ double st_ld(const double *p) {
+#if CCZ4_STAGE_STREAM
+  return __ldcs(p);
+#else
+  return *p;
+#endif
+}
+__device__ __forceinline__ void st_st(double *p, double v) {
+#if CCZ4_STAGE_STREAM
+  __stcs(p, v);
+#else
+  *p = v;
+#endif
+}
 
 struct StageArgs {
   const double *U;  // U_n
@@ -97,12 +123,12 @@ struct StageSink {
   __device__ __forceinline__ void operator()(int v, double k) {
     const long long o = v * g.S + i;
     if (MODE < 0) {
-      a.out[o] = k;
+      st_st(a.out + o, k);
       return;
     }
-    double acc = MODE == 0 ? 0.0 : a.acc[o];
-    const double un = rk_combine<(MODE < 0 ? 0 : MODE), double>(a.U[o], acc, k, a.dt);
-    if (MODE < 3) a.acc[o] = acc;
+    double acc = MODE == 0 ? 0.0 : st_ld(a.acc + o);
+    const double un = rk_combine<(MODE < 0 ? 0 : MODE), double>(st_ld(a.U + o), acc, k, a.dt);
+    if (MODE < 3) st_st(a.acc + o, acc);
     if (MODE == 3 && v >= GXX && v <= GZZ) {
       ug[v - GXX] = un;
       return;
@@ -111,15 +137,15 @@ struct StageSink {
       uA[v - AXX] = un;
       return;
     }
-    a.out[o] = un;
+    st_st(a.out + o, un);
   }
   __device__ __forceinline__ void finish() {
     if (MODE != 3) return;
     enforce_point<double>(ug, uA);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      a.out[(GXX + c) * g.S + i] = ug[c];
-      a.out[(AXX + c) * g.S + i] = uA[c];
+      st_st(a.out + (GXX + c) * g.S + i, ug[c]);
+      st_st(a.out + (AXX + c) * g.S + i, uA[c]);
     }
   }
 };
