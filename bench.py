@@ -410,7 +410,7 @@ def run_gb300(args):
                         flm["fp32"] * cfg.n_points / (FP32_PEAK_TFLOPS * 1e12))
         mixed = {"value": world * cfg.n_points * 4 * K / (ms_mx * 1e-3), "unit": UNIT,
                  "speedup_vs_fp64": ms / ms_mx, "ms_per_step": ms_mx / K,
-                 "dtype": "f64 state/differences/1-over-phi terms/update + f32 algebra",
+                 "dtype": "f64 state/1-over-phi terms/update + f64-accurate differences on split f32 pairs + f32 algebra",
                  "max_rel_state_error_vs_fp64": float(err.max()),
                  "worst_field": I.FIELDS[int(err.argmax())],
                  "rel_state_error_per_field": {f: float(e) for f, e in zip(I.FIELDS, err)},

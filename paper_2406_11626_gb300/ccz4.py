@@ -306,7 +306,11 @@ class Grid:
     # -- the hot path -----------------------------------------------------------
     def fill_halos(self, buf="U", stream=None, P=None):
         """Halo fill of a state buffer; with parameters P, as the stage kernel
-        for P needs it (FP32 weights of the mixed derivatives in the mixed path)."""
+        for P needs it. In the mixed path, the tiles of every field but alpha
+        and phi then hold split FP32 pairs {hi, lo} (hi + lo = the FP64 value
+        within 2^-48 of it; view a downloaded tile field as float32 pairs),
+        and the mixed derivatives of g~ and beta are stored with FP32
+        weights as FP32."""
         if P is None:
             _check(lib().ccz4_fill_halos(self._h, _buf(buf), _stream(stream)))
         else:
