@@ -166,15 +166,16 @@ ccz4_status ccz4_download(ccz4_grid *g, int buf, double *U, double *G, void *str
    first-derivative stencils) into CCZ4_BUF_MIX. */
 ccz4_status ccz4_fill_halos(ccz4_grid *g, int buf, void *stream);
 
-/* The halo fill as the stage kernel for parameters P needs it: for
+/* The halo fill as the stage kernel for parameters P needs it. For
    P->precision == CCZ4_PREC_MIXED the tiles of every field but alpha and
    phi hold split FP32 pairs (see the TILE layout above), on which the
-   mixed stage kernel takes its stencil differences, and the mixed derivatives that
-   the mixed stage kernel uses in FP32 -- those of g~ and beta -- take their
-   differences in FP64 and their weights in FP32 and are stored as FP32 in
-   the first 27 x n_points floats of CCZ4_BUF_MIX (g~'s 18 slots, then
-   beta's 9), while those of alpha and phi stay FP64 in their slots
-   (and their tiles FP64); otherwise the buffers equal ccz4_fill_halos'. A mixed-precision
+   mixed stage kernel takes its stencil differences with the accuracy of
+   FP64 differences. The mixed derivatives that the mixed stage kernel uses
+   in FP32 -- those of g~ and beta -- take their inner differences on the
+   same pairs and everything else in FP32, and are stored as FP32 in the
+   first 27 x n_points floats of CCZ4_BUF_MIX (g~'s 18 slots, then beta's
+   9); those of alpha and phi stay FP64 in their slots (and their tiles
+   FP64). Otherwise the buffers equal ccz4_fill_halos'. A mixed-precision
    ccz4_rk_stage must follow this fill (ccz4_rhs, ccz4_step and
    ccz4_step_graph fill this way). */
 ccz4_status ccz4_fill_halos_for(ccz4_grid *g, int buf, const ccz4_params *P, void *stream);

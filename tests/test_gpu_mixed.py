@@ -77,8 +77,9 @@ def test_mixed_puncture_evolution_tracks_fp64():
 
 def test_mixed_fill_keeps_fp32_slots_for_the_fp32_algebra():
     """For the mixed path the halo fill takes the mixed derivatives of g~ and
-    beta (used in FP32 by the mixed stage kernel) with FP64 differences and
-    FP32 weights and stores them as FP32 in the first 27 float slots of the
+    beta (used in FP32 by the mixed stage kernel) with inner differences on
+    the split pairs and FP32 weights and outer differences, and stores them
+    as FP32 in the first 27 float slots of the
     buffer; those of alpha and phi (used in FP64 next to 1/phi) stay FP64 and
     equal the FP64 fill bit for bit. The tiles of alpha and phi equal the
     FP64 fill's; every other field's tile holds the split pair of the FP64
