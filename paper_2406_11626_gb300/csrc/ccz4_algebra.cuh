@@ -129,9 +129,10 @@ __host__ __device__ constexpr int S6(int i, int j) {
   return i > j ? S6(j, i) : (i == 0 ? j : (i == 1 ? 2 + j : 5));
 }
 
-// Tile loads of the stage kernel: the streaming (evict-first) hint, which
-// leaves L2 to the kernel's register spills (a tile is reused within a
-// block, through L1); 0 for the read-only path.
+// Tile loads through Nbhd (the stage kernel and the constraint monitors):
+// the streaming (evict-first) hint, which leaves L2 to the stage kernel's
+// register spills (a tile is reused within a block, through L1); 0 for the
+// read-only path.
 #ifndef CCZ4_TILE_LOAD_CS
 #define CCZ4_TILE_LOAD_CS 1
 #endif
