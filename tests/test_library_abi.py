@@ -48,3 +48,8 @@ def test_flop_count_is_available_without_a_gpu():
     assert f64["fp32"] == 0 and 2500 < f64["fp64"] < 4000 and f64["conversions"] == 0
     assert f64["fp64"] == 2 * f64["fp64_fma"] + f64["fp64_add_mul"] + f64["fp64_div_root"]
     assert fmx["fp32"] > 1000 and fmx["fp64"] < f64["fp64"] and fmx["conversions"] > 0
+    # the mixed path's stencil differences (every field but alpha and phi) run on split FP32
+    # pairs: what stays FP64 is the 1/phi terms, the differences of alpha and phi and the
+    # update, under a fifth of the FP64 path's work; the differences add thousands of FP32 flops
+    assert fmx["fp64"] < 0.2 * f64["fp64"] and fmx["fp32"] > 5000
+    assert fmx["fp64"] == 2 * fmx["fp64_fma"] + fmx["fp64_add_mul"] + fmx["fp64_div_root"]
