@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gpu_common import both_params, make_pair, random_state, rel_err
+from gpu_common import both_params, ko_pieces, make_pair, offset_state, random_state, rel_err
 from paper_2406_11626_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -120,31 +120,6 @@ def test_mixed_fill_keeps_fp32_slots_for_the_fp32_algebra():
         np.testing.assert_array_equal(raw[s], m64[s])
 
 
-def _ko_pieces(tiles, v, p):
-    """From an FP64 tile of field v: the largest first second difference
-    |u(x+h) + u(x-h) - 2u(x)| over the interior points and the three axes,
-    and the Kreiss-Oliger sum evaluated naively in FP32 (every value
-    rounded to FP32 first, the sum in FP32), shaped like the interior."""
-    t = tiles[v]
-    n = t.shape[0]
-    inner = (slice(None),) + (slice(3, 3 + p),) * 3
-
-    def shift(a, axis, k):
-        sl = [slice(None), slice(3, 3 + p), slice(3, 3 + p), slice(3, 3 + p)]
-        sl[axis] = slice(3 + k, 3 + k + p)
-        return a[tuple(sl)]
-
-    b1 = max(np.abs(shift(t, ax, 1) + shift(t, ax, -1) - 2.0 * t[inner]).max() for ax in (1, 2, 3))
-    t32 = t.astype(np.float32)
-    ko = np.zeros((n, p, p, p), np.float32)
-    for ax in (1, 2, 3):
-        s1 = shift(t32, ax, 1) + shift(t32, ax, -1)
-        s2 = shift(t32, ax, 2) + shift(t32, ax, -2)
-        s3 = shift(t32, ax, 3) + shift(t32, ax, -3)
-        ko += s3 - np.float32(6.0) * s2 + np.float32(15.0) * s1 - np.float32(20.0) * t32[inner]
-    return b1, ko
-
-
 def test_split_pair_differences_keep_fp64_accuracy_on_a_large_offset():
     """The mixed path takes stencil differences on split FP32 pairs with the
     accuracy of FP64 differences. With the zero-shift option the right-hand
@@ -158,10 +133,7 @@ def test_split_pair_differences_keep_fp64_accuracy_on_a_large_offset():
     p, npv, dx = 6, (3, 2, 2), 1.0 / 18
     origin = (-0.5 * npv[0] * p * dx, -0.5 * npv[1] * p * dx, -0.5 * npv[2] * p * dx)
     gg, og, ijk = make_pair(p, npv, origin, dx, "periodic", permute_seed=6)
-    U, G = random_state(p, npv, origin, dx, ijk, seed=9, bc="periodic")
-    offset = {"betax": 1000.0, "betay": 1000.0, "betaz": 1000.0, "bx": -500.0, "by": -500.0, "bz": -500.0}
-    for name, c in offset.items():
-        U[I.IDX[name]] = c + 0.05 * (U[I.IDX[name]] + U[I.IDX["gxx"]] - 1.0)
+    U, G, offset = offset_state(p, npv, origin, dx, ijk)
     kw = dict(PUNC, shift="zero", ko_eps=0.3)
     cp, op = both_params(**dict(kw, precision="mixed"))
     gg.upload(U, G)
@@ -173,7 +145,7 @@ def test_split_pair_differences_keep_fp64_accuracy_on_a_large_offset():
     eps32 = 2.0 ** -24
     for name in offset:
         v = I.IDX[name]
-        b1, ko_naive = _ko_pieces(tiles, v, p)
+        b1, ko_naive = ko_pieces(tiles, v, p)
         bar = 4.0 * eps32 * 144.0 * cko * b1
         err = np.abs(rU[v] - oU[v]).max()
         assert np.abs(oU[v]).max() > 100.0 * bar, name      # the dissipation itself is resolved
