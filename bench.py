@@ -36,6 +36,32 @@ KERNEL_SOURCES = ("paper_2406_11626_gb300/csrc/stage_kernels.cuh", "paper_2406_1
                   "paper_2406_11626_gb300/csrc/ccz4_internal.cuh")
 
 
+def measure_fma_peaks():
+    """FP64 and FP32 FMA throughput of this GPU (TFLOP/s), from the probe in
+    paper_2406_11626_gb300/measure (eight independent FMA chains per thread,
+    eight blocks of 256 threads per SM), or None if its library is missing."""
+    import ctypes
+    path = os.path.join(ROOT, "paper_2406_11626_gb300", "lib", "libccz4_peaks.so")
+    if not os.path.exists(path):
+        return None
+    L = ctypes.CDLL(path)
+    f = L.ccz4_probe_fma_rate
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                  ctypes.POINTER(ctypes.c_double)]
+    f.restype = ctypes.c_int
+    out = {}
+    for prec, iters in ((64, 4000), (32, 200000)):
+        best = 0.0
+        for _ in range(3):
+            t, ms = ctypes.c_double(), ctypes.c_double()
+            if f(prec, 8, iters, ctypes.byref(t), ctypes.byref(ms)) != 0:
+                return None
+            best = max(best, t.value)
+        out["fp%d_tflops" % prec] = best
+    out["how"] = "FMA-chain probe (measure/fma_peaks.cu), best of 3 launches of 8 x 256-thread blocks per SM"
+    return out
+
+
 def kernel_hash():
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
@@ -153,31 +179,86 @@ def time_oracle(n_steps, n_warm=0, workload="puncture144"):
     return cfg, dt
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def time_oracle_threads(n_steps, n_threads, workload="puncture144"):
+    """The oracle on all host cores: n_threads threads, each stepping its
+    own copy of the sample n_steps times (the oracle's C code holds no
+    shared mutable state, and ctypes releases the interpreter lock during
+    each call, so the copies run in parallel). Returns (cfg, wall seconds)."""
+    import threading
+    import oracle as O
+    from paper_2406_11626_gb300 import inputs as I
+    cfg = oracle_sample_config(workload)
+    P = O.make_params(**cfg.params)
+    U0, G0 = I.initial_state(cfg)
+    grids = [O.Grid(cfg.p, cfg.np, cfg.ijk(), cfg.origin, cfg.dx, cfg.bc, level=getattr(cfg, "level", None))
+             for _ in range(n_threads)]
+    start = threading.Barrier(n_threads + 1)
+    done = threading.Barrier(n_threads + 1)
+
+    def work(og):
+        U, G = U0, G0
+        start.wait()
+        for _ in range(n_steps):
+            U, G = og.rk4_step(P, cfg.dt, U, G, G0)
+        done.wait()
+
+    th = [threading.Thread(target=work, args=(og,)) for og in grids]
+    for t in th:
+        t.start()
+    start.wait()
+    t0 = time.perf_counter()
+    done.wait()
+    wall = time.perf_counter() - t0
+    for t in th:
+        t.join()
+    return cfg, wall
+
+
 def cpu_baseline(target_s=12.0, workload="puncture144"):
+    """The oracle on the host: all cores (one sample per core, in parallel)
+    as the value, and one core beside it."""
     cfg, t1 = time_oracle(1, workload=workload)
-    n = max(1, int(target_s / max(t1, 1e-3)))
+    n = max(1, int(target_s / 2 / max(t1, 1e-3)))
     cfg, t = time_oracle(n, workload=workload)
-    v = cfg.n_points * 4 * n / t
-    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d RK4 steps of the same puncture physics and dx on %s, single-threaded plain C FP64"
-                      % (n, sample_text(cfg))}
+    v1 = cfg.n_points * 4 * n / t
+    cores = host_cores()
+    cfg, tw = time_oracle_threads(n, cores, workload=workload)
+    v = cfg.n_points * 4 * n * cores / tw
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d RK4 steps of the same puncture physics and dx on %s per core, plain C FP64, "
+                      "one independent copy per host core in parallel" % (n, sample_text(cfg)),
+            "single_core": {"value": v1, "cores": 1, "sample": "%d RK4 steps on one copy, one thread" % n}}
 
 
 def run_reference(args):
+    """The oracle as it stands, on all host cores: each timed step is one
+    RK4 step of the bounded sample on every core (one independent copy per
+    core, in parallel)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     wl = args.workload
-    cfg, _ = time_oracle(args.warmup, workload=wl) if args.warmup > 0 else (oracle_sample_config(wl), 0.0)
-    cfg, t = time_oracle(max(args.steps, 1), workload=wl)
-    v = cfg.n_points * 4 * max(args.steps, 1) / t
+    cores = host_cores()
+    if args.warmup > 0:
+        time_oracle_threads(args.warmup, cores, workload=wl)
+    steps = max(args.steps, 1)
+    cfg, t = time_oracle_threads(steps, cores, workload=wl)
+    v = cfg.n_points * 4 * steps * cores / t
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / max(args.steps, 1) * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": workload_config(None, workload=wl),
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "each step: one RK4 step of the puncture physics on " + sample_text(cfg)},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "each step: one RK4 step of the puncture physics on " + sample_text(cfg)
+                                   + " on each of the %d host cores (one copy per core, in parallel)" % cores},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -242,17 +323,17 @@ def _has_children(cfg, n):
 # ----------------------------------------------------------------------------
 def load_traffic(n_points, precision="fp64", mesh=False):
     """DRAM bytes of one stage-kernel launch over n_points, from the ncu
-    capture recorded in profiles/traffic.json (FP64, single-level instance),
-    scaled by points; None for another kernel instance (mixed precision, a
-    refined mesh) or once the kernel sources have changed."""
+    capture of the single-level instance of that precision recorded in
+    profiles/traffic.json, scaled by points; None for a refined mesh, for a
+    precision without a record, or once the kernel sources have changed."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
-    if d.get("kernel_hash") != kernel_hash() or precision != "fp64" or mesh:
+    if d.get("kernel_hash") != kernel_hash() or mesh:
         return None
-    cap = d.get("captured", {})
+    cap = d.get(precision, {})
     if not cap.get("points"):
         return None
     return (cap["dram_bytes_read"] + cap["dram_bytes_write"]) * n_points / cap["points"]
@@ -335,6 +416,26 @@ def time_path(C, I, cfg, precision, K, W, stream, dist, clocks_index=None):
     return g, P, ms, stage_ms, clocks
 
 
+def time_graph(g, P, dt, K, W, stream, dist):
+    """K RK4 steps through ccz4_step_graph (one captured CUDA graph per step,
+    the path a time loop of the library runs), after W warm-up replays (the
+    first one captures the graph); returns milliseconds."""
+    import torch
+    g.step_graph(P, dt, max(W, 1), stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    g.step_graph(P, dt, K, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    return e0.elapsed_time(e1)
+
+
 def max_over_ranks(x, dist, device):
     """The largest value of x over the ranks (the slowest rank sets the job time)."""
     import torch
@@ -370,6 +471,8 @@ def run_gb300(args):
     ms = max_over_ranks(ms, dist, "cuda")
     value = job_rate(world, cfg.n_points, 4 * K, ms * 1e-3)
     out = g.constraints("U", raise_nonfinite=False)
+    ms_graph = max_over_ranks(time_graph(g, P, cfg.dt, K, args.warmup, stream, dist), dist, "cuda")
+    peaks = measure_fma_peaks() if rank == 0 else None
 
     # end to end through the C ABI from pinned host memory, one step per call
     n_state = g.n_points + g.n_ghost
@@ -417,7 +520,8 @@ def run_gb300(args):
                  "rms_state_error_per_field": {f: float(e) for f, e in zip(I.FIELDS, err2)},
                  "after_steps": K + args.warmup,
                  "L2_H": cmx[0], "L2_H_fp64": c64[0], "L2_M": cmx[1], "L2_M_fp64": c64[1],
-                 "roofline_frac": t_roof_mx / t_stage_mx,
+                 "roofline_frac": t_roof_mx / t_stage_mx, "stage_kernel_ms": t_stage_mx * 1e3,
+                 "traffic": load_traffic(cfg.n_points, "mixed", g.n_levels > 1),
                  "fp64_flops_per_point_stage": flm["fp64"], "fp32_flops_per_point_stage": flm["fp32"]}
         del g64, gmx
 
@@ -434,14 +538,15 @@ def run_gb300(args):
                 "frac": f64 / t_stage / 1e12 / FP64_PEAK_TFLOPS, "traffic": load_traffic(cfg.n_points, args.precision, g.n_levels > 1),
                 "kernel": "interior_kernel (fused RHS + RK stage) with the ghost-cell kernel of the same stage",
                 "flops_per_point_stage": fl["fp64"], "units_per_launch": cfg.n_points,
-                "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz"}
+                "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz",
+                "peak_measured": peaks}
     else:
         t_roof = max(f64 / (FP64_PEAK_TFLOPS * 1e12), f32 / (FP32_PEAK_TFLOPS * 1e12))
         roof = {"bound": "alu", "achieved": f64 / t_stage / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": t_roof / t_stage, "traffic": load_traffic(cfg.n_points, args.precision, g.n_levels > 1),
                 "fp64_flops_per_point_stage": fl["fp64"], "fp32_flops_per_point_stage": fl["fp32"],
                 "fp32_tflops": f32 / t_stage / 1e12,
-                "note": "frac = max(F64/P64, F32/P32) / kernel time"}
+                "note": "frac = max(F64/P64, F32/P32) / kernel time", "peak_measured": peaks}
     launches_per_stage = 2 + (1 if g.n_ghost > 0 else 0)
     restrict_per_step = g.n_levels - 1
     line = {
@@ -458,6 +563,11 @@ def run_gb300(args):
                 "d2h_bytes_per_step": 8 * I.NV * n_state,
                 "how": "ccz4_evolve_host per step: pinned host state -> device, one RK4 step, device -> host"},
         "gpu_launches": (launches_per_stage * 4 + restrict_per_step) * K,
+        "graph": {"value": job_rate(world, cfg.n_points, 4 * K, ms_graph * 1e-3), "unit": UNIT,
+                  "ms_per_step": ms_graph / K, "gpu_launches": (launches_per_stage * 4 + restrict_per_step) * K,
+                  "how": "ccz4_step_graph: each RK4 step one replay of a captured CUDA graph (the halo fills, "
+                         "stage kernels, ghost kernels and restriction of the step), the same K steps after the "
+                         "launch-path run; value and the kernel times above come from the launch path"},
         "constraints_after": {"L2_H": out[0], "L2_M": out[1], "max_H": out[2], "nonfinite": out[4]},
     }
     if mixed is not None:

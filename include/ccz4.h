@@ -251,9 +251,14 @@ ccz4_status ccz4_constraints(ccz4_grid *g, int buf, double out[5], double *dev_H
    host framework that owns all device memory and forbids other
    allocations, or a time loop that must not allocate once running). The
    paper has no counterpart; this is a service of this library.
-   Computes what ccz4_constraints computes, but from halo tiles the caller
-   already holds, and allocates nothing: it calls no cudaMalloc, cudaFree
-   or allocating library routine.
+   Computes what ccz4_constraints computes for a grid of one uniform level,
+   but from halo tiles the caller already holds, and allocates nothing: it
+   calls no cudaMalloc, cudaFree or allocating library routine.
+   Single level only: every patch is differenced with the one spacing dx
+   and counted in the norms. The tile buffer of a refined mesh
+   (ccz4_alloc_mesh) has the same layout but patches of several spacings
+   and covered coarse points; given it, this call returns wrong norms
+   without an error, so use ccz4_constraints for meshes.
      tiles    device, [25][n_patches][(p+6)^3] halo tiles in the layout of
               CCZ4_BUF_TILE (for instance that buffer after ccz4_fill_halos)
      dev_H    device [n_points] or NULL; dev_M device [3][n_points] or NULL
@@ -262,8 +267,11 @@ ccz4_status ccz4_constraints(ccz4_grid *g, int buf, double out[5], double *dev_H
    n_points = n_patches * p^3 must not exceed 4,194,304: the per-block
    partial sums of the reduction live in one fixed device array of
    640 KiB that every GPU loading this library holds until the process
-   exits. The first call on a device looks up that array's address on
-   the current device; make that first call before any stream capture.
+   exits. p above 161 is rejected before any size is formed. The first
+   call on a device looks up that array's address on the current device
+   and keeps it for the life of the process; make that first call before
+   any stream capture, and do not call this entry point again on a device
+   that the process has reset (cudaDeviceReset).
    Every call shares the array and leaves its partial sums in it (each
    call overwrites all the entries it reads), so calls that overlap on
    the GPU race: serialise them, e.g. on one stream. Sizes beyond the

@@ -1,7 +1,10 @@
 """Builds the CCZ4 CUDA library for sm_103a, in tree.
 
 Each translation unit under csrc/ is compiled by nvcc in parallel into
-_build/, then linked into lib/libccz4_gb300.so. Rebuilds only what changed.
+_build/, then linked into lib/libccz4_gb300.so. The FMA-throughput probe
+under measure/ (used by bench.py to measure the FP64 and FP32 pipe rates)
+is linked into a library of its own, lib/libccz4_peaks.so, so the product
+library carries no measurement code. Rebuilds only what changed.
 """
 import concurrent.futures as cf
 import glob
@@ -13,7 +16,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
+MEASURE = os.path.join(PKG, "measure")
 LIB = os.path.join(LIBDIR, "libccz4_gb300.so")
+PEAKS_LIB = os.path.join(LIBDIR, "libccz4_peaks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
                      "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
@@ -43,6 +48,14 @@ def _compile(src):
     return obj
 
 
+def _link(lib, objs):
+    if not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib + ".tmp%d" % os.getpid()
+        cmd = [_nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
+        subprocess.check_call(cmd)
+        os.replace(tmp, lib)
+
+
 def build(force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
@@ -50,13 +63,11 @@ def build(force: bool = False) -> str:
         for f in glob.glob(os.path.join(BUILD, "*.o")):
             os.remove(f)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(_compile, srcs))
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = [_nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
-        subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
+    probes = sorted(glob.glob(os.path.join(MEASURE, "*.cu")))
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs) + len(probes))) as ex:
+        objs = list(ex.map(_compile, srcs + probes))
+    _link(LIB, objs[:len(srcs)])
+    _link(PEAKS_LIB, objs[len(srcs):])
     return LIB
 
 

@@ -24,13 +24,18 @@ namespace {
 // 16384 x 5 doubles = 640 KiB of device memory.
 constexpr int kMaxBlocks = 16384;
 constexpr long long kMaxPoints = (long long)kMaxBlocks * 256;
+// largest patch edge whose p^3 fits within kMaxPoints (161^3 = 4,173,281)
+constexpr int kMaxEdge = 161;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_partials[kMaxBlocks * 5];
 
 // Device address of g_partials on each device. In host code the name
 // g_partials is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current. The
+// address is kept for the life of the process: after a reset of the device
+// (cudaDeviceReset) the module may load elsewhere, so a process that resets
+// a device must not call this entry point again on it.
 double *g_partials_addr[kMaxDevices] = {nullptr};
 std::mutex g_setup_mutex;
 
@@ -67,12 +72,13 @@ extern "C" ccz4_status ccz4_constraints_noalloc(const double *tiles, int p, int 
     set_error("constraints_noalloc: tiles and dev_out must be given, p >= 1, n_patches >= 1, dx > 0");
     return CCZ4_ERR_INVALID;
   }
-  const long long n_points = (long long)n_patches * p * p * p;
-  if (n_points > kMaxPoints) {
-    set_error("constraints_noalloc: %lld points exceed the maximum of %lld (fixed scratch of %d blocks)",
-              n_points, kMaxPoints, kMaxBlocks);
+  // bound p before any product is formed, so that no size can overflow
+  if (p > kMaxEdge || (long long)n_patches > kMaxPoints / ((long long)p * p * p)) {
+    set_error("constraints_noalloc: %d patches of %d^3 points exceed the maximum of %lld points (fixed scratch "
+              "of %d blocks)", n_patches, p, kMaxPoints, kMaxBlocks);
     return CCZ4_ERR_INVALID;
   }
+  const long long n_points = (long long)n_patches * p * p * p;
   double *partials = nullptr;
   ccz4_status st = partials_address(&partials);
   if (st != CCZ4_OK) return st;

@@ -66,13 +66,15 @@ def test_traffic_is_scaled_by_points_and_kept_to_the_captured_kernel(tmp_path, m
     prof = tmp_path / "profiles"
     prof.mkdir()
     rec = {"kernel_hash": bench.kernel_hash(),
-           "captured": {"points": 1000, "dram_bytes_read": 3.0e6, "dram_bytes_write": 1.0e6}}
+           "fp64": {"points": 1000, "dram_bytes_read": 3.0e6, "dram_bytes_write": 1.0e6},
+           "mixed": {"points": 2000, "dram_bytes_read": 1.0e6, "dram_bytes_write": 1.0e6}}
     (prof / "traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     # kernel_hash reads the kernel sources under ROOT: keep the real ones
     monkeypatch.setattr(bench, "kernel_hash", lambda h=rec["kernel_hash"]: h)
     assert bench.load_traffic(5000) == 2.0e7                 # 4 kB per point x 5000
-    assert bench.load_traffic(5000, "mixed") is None         # another kernel instance
+    assert bench.load_traffic(5000, "mixed") == 5.0e6        # its own record: 1 kB per point
+    assert bench.load_traffic(5000, "other") is None         # a kernel instance without a record
     assert bench.load_traffic(5000, mesh=True) is None
     rec["kernel_hash"] = "0" * 16                            # sources changed since the capture
     (prof / "traffic.json").write_text(json.dumps(rec))

@@ -39,6 +39,12 @@ def test_bench_line_has_the_contract_keys():
     assert e["value"] > 0 and e["h2d_bytes_per_step"] == e["d2h_bytes_per_step"] == 25 * pts * 8 + 25 * 8 * (
         d["config"]["ghost_cells"])
     assert d["gpu_launches"] > 0 and d["clocks"]["sm_mhz"] > 0
+    # the CUDA-graph path runs the same kernels: within 20 % of the launch path per step
+    gr = d["graph"]
+    assert gr["value"] > 0 and abs(gr["ms_per_step"] - d["ms_per_step"]) <= 0.2 * d["ms_per_step"]
+    # measured FMA peaks: FP64 below the nominal unit-count peak, FP32 far above FP64
+    pk = r["peak_measured"]
+    assert 0.5 * r["peak"] < pk["fp64_tflops"] <= 1.05 * r["peak"] and pk["fp32_tflops"] > 20 * pk["fp64_tflops"]
     m = d["mixed"]
     assert m["speedup_vs_fp64"] > 1.0 and m["max_rel_state_error_vs_fp64"] < 1e-5
     assert set(m["rms_state_error_per_field"]) == set(m["rel_state_error_per_field"])

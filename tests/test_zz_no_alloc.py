@@ -43,8 +43,12 @@ def test_noalloc_constraints_match_the_allocating_entry_point_twice():
         H2 = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
         M2 = torch.full((3 * n,), float("nan"), dtype=torch.float64, device="cuda")
         out2 = torch.full((5,), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         C.constraints_noalloc(tiles, g.p, g.n_patches, g.dx, H2.data_ptr(), M2.data_ptr(), out2.data_ptr())
         torch.cuda.synchronize()
+        # the call took no device memory (its scratch is the library's fixed array)
+        assert torch.cuda.mem_get_info()[0] == free0
         h2, m2, o2 = H2.cpu().numpy(), M2.cpu().numpy(), out2.cpu().numpy()
         assert np.abs(h2 - h1).max() <= TOL * max(np.abs(h1).max(), 1.0)
         assert np.abs(m2 - m1).max() <= TOL * max(np.abs(m1).max(), 1.0)
@@ -59,3 +63,8 @@ def test_noalloc_constraints_reject_sizes_beyond_the_fixed_scratch():
         C.constraints_noalloc(tiles, 9, 5800, g.dx, None, None, tiles)   # 4.23M points > 4,194,304
     assert e.value.code == C.ERR_INVALID
     assert "exceed the maximum" in str(e.value)
+    # an edge whose cube overflows 64-bit sizes is rejected before any size is formed
+    for p, n in ((1 << 21, 1), (162, 1), (161, 2)):
+        with pytest.raises(C.CCZ4Error) as e:
+            C.constraints_noalloc(tiles, p, n, g.dx, None, None, tiles)
+        assert e.value.code == C.ERR_INVALID
