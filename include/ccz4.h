@@ -375,6 +375,42 @@ ccz4_status ccz4_mesh_plan(const ccz4_mesh_desc *desc, long long *n_interp, int 
 enum { CCZ4_LAUNCH_FLAT = 0, CCZ4_LAUNCH_QUEUE = 1 };
 ccz4_status ccz4_set_launch(ccz4_grid *g, int mode);
 
+/* ---- particle tracers and puncture trackers ----
+   (Sec. "Particle Tracers as Data Probes"; Sec. "Particle tracers" for
+   puncture trackers.) A set of n tracers on a grid. Each step records the
+   25 fields at every tracer's position by trilinear interpolation from the
+   2^3 closest sample points (cell centres): those of the finest level that
+   holds all eight as interior points of its patches, or, where no refined
+   level does, those of level 0 with its boundary rule (periodic wrap,
+   clamped copy, or the Sommerfeld ghost cells). Weights (1 - t, t) per
+   axis, t the offset from the lower sample point in units of the level's
+   spacing; the value is the sum over the corners (z outermost, x innermost)
+   of (w_x w_y) w_z q, every product and sum rounded on its own.
+   With a velocity (vel_field >= 0) the step then moves each tracer by the
+   explicit Euler step x <- x + (dt vel_scale) v, v the projected fields
+   vel_field .. vel_field + 2. A puncture tracker is a tracer dropped at a
+   black hole with the shift as velocity and vel_scale = -1 (the paper's
+   opposite shift); vel_field = -1 gives static probes.
+
+   ccz4_tracers_new: pos is host [n][3] (x, y, z), copied; the grid must
+   outlive the tracers. Synchronous (builds the slot tables of the refined
+   levels on the device). CCZ4_ERR_INVALID for n < 1 or vel_field outside
+   [-1, 22].
+   ccz4_tracers_step: one step on state buffer buf (CCZ4_BUF_U .. INI);
+   asynchronous on stream, one small kernel (capturable in a graph). A
+   tracer the grid cannot resolve (outside the Sommerfeld ghost shell, or
+   a non-finite coordinate) is left in place with NaN values and flagged.
+   ccz4_tracers_read: copies positions (host [n][3]) and the last step's
+   values (host [n][25]) when not NULL, synchronising the stream; returns
+   CCZ4_ERR_BOUNDS with a message if the last step flagged any tracer.
+   ccz4_tracers_free: releases the tracers. */
+typedef struct ccz4_tracers ccz4_tracers;
+ccz4_status ccz4_tracers_new(ccz4_grid *g, int n, const double *pos, int vel_field, double vel_scale,
+                             ccz4_tracers **out);
+ccz4_status ccz4_tracers_step(ccz4_tracers *t, int buf, double dt, void *stream);
+ccz4_status ccz4_tracers_read(ccz4_tracers *t, double *pos, double *values, void *stream);
+ccz4_status ccz4_tracers_free(ccz4_tracers *t);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *ccz4_last_error(void);
 

@@ -79,6 +79,9 @@ def lib():
         L.og_constraints_points.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, ctypes.c_long, _lng_p, _dbl_p]
         L.og_point_derivs.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, ctypes.c_long, ctypes.c_double,
                                       _dbl_p, _dbl_p, _dbl_p]
+        L.og_tracers_step.restype = ctypes.c_long
+        L.og_tracers_step.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, ctypes.c_long, _dbl_p, ctypes.c_double,
+                                      ctypes.c_int, ctypes.c_double, _dbl_p]
         _lib = L
     return _lib
 
@@ -234,6 +237,17 @@ class Grid:
         if rc:
             raise IndexError("oracle: sample point out of range")
         return d1, d2, ko
+
+    def tracers_step(self, U, G, pos, dt=0.0, vel_field=-1, vel_scale=-1.0):
+        """One tracer step: returns (new positions (n, 3), projected fields
+        (n, 25), number of tracers that could not be projected)."""
+        U = _f64(U, self.ushape)
+        G = self._g(G)
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3).copy()
+        vals = np.empty((len(pos), NV))
+        bad = lib().og_tracers_step(self._h, _d(U), _d(G), len(pos), _d(pos), float(dt), int(vel_field),
+                                    float(vel_scale), _d(vals))
+        return pos, vals, int(bad)
 
 
 # ---------------------------------------------------------------------------

@@ -1201,3 +1201,95 @@ int og_point_derivs(const og_grid *g, const double *U, const double *G, long pt,
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* particle tracers (Sec. "Particle Tracers as Data Probes")                */
+/* ------------------------------------------------------------------------ */
+
+/* Data projection of the 25 fields onto the point x by trilinear
+   interpolation from the 2^3 closest sample points (Sec. "Particle Tracers
+   as Data Probes"). Readings: the sample points are the cell centres of the
+   finest level that holds all eight as interior points of its patches;
+   where no refined level does, level 0 with its boundary rule (periodic
+   wrap, clamped copy, or the cells of the Sommerfeld ghost shell). The
+   weights along an axis are (1 - t, t), t the offset of x from the lower
+   sample point in units of the level's spacing; the value is the sum over
+   the eight corners (z outermost, x innermost) of (w_x w_y) w_z q. Returns 1
+   where x lies beyond what level 0 resolves (outside the Sommerfeld ghost
+   shell, or not a finite coordinate). */
+static int tracer_sample(const og_grid *g, const double *U, const double *G, const double x[3],
+                         double out[OG_NV]) {
+  for (int l = g->n_levels - 1; l >= 0; --l) {
+    const double h = g->dxl[l];
+    int i0[3];
+    double t[3];
+    int finite = 1;
+    for (int d = 0; d < 3; ++d) {
+      double s = (x[d] - g->origin[d]) / h - 0.5;
+      if (!(fabs(s) < 1.0e9)) finite = 0;
+      double f = finite ? floor(s) : 0.0;
+      i0[d] = (int)f;
+      t[d] = s - f;
+    }
+    if (!finite) return 1;
+    long idx[8];
+    int kind[8], ok = 1;
+    for (int c = 0; c < 2 && ok; ++c)
+      for (int b = 0; b < 2 && ok; ++b)
+        for (int a = 0; a < 2 && ok; ++a) {
+          int k = (c * 2 + b) * 2 + a, px = i0[0] + a, py = i0[1] + b, pz = i0[2] + c;
+          if (l > 0) {
+            kind[k] = 0;
+            if (!level_has(g, l, px, py, pz, &idx[k])) ok = 0;
+          } else {
+            if (g->bc == OG_BC_SOMMERFELD &&
+                (px < -OG_HALO || px >= g->N[0] + OG_HALO || py < -OG_HALO || py >= g->N[1] + OG_HALO ||
+                 pz < -OG_HALO || pz >= g->N[2] + OG_HALO))
+              return 1;
+            kind[k] = locate(g, px, py, pz, &idx[k]);
+          }
+        }
+    if (!ok) continue;
+    double wx[2] = {1.0 - t[0], t[0]}, wy[2] = {1.0 - t[1], t[1]}, wz[2] = {1.0 - t[2], t[2]};
+    for (int v = 0; v < OG_NV; ++v) {
+      double acc = 0.0;
+      for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b)
+          for (int a = 0; a < 2; ++a) {
+            int k = (c * 2 + b) * 2 + a;
+            double q = kind[k] == 0 ? U[(long)v * n_interior(g) + idx[k]] : G[(long)v * g->n_ghost + idx[k]];
+            double w = (wx[a] * wy[b]) * wz[c];
+            acc = acc + w * q;
+          }
+      out[v] = acc;
+    }
+    return 0;
+  }
+  return 1;
+}
+
+/* One step of n tracers: each records the projected fields at its position
+   (values[s][25], if values is not NULL) and, if vel_field >= 0, moves by
+   the explicit Euler step x <- x + (dt * vel_scale) v of the paper's tracer
+   section, v the projected fields vel_field .. vel_field + 2 (puncture
+   trackers: the shift with vel_scale = -1, Sec. "Particle tracers" on the
+   opposite shift as the velocity). A tracer that cannot be projected is left
+   where it is, with NaN values. Returns the number of such tracers. */
+long og_tracers_step(const og_grid *g, const double *U, const double *G, long n, double *pos, double dt,
+                     int vel_field, double vel_scale, double *values) {
+  long bad = 0;
+  for (long s = 0; s < n; ++s) {
+    double val[OG_NV];
+    if (tracer_sample(g, U, G, pos + 3 * s, val)) {
+      ++bad;
+      if (values)
+        for (int v = 0; v < OG_NV; ++v) values[s * OG_NV + v] = NAN;
+      continue;
+    }
+    if (values)
+      for (int v = 0; v < OG_NV; ++v) values[s * OG_NV + v] = val[v];
+    if (vel_field >= 0 && vel_field + 2 < OG_NV)
+      for (int d = 0; d < 3; ++d) pos[3 * s + d] = pos[3 * s + d] + (dt * vel_scale) * val[vel_field + d];
+  }
+  return bad;
+}

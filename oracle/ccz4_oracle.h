@@ -84,6 +84,14 @@ int og_point_derivs(const og_grid *g, const double *U, const double *G, long pt,
                     double ko_eps, double *d1 /* [25][3] */, double *d2 /* [25][3][3] */,
                     double *ko /* [25] */);
 
+/* Particle tracers: trilinear projection of the fields at each of n
+   positions pos[n][3] (values[n][25], may be NULL) and, for vel_field >= 0,
+   one explicit Euler move by dt * vel_scale times the projected fields
+   vel_field .. vel_field + 2. Returns the number of tracers that could not
+   be projected (left in place, NaN values). */
+long og_tracers_step(const og_grid *g, const double *U, const double *G, long n, double *pos, double dt,
+                     int vel_field, double vel_scale, double *values);
+
 #ifdef __cplusplus
 }
 #endif

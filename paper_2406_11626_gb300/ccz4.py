@@ -95,6 +95,12 @@ def lib():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    L.ccz4_tracers_new.argtypes = [vp, ctypes.c_int, _dbl_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(vp)]
+    L.ccz4_tracers_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, vp]
+    L.ccz4_tracers_read.argtypes = [vp, _dbl_p, _dbl_p, vp]
+    L.ccz4_tracers_free.argtypes = [vp]
+    for f in (L.ccz4_tracers_new, L.ccz4_tracers_step, L.ccz4_tracers_read, L.ccz4_tracers_free):
+        f.restype = ctypes.c_int
     L.ccz4_flops_per_point_stage.argtypes = [ctypes.POINTER(Params), _dbl_p]
     L.ccz4_flops_per_point_stage.restype = ctypes.c_int
     L.ccz4_last_error.restype = ctypes.c_char_p
@@ -354,6 +360,49 @@ class Grid:
             return out
         _check(code)
         return out
+
+
+class Tracers:
+    """Particle tracers on a grid (ccz4_tracers_* in include/ccz4.h): each
+    step records the 25 fields at every tracer by trilinear interpolation
+    and, with a velocity field, moves it by one explicit Euler step.
+    Puncture trackers: ``Tracers(grid, positions, velocity="shift")``, which
+    moves with the opposite shift."""
+
+    def __init__(self, grid, pos, vel_field=-1, vel_scale=-1.0, velocity=None):
+        if velocity == "shift":
+            from .inputs import IDX
+            vel_field, vel_scale = IDX["betax"], -1.0
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        self.n = len(pos)
+        self.grid = grid     # the grid must outlive the tracers
+        h = ctypes.c_void_p()
+        _check(lib().ccz4_tracers_new(grid._h, self.n, _d(pos), int(vel_field), float(vel_scale), ctypes.byref(h)))
+        self._h = h
+
+    def step(self, buf="U", dt=0.0, stream=None):
+        _check(lib().ccz4_tracers_step(self._h, _buf(buf), float(dt), _stream(stream)))
+
+    def read(self, stream=None, raise_bounds=True):
+        """(positions (n, 3), last step's values (n, 25)); raises on a tracer
+        the grid could not resolve unless raise_bounds is False."""
+        pos = np.empty((self.n, 3))
+        val = np.empty((self.n, NV))
+        code = lib().ccz4_tracers_read(self._h, _d(pos), _d(val), _stream(stream))
+        if code != ERR_BOUNDS or raise_bounds:
+            _check(code)
+        return pos, val
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ccz4_tracers_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def constraints_noalloc(tiles_ptr, p, n_patches, dx, H_ptr, M_ptr, out_ptr, stream=None):
