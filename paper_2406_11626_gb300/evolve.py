@@ -3,9 +3,13 @@ the current GPU (CUDA-graph replays of one step) in FP64 or in the mixed
 precision, and reports the constraint monitors (Sec. "Hamiltonian and
 momentum constraints": L2 of H, L2 of |M|, max |H|, max |M| over the points
 of leaf patches, and the count of non-finite values) every `every` steps,
-one JSON line per report.
+one JSON line per report. With --track, puncture trackers (Sec. "Particle
+tracers": tracers dropped at the black holes that move with the opposite
+shift by explicit Euler steps of the solver's dt, projected by trilinear
+interpolation) follow the punctures, and each report carries their
+positions.
 
-    python -m paper_2406_11626_gb300.evolve --workload binary --steps 500 --every 50 --precision mixed
+    python -m paper_2406_11626_gb300.evolve --workload binary --steps 500 --every 50 --precision mixed --track
 """
 import json
 import time
@@ -39,10 +43,21 @@ def initial_state(cfg, g):
     return {}
 
 
-def run(workload="gauge_wave", steps=10, every=1, precision="fp64", launch="flat", log=None):
+def puncture_positions(cfg):
+    """Initial puncture positions of a workload: the binary's two punctures
+    at x = -d/2 and +d/2, the single puncture at the origin."""
+    if cfg.name == "binary_puncture":
+        h = 0.5 * cfg.extra["d"]
+        return [(-h, 0.0, 0.0), (h, 0.0, 0.0)]
+    if cfg.name == "single_puncture":
+        return [(0.0, 0.0, 0.0)]
+    return []
+
+
+def run(workload="gauge_wave", steps=10, every=1, precision="fp64", launch="flat", log=None, track=False):
     """Returns the reports: step 0 and every `every` steps up to `steps`,
     each {"step", "time", "L2_H", "L2_M", "max_H", "max_M", "nonfinite",
-    "wall_s"}."""
+    "wall_s"}, and with track=True "punctures" (tracker positions)."""
     import torch
     from . import ccz4 as C
     if steps < 0 or every < 1:
@@ -53,11 +68,16 @@ def run(workload="gauge_wave", steps=10, every=1, precision="fp64", launch="flat
     extra = initial_state(cfg, g)
     P = C.make_params(**cfg.params, precision=precision)
     reports = []
+    tracker = None
+    if track and puncture_positions(cfg):
+        tracker = C.Tracers(g, puncture_positions(cfg), velocity="shift")
 
     def report(n, wall):
         out = g.constraints("U", raise_nonfinite=False)
         r = {"step": n, "time": n * cfg.dt, "L2_H": out[0], "L2_M": out[1], "max_H": out[2], "max_M": out[3],
              "nonfinite": out[4], "wall_s": wall}
+        if tracker is not None:
+            r["punctures"] = tracker.read()[0].tolist()
         reports.append(r)
         if log:
             log(r)
@@ -68,10 +88,18 @@ def run(workload="gauge_wave", steps=10, every=1, precision="fp64", launch="flat
     n = 0
     while n < steps:
         k = min(every, steps - n)
-        g.step_graph(P, cfg.dt, k)
+        if tracker is None:
+            g.step_graph(P, cfg.dt, k)
+        else:
+            # x^{t+dt} = x^t - dt beta(x^t): the tracker moves with the state at the start of each step
+            for _ in range(k):
+                tracker.step("U", cfg.dt)
+                g.step_graph(P, cfg.dt, 1)
         n += k
         torch.cuda.synchronize()
         report(n, time.perf_counter() - t0)
+    if tracker is not None:
+        tracker.close()
     g.close()
     if log and extra:
         log(extra)
@@ -86,8 +114,10 @@ def main(argv=None):
     ap.add_argument("--every", type=int, default=1)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--launch", default="flat", choices=["flat", "queue"])
+    ap.add_argument("--track", action="store_true", help="follow the punctures with puncture trackers")
     a = ap.parse_args(argv)
-    reps = run(a.workload, a.steps, a.every, a.precision, a.launch, log=lambda r: print(json.dumps(r), flush=True))
+    reps = run(a.workload, a.steps, a.every, a.precision, a.launch, log=lambda r: print(json.dumps(r), flush=True),
+               track=a.track)
     return 0 if reps and reps[-1]["nonfinite"] == 0 else 1
 
 

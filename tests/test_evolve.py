@@ -28,3 +28,21 @@ def test_short_gauge_wave_run_reports_every_interval(precision):
     # the printed gauge wave is an exact solution: H stays at the truncation level
     assert all(r["L2_H"] < 1e-3 for r in reps)
     assert reps[-1]["time"] > 0 and reps[-1]["wall_s"] > 0
+
+
+def test_puncture_positions_of_the_workloads():
+    assert E.puncture_positions(E.WORKLOADS["binary"]()) == [(-3.0, 0.0, 0.0), (3.0, 0.0, 0.0)]
+    assert E.puncture_positions(E.WORKLOADS["mid"]()) == [(0.0, 0.0, 0.0)]
+    assert E.puncture_positions(E.WORKLOADS["gauge_wave"]()) == []
+
+
+@pytest.mark.gpu
+def test_puncture_tracker_follows_the_opposite_shift_on_a_mesh():
+    """A short three-level run with the tracker: the single puncture at the
+    origin stays there (the data are symmetric under x -> -x, y -> -y,
+    z -> -z, so the projected shift vanishes there), and every report
+    carries the tracker's position."""
+    reps = E.run("mesh-mid", steps=4, every=2, track=True)
+    assert [r["step"] for r in reps] == [0, 2, 4]
+    assert all(len(r["punctures"]) == 1 for r in reps)
+    assert max(abs(c) for c in reps[-1]["punctures"][0]) < 1e-12
