@@ -18,6 +18,7 @@ import numpy as np
 from . import build as _build
 
 NV = 25
+NV_FO = 58
 HALO = 3
 BC = {"periodic": 0, "copy": 1, "sommerfeld": 2}
 SLICING = {"harmonic": 0, "1+log": 1}
@@ -79,6 +80,11 @@ def lib():
         L.og_constraints_points.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, ctypes.c_long, _lng_p, _dbl_p]
         L.og_point_derivs.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, ctypes.c_long, ctypes.c_double,
                                       _dbl_p, _dbl_p, _dbl_p]
+        L.og_fo_rhs.argtypes = [ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_int, _dbl_p, _dbl_p, _dbl_p,
+                                _dbl_p, _dbl_p]
+        L.og_fo_reconstruct.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p]
+        L.og_fo_rk4_step.argtypes = [ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_int, ctypes.c_double,
+                                     _dbl_p, _dbl_p, _dbl_p]
         L.og_tracers_step.restype = ctypes.c_long
         L.og_tracers_step.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, ctypes.c_long, _dbl_p, ctypes.c_double,
                                       ctypes.c_int, ctypes.c_double, _dbl_p]
@@ -237,6 +243,42 @@ class Grid:
         if rc:
             raise IndexError("oracle: sample point out of range")
         return d1, d2, ko
+
+    # -- first-order formulation (58 fields; fo_* take and return (58, ...) arrays) --
+    @property
+    def fo_ushape(self):
+        return (NV_FO, self.n_patches, self.p, self.p, self.p)
+
+    def _gfo(self, G):
+        if self.n_ghost == 0:
+            return np.zeros((NV_FO, 1))
+        return _f64(G, (NV_FO, self.n_ghost))
+
+    def fo_rhs(self, P, U, G=None, Gini=None, red=True):
+        """Right-hand side of the 58 variables: red=True the first-order
+        formulation, False the second-order one without the red terms."""
+        U = _f64(U, self.fo_ushape)
+        G, Gini = self._gfo(G), self._gfo(Gini)
+        rU = np.empty(self.fo_ushape)
+        rG = np.empty((NV_FO, max(self.n_ghost, 1)))
+        lib().og_fo_rhs(self._h, ctypes.byref(P), int(bool(red)), _d(U), _d(G), _d(Gini), _d(rU), _d(rG))
+        return rU, rG[:, :self.n_ghost]
+
+    def fo_reconstruct(self, U, G=None):
+        """Interior auxiliary variables <- FD4 derivatives of the primaries."""
+        U = _f64(U, self.fo_ushape).copy()
+        lib().og_fo_reconstruct(self._h, _d(U), _d(self._gfo(G)))
+        return U
+
+    def fo_rk4_step(self, P, dt, U, G=None, Gini=None, variant="fo"):
+        """One RK4 step of the 58-variable state: variant "fo" (first order)
+        or "so-recon" (second order with reconstruction)."""
+        U = _f64(U, self.fo_ushape).copy()
+        G = self._gfo(G).copy()
+        Gini = self._gfo(Gini)
+        v = {"fo": 0, "so-recon": 1}[variant]
+        lib().og_fo_rk4_step(self._h, ctypes.byref(P), v, float(dt), _d(U), _d(G), _d(Gini))
+        return U, G[:, :self.n_ghost]
 
     def tracers_step(self, U, G, pos, dt=0.0, vel_field=-1, vel_scale=-1.0):
         """One tracer step: returns (new positions (n, 3), projected fields

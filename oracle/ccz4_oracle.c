@@ -1293,3 +1293,559 @@ long og_tracers_step(const og_grid *g, const double *U, const double *G, long n,
   }
   return bad;
 }
+
+/* ======================================================================== */
+/* first-order formulation (FO) and second-order with reconstruction        */
+/* ======================================================================== */
+
+/* The 58 variables of Eq. first-order-variables: the 25 primaries in their
+   usual order, then the auxiliary variables of Eq. auxiliary-variables:
+   A_k = d_k alpha (25..27), B_k^i = d_k beta^i (28 + 3k + i),
+   D_kij = 1/2 d_k g~_ij (37 + 6k + pair(i, j)), P_k = d_k phi (55..57). */
+enum { FO_A = 25, FO_B = 28, FO_D = 37, FO_P = 55 };
+
+/* Right-hand side of the 58 variables at one point from their values q and
+   their FD4 first derivatives d1[v][k] = d_k q_v (Alg. fd4-fo: only first
+   derivatives are taken). The nine primary equations of the appendix
+   "Spacetime foliation" are written with the auxiliary variables in place
+   of the derivatives of alpha, beta, g~ and phi: first derivatives become
+   A, B, D, P, and second derivatives the symmetrised first derivatives of
+   those (d_i d_j alpha -> d_(i A_j), d_k d_l beta^i -> d_(k B_l)^i,
+   d_k d_l g~_ij -> d_k D_lij + d_l D_kij, d_i d_j phi -> d_(i P_j)), which
+   is how the relations below the equations close the system (Christoffel
+   symbols from D, nabla nabla alpha = d_(i A_j) - Gamma^k_ij A_k, the
+   modified Ricci tensor of Eq. NR_foccz4_modified_ricci). The four
+   auxiliary equations are Eqs. NR_foccz4_A_k, NR_foccz4_B^i_j, the D_kij
+   equation and NR_foccz4_P_i. red != 0 keeps the red terms (the first-order
+   formulation); red == 0 removes them (the second-order formulation, whose
+   auxiliary variables are reconstructed instead of evolved).
+   Readings: those of the second-order right-hand side (ccz4_point_rhs),
+   and: g'(alpha) = -2/alpha^2 for 1+log, 0 for harmonic slicing; K0 is a
+   constant (d_k K0 = 0); zero shift sets the right-hand sides of beta^i,
+   b^i and B_k^i to zero (beta is then static, so B = d beta is too);
+   D_k^nm = g~^na g~^mb D_kab. */
+static void fo_point_rhs(const og_params *P, int red, const double q[OG_NV_FO], const double d1[OG_NV_FO][3],
+                         double rhs[OG_NV_FO]) {
+  double g[3][3], ig[3][3], det;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) g[i][j] = q[GXX + SYM[i][j]];
+  metric_inverse(g, ig, &det);
+  const double al = q[ALPHA], ph = q[PHI], Kt = q[KTR], Th = q[THETA];
+  double be[3], Gh[3], bb[3], Av[3], Pv[3], B[3][3], D[3][3][3], At[3][3];
+  for (int i = 0; i < 3; ++i) {
+    be[i] = q[BETAX + i];
+    Gh[i] = q[GHX + i];
+    bb[i] = q[BBX + i];
+    Av[i] = q[FO_A + i];
+    Pv[i] = q[FO_P + i];
+    for (int j = 0; j < 3; ++j) {
+      B[i][j] = q[FO_B + 3 * i + j];                  /* B[k][i] = B_k^i */
+      At[i][j] = q[AXX + SYM[i][j]];
+    }
+  }
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) D[k][i][j] = q[FO_D + 6 * k + SYM[i][j]];
+  /* first derivatives of the evolved variables */
+  double dA[3][3], dP[3][3], dB[3][3][3], dD[3][3][3][3], dAt[3][3][3], dK[3], dTh[3], dGh[3][3], dbb[3][3];
+  for (int k = 0; k < 3; ++k) {
+    dK[k] = d1[KTR][k];
+    dTh[k] = d1[THETA][k];
+    for (int i = 0; i < 3; ++i) {
+      dA[k][i] = d1[FO_A + i][k];                     /* d_k A_i */
+      dP[k][i] = d1[FO_P + i][k];                     /* d_k P_i */
+      dGh[k][i] = d1[GHX + i][k];                     /* d_k Gamma-hat^i */
+      dbb[k][i] = d1[BBX + i][k];                     /* d_k b^i */
+      for (int l = 0; l < 3; ++l) dB[k][l][i] = d1[FO_B + 3 * l + i][k];   /* d_k B_l^i */
+      for (int j = 0; j < 3; ++j) {
+        dAt[k][i][j] = d1[AXX + SYM[i][j]][k];        /* d_k A~_ij */
+        for (int m = 0; m < 3; ++m) dD[m][k][i][j] = d1[FO_D + 6 * k + SYM[i][j]][m];   /* d_m D_kij */
+      }
+    }
+  }
+  /* symmetrised stand-ins of the second derivatives */
+  double ddal[3][3], ddph[3][3], ddbe[3][3][3], ddg[3][3][3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      ddal[i][j] = 0.5 * (dA[i][j] + dA[j][i]);
+      ddph[i][j] = 0.5 * (dP[i][j] + dP[j][i]);
+      for (int l = 0; l < 3; ++l) ddbe[i][j][l] = 0.5 * (dB[i][j][l] + dB[j][i][l]);   /* d_(i B_j)^l */
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) ddg[i][j][a][b] = dD[i][j][a][b] + dD[j][i][a][b];   /* d_i d_j g~_ab */
+    }
+  /* Christoffel symbols from D: G~^k_ij = g~^kl (D_ijl + D_jil - D_lij) */
+  double Gam[3][3][3], GamL[3][3][3], Gc[3], PGam[3][3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int l = 0; l < 3; ++l) s += ig[k][l] * (D[i][j][l] + D[j][i][l] - D[l][i][j]);
+        Gam[k][i][j] = s;
+      }
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int l = 0; l < 3; ++l) s += g[k][l] * Gam[l][i][j];
+        GamL[k][i][j] = s;
+      }
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k) s += ig[j][k] * Gam[i][j][k];
+    Gc[i] = s;
+  }
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int l = 0; l < 3; ++l) s += ig[k][l] * (g[j][l] * Pv[i] + g[i][l] * Pv[j] - g[i][j] * Pv[l]);
+        PGam[k][i][j] = Gam[k][i][j] - s / ph;
+      }
+  /* D_k^nm = g~^na g~^mb D_kab, and its contraction with A~ */
+  double DuA[3];   /* D_k^nm A~_nm */
+  for (int k = 0; k < 3; ++k) {
+    double s = 0.0;
+    for (int n = 0; n < 3; ++n)
+      for (int m = 0; m < 3; ++m)
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) s += ig[n][a] * ig[m][b] * D[k][a][b] * At[n][m];
+    DuA[k] = s;
+  }
+  double gdAt[3];  /* g~^nm d_k A~_nm */
+  for (int k = 0; k < 3; ++k) {
+    double s = 0.0;
+    for (int n = 0; n < 3; ++n)
+      for (int m = 0; m < 3; ++m) s += ig[n][m] * dAt[k][n][m];
+    gdAt[k] = s;
+  }
+  /* Z_i = 1/2 g~_ij (Gh^j - G~^j); Z^i = 1/2 phi^2 (Gh^i - G~^i) */
+  double Zcov[3], Zup[3];
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < 3; ++j) s += g[i][j] * (Gh[j] - Gc[j]);
+    Zcov[i] = 0.5 * s;
+    Zup[i] = 0.5 * ph * ph * (Gh[i] - Gc[i]);
+  }
+  /* nabla~_i nabla~_j phi = d_(i P_j) - G~^k_ij P_k */
+  double cdph[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += Gam[k][i][j] * Pv[k];
+      cdph[i][j] = ddph[i][j] - s;
+    }
+  double trcdph = 0.0, PP = 0.0;
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) {
+      trcdph += ig[k][l] * cdph[k][l];
+      PP += ig[k][l] * Pv[k] * Pv[l];
+    }
+  /* R_ij + 2 nabla_(i Z_j), Eq. NR_foccz4_modified_ricci with D, P and d D, d P */
+  double RZ[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double t1 = 0.0;
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) t1 += ig[k][l] * ddg[k][l][i][j];
+      double t2 = 0.0, t3 = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        t2 += 0.5 * (g[k][i] * dGh[j][k] + g[k][j] * dGh[i][k]);
+        t3 += Gh[k] * 2.0 * D[k][i][j];
+      }
+      double t4 = 0.0;
+      for (int l = 0; l < 3; ++l)
+        for (int m = 0; m < 3; ++m)
+          for (int k = 0; k < 3; ++k)
+            t4 += ig[l][m] * (Gam[k][l][i] * GamL[j][k][m] + Gam[k][l][j] * GamL[i][k][m] +
+                              Gam[k][i][m] * GamL[k][l][j]);
+      double t7 = 0.0;
+      for (int k = 0; k < 3; ++k) t7 += Zup[k] * (g[i][k] * Pv[j] + g[j][k] * Pv[i] - g[i][j] * Pv[k]);
+      RZ[i][j] = -0.5 * t1 + t2 + 0.5 * t3 + t4 + (cdph[i][j] + g[i][j] * trcdph) / ph -
+                 2.0 / (ph * ph) * g[i][j] * PP + 2.0 / (ph * ph * ph) * t7;
+    }
+  /* nabla_i nabla_j alpha = d_(i A_j) - Gamma^k_ij A_k */
+  double DDal[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += PGam[k][i][j] * Av[k];
+      DDal[i][j] = ddal[i][j] - s;
+    }
+  double RpZ = 0.0, lapal = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      RpZ += ig[i][j] * RZ[i][j];
+      lapal += ig[i][j] * DDal[i][j];
+    }
+  RpZ *= ph * ph;
+  lapal *= ph * ph;
+  double trA = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) trA += ig[i][j] * At[i][j];
+  double Aup[3][3], AgA[3][3], AA = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0, u = 0.0;
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) {
+          s += ig[i][k] * ig[j][l] * At[k][l];
+          u += At[i][k] * ig[k][l] * At[l][j];
+        }
+      Aup[i][j] = s;
+      AgA[i][j] = u;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) AA += At[i][j] * Aup[i][j];
+  const double trB = B[0][0] + B[1][1] + B[2][2];
+  const double onelog = P->slicing == OG_SLICING_ONE_PLUS_LOG;
+  const double gfun = onelog ? 2.0 / al : 1.0;
+  const double gprime = onelog ? -2.0 / (al * al) : 0.0;
+  const double lapse_src = Kt - P->K0 - 2.0 * P->c * Th;
+
+  /* d_t g~_ij */
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) {
+      double adv = 0.0, lie = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        adv += be[k] * 2.0 * D[k][i][j];
+        lie += g[k][i] * B[j][k] + g[k][j] * B[i][k];
+      }
+      rhs[GXX + SYM[i][j]] = adv + lie - 2.0 / 3.0 * g[i][j] * trB - 2.0 * al * (At[i][j] - 1.0 / 3.0 * g[i][j] * trA) -
+                             (1.0 / P->tau) * (det - 1.0) * g[i][j];
+    }
+  /* d_t alpha, d_t phi */
+  {
+    double advA = 0.0, advP = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      advA += be[k] * Av[k];
+      advP += be[k] * Pv[k];
+    }
+    rhs[ALPHA] = advA - al * al * gfun * lapse_src;
+    rhs[PHI] = advP + 1.0 / 3.0 * ph * (al * Kt - trB);
+  }
+  /* d_t A~_ij */
+  {
+    double Mx[3][3], trM = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Mx[i][j] = -DDal[i][j] + al * RZ[i][j];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) trM += ig[i][j] * Mx[i][j];
+    for (int i = 0; i < 3; ++i)
+      for (int j = i; j < 3; ++j) {
+        double adv = 0.0, lie = 0.0;
+        for (int k = 0; k < 3; ++k) {
+          adv += be[k] * dAt[k][i][j];
+          lie += At[k][i] * B[j][k] + At[k][j] * B[i][k];
+        }
+        rhs[AXX + SYM[i][j]] = adv + ph * ph * (Mx[i][j] - 1.0 / 3.0 * g[i][j] * trM) + lie -
+                               2.0 / 3.0 * At[i][j] * trB + al * At[i][j] * (Kt - 2.0 * Th * P->c) -
+                               2.0 * al * AgA[i][j];
+      }
+  }
+  /* d_t K, d_t Theta */
+  {
+    double advK = 0.0, advT = 0.0, ZA = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      advK += be[k] * dK[k];
+      advT += be[k] * dTh[k];
+      ZA += Zup[k] * Av[k];
+    }
+    rhs[KTR] = advK - lapal + al * RpZ + al * Kt * (Kt - 2.0 * Th * P->c) - 3.0 * al * P->kappa1 * (1.0 + P->kappa2) * Th;
+    rhs[THETA] = advT + 0.5 * al * P->e * P->e * RpZ + 0.5 * al * P->e * P->e * (2.0 / 3.0 * Kt * Kt - AA) -
+                 al * Th * Kt * P->c - ZA - al * P->kappa1 * (2.0 + P->kappa2) * Th;
+  }
+  /* d_t Gamma-hat^i (red: + 2 alpha g~^ik g~^nm d_k A~_nm - 4 alpha g~^ik D_k^nm A~_nm) */
+  double rGh[3], advGh[3];
+  for (int i = 0; i < 3; ++i) {
+    double adv = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0, t4 = 0.0, t5 = 0.0, tr = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      adv += be[k] * dGh[k][i];
+      t1 += 2.0 * al * ig[k][i] * dTh[k];
+      for (int l = 0; l < 3; ++l) {
+        t2 += ig[k][l] * ddbe[k][l][i];
+        t3 += P->s / 3.0 * ig[i][k] * ddbe[k][l][l];
+      }
+      t4 += -4.0 / 3.0 * al * ig[i][k] * dK[k];
+      t5 += -Gc[k] * B[k][i];
+      tr += 2.0 * al * ig[i][k] * gdAt[k] - 4.0 * al * ig[i][k] * DuA[k];
+    }
+    double GA = 0.0, AP = 0.0, thz = 0.0, AA1 = 0.0, kz = 0.0, k3 = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      for (int k = 0; k < 3; ++k) {
+        GA += Gam[i][j][k] * Aup[j][k];
+        k3 += ig[j][k] * Zcov[j] * B[k][i];
+      }
+      AP += Aup[i][j] * Pv[j] / ph;
+      thz += ig[j][i] * (Th * Av[j] / al + 2.0 / 3.0 * Kt * Zcov[j]);
+      AA1 += Aup[i][j] * Av[j];
+      kz += ig[i][j] * Zcov[j];
+    }
+    double t6 = 2.0 / 3.0 * Gc[i] * trB + 2.0 * al * (GA - 3.0 * AP) - 2.0 * al * thz - 2.0 * AA1;
+    double t7 = -2.0 * al * P->kappa1 * kz;
+    double t8 = 2.0 * P->kappa3 * (2.0 / 3.0 * kz * trB - k3);
+    advGh[i] = adv;
+    rGh[i] = adv + t1 + t2 + t3 + t4 + t5 + t6 + t7 + t8 + (red ? tr : 0.0);
+    rhs[GHX + i] = rGh[i];
+  }
+  /* gauge: d_t beta^i, d_t b^i */
+  const int driver = P->shift == OG_SHIFT_GAMMA_DRIVER;
+  for (int i = 0; i < 3; ++i) {
+    if (driver) {
+      double advb = 0.0, advbb = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        advb += be[k] * B[k][i];
+        advbb += be[k] * dbb[k][i];
+      }
+      rhs[BETAX + i] = advb + P->f * bb[i];
+      rhs[BBX + i] = advbb + (rGh[i] - advGh[i]) - P->eta * bb[i];
+    } else {
+      rhs[BETAX + i] = 0.0;
+      rhs[BBX + i] = 0.0;
+    }
+  }
+  /* Eq. NR_foccz4_A_k (red: - alpha g g~^nm d_k A~_nm + 2 alpha g D_k^nm A~_nm) */
+  for (int k = 0; k < 3; ++k) {
+    double adv = 0.0, BA = 0.0;
+    for (int l = 0; l < 3; ++l) {
+      adv += be[l] * dA[l][k];
+      BA += B[k][l] * Av[l];
+    }
+    double r = adv - al * al * gfun * (dK[k] - 2.0 * P->c * dTh[k]) + BA -
+               (2.0 * al * gfun + al * al * gprime) * lapse_src * Av[k];
+    if (red) r += -al * gfun * gdAt[k] + 2.0 * al * gfun * DuA[k];
+    rhs[FO_A + k] = r;
+  }
+  /* Eq. NR_foccz4_B^i_j (red: the mu terms) */
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i) {
+      if (!driver) {
+        rhs[FO_B + 3 * k + i] = 0.0;
+        continue;
+      }
+      double adv = 0.0, BB = 0.0;
+      for (int l = 0; l < 3; ++l) {
+        adv += be[l] * dB[l][k][i];
+        BB += B[k][l] * B[l][i];
+      }
+      double r = adv + P->f * dbb[k][i] + BB;
+      if (red) {
+        double m1 = 0.0, m2 = 0.0;
+        for (int j = 0; j < 3; ++j) {
+          m1 += ig[i][j] / ph * (dP[k][j] - dP[j][k]);
+          for (int n = 0; n < 3; ++n)
+            for (int l = 0; l < 3; ++l) m2 += ig[i][j] * ig[n][l] * (dD[k][l][j][n] - dD[l][k][j][n]);
+        }
+        r += -al * al * P->mu * m1 + al * al * P->mu * m2;
+      }
+      rhs[FO_B + 3 * k + i] = r;
+    }
+  /* the D_kij equation (red: + alpha/3 g~_ij g~^nm d_k A~_nm - 2 alpha/3 g~_ij D_k^nm A~_nm) */
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
+      for (int j = i; j < 3; ++j) {
+        double adv = 0.0, sh = 0.0, trdB = 0.0, BD = 0.0;
+        for (int l = 0; l < 3; ++l) {
+          adv += be[l] * dD[l][k][i][j];
+          sh += -0.5 * g[l][i] * ddbe[k][j][l] - 0.5 * g[l][j] * ddbe[k][i][l];
+          trdB += ddbe[k][l][l];
+          BD += B[k][l] * D[l][i][j] + B[j][l] * D[k][l][i] + B[i][l] * D[k][l][j];
+        }
+        sh += 1.0 / 3.0 * g[i][j] * trdB;
+        double r = adv - P->s * sh - al * dAt[k][i][j] + BD - 2.0 / 3.0 * trB * D[k][i][j] -
+                   Av[k] * (At[i][j] - 1.0 / 3.0 * g[i][j] * trA);
+        if (red) r += al / 3.0 * g[i][j] * gdAt[k] - 2.0 * al / 3.0 * g[i][j] * DuA[k];
+        rhs[FO_D + 6 * k + SYM[i][j]] = r;
+      }
+  /* Eq. NR_foccz4_P_i (red: + 1/3 alpha phi g~^nm d_k A~_nm - 2/3 alpha phi D_k^nm A~_nm) */
+  for (int k = 0; k < 3; ++k) {
+    double adv = 0.0, BP = 0.0, trdB = 0.0;
+    for (int l = 0; l < 3; ++l) {
+      adv += be[l] * dP[l][k];
+      BP += B[k][l] * Pv[l];
+      trdB += ddbe[k][l][l];
+    }
+    double r = adv + 1.0 / 3.0 * ph * (al * dK[k] - trdB) + BP + 1.0 / 3.0 * (al * Kt - trB) * Pv[k] +
+               1.0 / 3.0 * ph * Kt * Av[k];
+    if (red) r += 1.0 / 3.0 * al * ph * gdAt[k] - 2.0 / 3.0 * al * ph * DuA[k];
+    rhs[FO_P + k] = r;
+  }
+}
+
+/* Halo'd tile of patch n for the first nv fields of U and G (point-major,
+   nv values per point). */
+static void build_tile_nv(const og_grid *g, int n, const double *U, const double *G, double *tile, int nv) {
+  int T = g->T, p = g->p, l = g->lev[n];
+  int bx = g->ijk[3 * n] * p, by = g->ijk[3 * n + 1] * p, bz = g->ijk[3 * n + 2] * p;
+  for (int lz = 0; lz < T; ++lz)
+    for (int ly = 0; ly < T; ++ly)
+      for (int lx = 0; lx < T; ++lx) {
+        long t = ((long)lz * T + ly) * T + lx;
+        for (int v = 0; v < nv; ++v)
+          tile[t * nv + v] = value_at_l(g, U, G, v, l, bx + lx - OG_HALO, by + ly - OG_HALO, bz + lz - OG_HALO);
+      }
+}
+
+/* The FD4 first derivative (Eq. exa_fd4_central_difference) and the
+   Kreiss-Oliger sum (Eq. exa_fd4_ko) on a point-major tile of nv fields. */
+static double tqn(const double *tile, long c, int nv, long off, int v) { return tile[(c + off) * nv + v]; }
+
+static double fd1n(const double *tile, long c, const long st[3], int nv, int v, int k, double dx) {
+  long s = st[k];
+  return (8.0 * (tqn(tile, c, nv, s, v) - tqn(tile, c, nv, -s, v)) -
+          (tqn(tile, c, nv, 2 * s, v) - tqn(tile, c, nv, -2 * s, v))) / (12.0 * dx);
+}
+
+static double ko_sumn(const double *tile, long c, const long st[3], int nv, int v, double eps, double dx) {
+  double acc = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    long s = st[k];
+    double d = tqn(tile, c, nv, -3 * s, v) - 6.0 * tqn(tile, c, nv, -2 * s, v) + 15.0 * tqn(tile, c, nv, -s, v) -
+               20.0 * tqn(tile, c, nv, 0, v) + 15.0 * tqn(tile, c, nv, s, v) - 6.0 * tqn(tile, c, nv, 2 * s, v) +
+               tqn(tile, c, nv, 3 * s, v);
+    acc += eps / (64.0 * dx) * d;
+  }
+  return acc;
+}
+
+/* Sommerfeld ghost cell id of the 58-variable state: the radiative
+   condition of ghost_rhs for every variable, with speed somm_speed[v] for
+   the primaries and 1 for the auxiliary variables. */
+static void fo_ghost_rhs(const og_grid *g, const og_params *P, const double *U, const double *G, const double *Gini,
+                         long id, double out[OG_NV_FO]) {
+  int c[3] = {g->gcoord[3 * id], g->gcoord[3 * id + 1], g->gcoord[3 * id + 2]};
+  int d = -1, side = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (c[a] < 0) { d = a; side = -1; }
+    if (c[a] >= g->N[a]) { d = a; side = +1; }
+  }
+  int nb[3] = {c[0], c[1], c[2]};
+  nb[d] -= side;
+  double xs[3];
+  for (int a = 0; a < 3; ++a) xs[a] = g->origin[a] + (c[a] + 0.5) * g->dx;
+  double r = sqrt(xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2]);
+  for (int v = 0; v < OG_NV_FO; ++v) {
+    double qg = G[(long)v * g->n_ghost + id];
+    double qn = value_at(g, U, G, v, nb[0], nb[1], nb[2]);
+    double dQ = side > 0 ? (qg - qn) / g->dx : (qn - qg) / g->dx;
+    double cv = v < OG_NV ? P->somm_speed[v] : 1.0;
+    out[v] = -cv * (r / xs[d]) * dQ - cv / r * (qg - Gini[(long)v * g->n_ghost + id]);
+  }
+}
+
+/* Right-hand side of the 58 variables (Alg. fd4-fo): for every interior
+   point the FD4 first derivatives of all 58, fo_point_rhs, plus the
+   Kreiss-Oliger dissipation of every variable; the Sommerfeld ghost cells
+   by their radiative condition. red selects the first-order formulation
+   (with the red terms) or the reconstructed second-order one (without). */
+int og_fo_rhs(const og_grid *g, const og_params *P, int red, const double *U, const double *G, const double *Gini,
+              double *rU, double *rG) {
+  const int T = g->T, p = g->p, nv = OG_NV_FO;
+  const long T3 = (long)T * T * T, pts = n_interior(g);
+  const long st[3] = {1, T, (long)T * T};
+  double *tile = (double *)malloc(sizeof(double) * (size_t)T3 * nv);
+  double d1[OG_NV_FO][3];
+  double q[OG_NV_FO], r[OG_NV_FO];
+  for (int n = 0; n < g->n_patches; ++n) {
+    build_tile_nv(g, n, U, G, tile, nv);
+    const double dx = g->dxl[g->lev[n]];
+    for (int z = 0; z < p; ++z)
+      for (int y = 0; y < p; ++y)
+        for (int x = 0; x < p; ++x) {
+          const long c = ((long)(z + OG_HALO) * T + (y + OG_HALO)) * T + (x + OG_HALO);
+          for (int v = 0; v < nv; ++v) {
+            q[v] = tqn(tile, c, nv, 0, v);
+            for (int k = 0; k < 3; ++k) d1[v][k] = fd1n(tile, c, st, nv, v, k, dx);
+          }
+          fo_point_rhs(P, red, q, (const double(*)[3])d1, r);
+          const long li = (long)n * p * p * p + ((long)z * p + y) * p + x;
+          for (int v = 0; v < nv; ++v) rU[(long)v * pts + li] = r[v] + ko_sumn(tile, c, st, nv, v, P->ko_eps, dx);
+        }
+  }
+  free(tile);
+  for (long id = 0; id < g->n_ghost; ++id) {
+    double rg[OG_NV_FO];
+    fo_ghost_rhs(g, P, U, G, Gini, id, rg);
+    for (int v = 0; v < nv; ++v) rG[(long)v * g->n_ghost + id] = rg[v];
+  }
+  return 0;
+}
+
+/* The reconstruction of Alg. fd4-so: the auxiliary variables of every
+   interior point become the FD4 first derivatives of the primaries
+   (A_k = d_k alpha, B_k^i = d_k beta^i, D_kij = 1/2 d_k g~_ij,
+   P_k = d_k phi, Eq. auxiliary-variables); the ghost cells keep theirs. */
+int og_fo_reconstruct(const og_grid *g, double *U, const double *G) {
+  const int T = g->T, p = g->p, nv = OG_NV;
+  const long T3 = (long)T * T * T, pts = n_interior(g);
+  const long st[3] = {1, T, (long)T * T};
+  double *tile = (double *)malloc(sizeof(double) * (size_t)T3 * nv);
+  double *aux = (double *)malloc(sizeof(double) * (size_t)(OG_NV_FO - OG_NV) * (size_t)pts);
+  for (int n = 0; n < g->n_patches; ++n) {
+    build_tile_nv(g, n, U, G, tile, nv);
+    const double dx = g->dxl[g->lev[n]];
+    for (int z = 0; z < p; ++z)
+      for (int y = 0; y < p; ++y)
+        for (int x = 0; x < p; ++x) {
+          const long c = ((long)(z + OG_HALO) * T + (y + OG_HALO)) * T + (x + OG_HALO);
+          const long li = (long)n * p * p * p + ((long)z * p + y) * p + x;
+          for (int k = 0; k < 3; ++k) {
+            aux[(long)(FO_A - OG_NV + k) * pts + li] = fd1n(tile, c, st, nv, ALPHA, k, dx);
+            aux[(long)(FO_P - OG_NV + k) * pts + li] = fd1n(tile, c, st, nv, PHI, k, dx);
+            for (int i = 0; i < 3; ++i)
+              aux[(long)(FO_B - OG_NV + 3 * k + i) * pts + li] = fd1n(tile, c, st, nv, BETAX + i, k, dx);
+            for (int s = 0; s < 6; ++s)
+              aux[(long)(FO_D - OG_NV + 6 * k + s) * pts + li] = 0.5 * fd1n(tile, c, st, nv, GXX + s, k, dx);
+          }
+        }
+  }
+  memcpy(U + (long)OG_NV * pts, aux, sizeof(double) * (size_t)(OG_NV_FO - OG_NV) * (size_t)pts);
+  free(aux);
+  free(tile);
+  return 0;
+}
+
+/* One classic RK4 step of the 58-variable state (the tableau of
+   og_rk4_step) over the interior points and the Sommerfeld ghost cells,
+   then the algebraic enforcement of the primaries (Sec. "Evolution
+   equations"; the auxiliary variables are left as they are).
+   variant 0: the first-order formulation, every variable evolved with the
+   red terms (Alg. fd4-fo).
+   variant 1: the second-order formulation with reconstruction (Alg.
+   fd4-so): before the right-hand side of every stage the auxiliary
+   variables of the interior points are reconstructed from that stage's
+   primaries, the red terms are removed, the interior auxiliary variables
+   are not evolved, and after the step they are reconstructed from the new
+   primaries. The ghost cells of the auxiliary variables follow their
+   radiative condition in both variants. */
+int og_fo_rk4_step(const og_grid *g, const og_params *P, int variant, double dt, double *U, double *G,
+                   const double *Gini) {
+  const long pts = n_interior(g), nu = pts * OG_NV_FO, ng = g->n_ghost * OG_NV_FO;
+  double *k[4], *kg[4];
+  for (int s = 0; s < 4; ++s) {
+    k[s] = (double *)malloc(sizeof(double) * (size_t)nu);
+    kg[s] = (double *)malloc(sizeof(double) * (size_t)(ng > 0 ? ng : 1));
+  }
+  double *Y = (double *)malloc(sizeof(double) * (size_t)nu);
+  double *YG = (double *)malloc(sizeof(double) * (size_t)(ng > 0 ? ng : 1));
+  const double cnode[4] = {0.0, 0.5, 0.5, 1.0};
+  for (int s = 0; s < 4; ++s) {
+    if (s == 0) {
+      memcpy(Y, U, sizeof(double) * (size_t)nu);
+      if (ng) memcpy(YG, G, sizeof(double) * (size_t)ng);
+    } else {
+      for (long i = 0; i < nu; ++i) Y[i] = U[i] + cnode[s] * dt * k[s - 1][i];
+      for (long i = 0; i < ng; ++i) YG[i] = G[i] + cnode[s] * dt * kg[s - 1][i];
+    }
+    if (variant == 1) og_fo_reconstruct(g, Y, YG);
+    og_fo_rhs(g, P, variant == 0, Y, YG, Gini, k[s], kg[s]);
+    if (variant == 1) memset(k[s] + (long)OG_NV * pts, 0, sizeof(double) * (size_t)(nu - (long)OG_NV * pts));
+  }
+  for (long i = 0; i < nu; ++i) U[i] = U[i] + dt / 6.0 * (k[0][i] + 2.0 * k[1][i] + 2.0 * k[2][i] + k[3][i]);
+  for (long i = 0; i < ng; ++i) G[i] = G[i] + dt / 6.0 * (kg[0][i] + 2.0 * kg[1][i] + 2.0 * kg[2][i] + kg[3][i]);
+  og_enforce(g, U);
+  if (variant == 1) og_fo_reconstruct(g, U, G);
+  for (int s = 0; s < 4; ++s) { free(k[s]); free(kg[s]); }
+  free(Y); free(YG);
+  return 0;
+}

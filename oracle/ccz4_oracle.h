@@ -31,6 +31,7 @@ extern "C" {
 #endif
 
 #define OG_NV 25
+#define OG_NV_FO 58
 #define OG_HALO 3
 #define OG_MAX_LEVELS 8
 
@@ -83,6 +84,20 @@ int og_constraints_points(const og_grid *g, const double *U, const double *G, lo
 int og_point_derivs(const og_grid *g, const double *U, const double *G, long pt,
                     double ko_eps, double *d1 /* [25][3] */, double *d2 /* [25][3][3] */,
                     double *ko /* [25] */);
+
+/* First-order formulation (Eq. first-order-variables): arrays of 58
+   fields, the 25 primaries followed by A_k (25..27), B_k^i (28 + 3k + i),
+   D_kij (37 + 6k + pair(i,j)) and P_k (55..57), in the layouts above with
+   58 in place of 25. og_fo_rhs: red = 1 the first-order right-hand side
+   with the red terms, 0 without them. og_fo_reconstruct: the auxiliary
+   variables of the interior points from FD4 derivatives of the primaries.
+   og_fo_rk4_step: variant 0 first-order, 1 second-order with the
+   reconstruction of Alg. fd4-so. */
+int og_fo_rhs(const og_grid *g, const og_params *P, int red, const double *U, const double *G,
+              const double *Gini, double *rU, double *rG);
+int og_fo_reconstruct(const og_grid *g, double *U, const double *G);
+int og_fo_rk4_step(const og_grid *g, const og_params *P, int variant, double dt, double *U, double *G,
+                   const double *Gini);
 
 /* Particle tracers: trilinear projection of the fields at each of n
    positions pos[n][3] (values[n][25], may be NULL) and, for vel_field >= 0,

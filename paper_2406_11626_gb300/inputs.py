@@ -199,6 +199,85 @@ def brill_lindquist(x, y, z, masses=(1.0,), centres=((0.0, 0.0, 0.0),)):
     return Q
 
 
+# ---- the 58 variables of the first-order formulation ---------------------------
+# The 25 primaries, then A_k = d_k alpha (25..27), B_k^i = d_k beta^i
+# (28 + 3k + i), D_kij = 1/2 d_k g~_ij (37 + 6k + pair) and P_k = d_k phi
+# (55..57) (Eq. auxiliary-variables of the paper).
+NV_FO = 58
+FO_A, FO_B, FO_D, FO_P = 25, 28, 37, 55
+FO_FIELDS = FIELDS + tuple("A" + "xyz"[k] for k in range(3)) + tuple(
+    "B" + "xyz"[k] + "xyz"[i] for k in range(3) for i in range(3)) + tuple(
+    "D" + "xyz"[k] + p for k in range(3) for p in ("xx", "xy", "xz", "yy", "yz", "zz")) + tuple(
+    "P" + "xyz"[k] for k in range(3))
+
+
+def fo_state(Q, dQ):
+    """58 variables from the 25 primaries Q (25, ...) and their spatial
+    derivatives dQ (3, 25, ...), dQ[k, v] = d_k Q_v."""
+    out = np.zeros((NV_FO,) + Q.shape[1:])
+    out[:NV] = Q
+    for k in range(3):
+        out[FO_A + k] = dQ[k, IDX["alpha"]]
+        out[FO_P + k] = dQ[k, IDX["phi"]]
+        for i in range(3):
+            out[FO_B + 3 * k + i] = dQ[k, IDX["betax"] + i]
+        for c in range(6):
+            out[FO_D + 6 * k + c] = 0.5 * dQ[k, IDX["gxx"] + c]
+    return out
+
+
+def fo_gauge_wave(x, t=0.0, A=0.1, k=2.0):
+    """The gauge wave's 58 variables: every field is a function of x - t,
+    so d_x = -d_t, taken from the closed-form gauge_wave_dt."""
+    Q = gauge_wave(x, t, A, k)
+    dQ = np.zeros((3,) + Q.shape)
+    dQ[0] = -gauge_wave_dt(x, t, A, k)
+    return fo_state(Q, dQ)
+
+
+def fo_brill_lindquist(x, y, z, masses=(1.0,), centres=((0.0, 0.0, 0.0),)):
+    """Brill-Lindquist data with its auxiliary variables in closed form:
+    psi = 1 + s, s = sum m/(2 r), phi = psi^-2, the averaged lapse
+    ((1 - s)/(1 + s) + 1)/2 = 1/psi, so P_k = -2 psi^-3 d_k s and
+    A_k = -psi^-2 d_k s with d_k s = -sum m (x_k - c_k)/(2 r^3); B = D = 0."""
+    x, y, z = (np.asarray(v, dtype=np.float64) for v in (x, y, z))
+    Q = brill_lindquist(x, y, z, masses, centres)
+    s = np.zeros_like(x)
+    ds = np.zeros((3,) + x.shape)
+    for m, c in zip(masses, centres):
+        d = (x - c[0], y - c[1], z - c[2])
+        r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+        s = s + m / (2.0 * r)
+        for k in range(3):
+            ds[k] = ds[k] - m * d[k] / (2.0 * r ** 3)
+    psi = 1.0 + s
+    dQ = np.zeros((3,) + Q.shape)
+    for k in range(3):
+        dQ[k, IDX["phi"]] = -2.0 * psi ** -3 * ds[k]
+        dQ[k, IDX["alpha"]] = -(psi ** -2) * ds[k]
+    return fo_state(Q, dQ)
+
+
+def fo_initial_state(cfg):
+    """(U, G) of the 58 variables at t = 0 for the gauge-wave and
+    single-puncture configurations (single level)."""
+    x, y, z = point_coords(cfg.p, cfg.ijk(), cfg.origin, cfg.dx)
+    if cfg.name == "gauge_wave":
+        U = fo_gauge_wave(x, 0.0, cfg.extra["A"], cfg.extra["k"])
+        G = np.zeros((NV_FO, 0))
+        if cfg.bc == "sommerfeld":
+            gx, _, _ = ghost_positions(cfg.N, cfg.origin, cfg.dx)
+            G = fo_gauge_wave(gx, 0.0, cfg.extra["A"], cfg.extra["k"])
+    elif cfg.name == "single_puncture":
+        U = fo_brill_lindquist(x, y, z, (cfg.extra["M"],))
+        G = np.zeros((NV_FO, 0))
+        if cfg.bc == "sommerfeld":
+            G = fo_brill_lindquist(*ghost_positions(cfg.N, cfg.origin, cfg.dx), (cfg.extra["M"],))
+    else:
+        raise ValueError(cfg.name)
+    return np.ascontiguousarray(U), np.ascontiguousarray(G)
+
+
 def smooth_perturbation(x, y, z, seed, amp=1e-2, box=1.0, modes=3, base=None):
     """Flat space (or ``base``) plus, in every one of the 25 fields, a sum of
     ``modes`` seeded Fourier modes exp-periodic on a cube of side ``box``
