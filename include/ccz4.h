@@ -375,6 +375,54 @@ ccz4_status ccz4_mesh_plan(const ccz4_mesh_desc *desc, long long *n_interp, int 
 enum { CCZ4_LAUNCH_FLAT = 0, CCZ4_LAUNCH_QUEUE = 1 };
 ccz4_status ccz4_set_launch(ccz4_grid *g, int mode);
 
+/* ---- the first-order formulation and the second order with reconstruction ----
+   (Sec. "First- and Second-order Formulations", Eq. first-order-variables;
+   appendix "Spacetime foliation": the nine primary equations with the red
+   terms, Eqs. NR_foccz4_A_k, NR_foccz4_B^i_j, the D_kij equation and
+   NR_foccz4_P_i; Sec. "Explicit gradient reconstruction", Alg. fd4-fo and
+   Alg. fd4-so.) A ccz4_fo holds a 58-variable state on the geometry of a
+   single-level grid: the 25 primaries in the order above, then
+   A_k = d_k alpha (25..27), B_k^i = d_k beta^i (28 + 3k + i),
+   D_kij = 1/2 d_k g~_ij (37 + 6k + pair(i, j), pairs xx, xy, xz, yy, yz,
+   zz) and P_k = d_k phi (55..57). Only first derivatives are taken (FD4),
+   and Kreiss-Oliger dissipation is applied to all 58.
+     CCZ4_FO_FIRST_ORDER: every variable is evolved, with the red terms and
+       the mu terms of the B equation.
+     CCZ4_FO_SO_RECONSTRUCT: the paper's second-order formulation written
+       over the same 58 variables: the red terms are removed, only the
+       primaries (and the Sommerfeld ghost cells of every variable) are
+       evolved, and before the right-hand side of every RK stage, and after
+       every step, the auxiliary variables of the interior points are
+       reconstructed as FD4 first derivatives of the primaries (the extra
+       sweep of Alg. fd4-so).
+   The Sommerfeld ghost cells of every variable follow the radiative
+   condition of the boundary (speed somm_speed[v] for the primaries, 1 for
+   the auxiliary variables). After each step the primaries are enforced
+   (det g~ = 1, tr A~ = 0) as in ccz4_step. FP64 only (P->precision is
+   ignored). Buffers: CCZ4_BUF_U, Y0, Y1, ACC, RHS and (Sommerfeld) INI,
+   each [58][field stride] in the grid's layout; the stages use them as
+   ccz4_stage_buffers says.
+   ccz4_fo_alloc: CCZ4_ERR_INVALID for a refined mesh or an unknown
+   variant; CCZ4_ERR_NOMEM if the device memory runs out (about
+   58 x 8 bytes x (6 state buffers + 4.6 tile copies) per point).
+   ccz4_fo_upload / ccz4_fo_download: host U [58][n_points] (the grid's
+   point order) and G [58][n_ghost]; synchronous.
+   ccz4_fo_rhs: the right-hand side of all 58 (with the red terms only in
+   the first-order variant) of in_buf into out_buf; asynchronous.
+   ccz4_fo_reconstruct: the interior auxiliary variables of buf from FD4
+   derivatives of its primaries; asynchronous.
+   ccz4_fo_rk_stage / ccz4_fo_step: RK4 stages / steps, asynchronous. */
+enum { CCZ4_FO_FIRST_ORDER = 0, CCZ4_FO_SO_RECONSTRUCT = 1 };
+typedef struct ccz4_fo ccz4_fo;
+ccz4_status ccz4_fo_alloc(ccz4_grid *g, int variant, ccz4_fo **out);
+ccz4_status ccz4_fo_free(ccz4_fo *f);
+ccz4_status ccz4_fo_upload(ccz4_fo *f, int buf, const double *U, const double *G, void *stream);
+ccz4_status ccz4_fo_download(ccz4_fo *f, int buf, double *U, double *G, void *stream);
+ccz4_status ccz4_fo_rhs(ccz4_fo *f, const ccz4_params *P, int in_buf, int out_buf, void *stream);
+ccz4_status ccz4_fo_reconstruct(ccz4_fo *f, int buf, void *stream);
+ccz4_status ccz4_fo_rk_stage(ccz4_fo *f, const ccz4_params *P, int stage, double dt, void *stream);
+ccz4_status ccz4_fo_step(ccz4_fo *f, const ccz4_params *P, double dt, int n_steps, void *stream);
+
 /* ---- particle tracers and puncture trackers ----
    (Sec. "Particle Tracers as Data Probes"; Sec. "Particle tracers" for
    puncture trackers.) A set of n tracers on a grid. Each step records the

@@ -95,6 +95,20 @@ def lib():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    fo_sig = {
+        "ccz4_fo_alloc": [vp, ctypes.c_int, ctypes.POINTER(vp)],
+        "ccz4_fo_free": [vp],
+        "ccz4_fo_upload": [vp, ctypes.c_int, _dbl_p, _dbl_p, vp],
+        "ccz4_fo_download": [vp, ctypes.c_int, _dbl_p, _dbl_p, vp],
+        "ccz4_fo_rhs": [vp, ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int, vp],
+        "ccz4_fo_reconstruct": [vp, ctypes.c_int, vp],
+        "ccz4_fo_rk_stage": [vp, ctypes.POINTER(Params), ctypes.c_int, ctypes.c_double, vp],
+        "ccz4_fo_step": [vp, ctypes.POINTER(Params), ctypes.c_double, ctypes.c_int, vp],
+    }
+    for name, args in fo_sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
     L.ccz4_tracers_new.argtypes = [vp, ctypes.c_int, _dbl_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(vp)]
     L.ccz4_tracers_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, vp]
     L.ccz4_tracers_read.argtypes = [vp, _dbl_p, _dbl_p, vp]
@@ -360,6 +374,63 @@ class Grid:
             return out
         _check(code)
         return out
+
+
+FO_VARIANT = {"fo": 0, "so-recon": 1}
+
+
+class FirstOrder:
+    """The 58-variable formulations on a single-level grid (ccz4_fo_* in
+    include/ccz4.h): variant "fo", the first-order formulation (every
+    variable evolved, red terms kept), or "so-recon", the second-order one
+    whose auxiliary variables are reconstructed from FD4 derivatives of the
+    primaries before every stage. Arrays are (58, n_patches, p, p, p) and
+    (58, n_ghost)."""
+
+    NV = 58
+
+    def __init__(self, grid, variant="fo"):
+        self.grid = grid   # the grid must outlive the formulation
+        self.variant = variant
+        h = ctypes.c_void_p()
+        _check(lib().ccz4_fo_alloc(grid._h, FO_VARIANT[variant], ctypes.byref(h)))
+        self._h = h
+
+    def upload(self, U, G=None, buf="U", stream=None):
+        g = self.grid
+        U = np.ascontiguousarray(U, dtype=np.float64).reshape(self.NV, g.n_points)
+        Gc = np.ascontiguousarray(G, dtype=np.float64).reshape(self.NV, g.n_ghost) if g.n_ghost else None
+        _check(lib().ccz4_fo_upload(self._h, _buf(buf), _d(U), _d(Gc), _stream(stream)))
+
+    def download(self, buf="U", stream=None):
+        g = self.grid
+        U = np.empty((self.NV, g.n_patches, g.p, g.p, g.p))
+        G = np.empty((self.NV, g.n_ghost))
+        _check(lib().ccz4_fo_download(self._h, _buf(buf), _d(U), _d(G) if g.n_ghost else None, _stream(stream)))
+        return U, G
+
+    def rhs(self, P, in_buf="U", out_buf="RHS", stream=None):
+        _check(lib().ccz4_fo_rhs(self._h, ctypes.byref(P), _buf(in_buf), _buf(out_buf), _stream(stream)))
+
+    def reconstruct(self, buf="U", stream=None):
+        _check(lib().ccz4_fo_reconstruct(self._h, _buf(buf), _stream(stream)))
+
+    def rk_stage(self, P, stage, dt, stream=None):
+        _check(lib().ccz4_fo_rk_stage(self._h, ctypes.byref(P), int(stage), float(dt), _stream(stream)))
+
+    def step(self, P, dt, n_steps=1, stream=None):
+        _check(lib().ccz4_fo_step(self._h, ctypes.byref(P), float(dt), int(n_steps), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ccz4_fo_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Tracers:
