@@ -436,6 +436,34 @@ def time_graph(g, P, dt, K, W, stream, dist):
     return e0.elapsed_time(e1)
 
 
+def time_first_order(C, I, cfg, K, W, stream):
+    """The paper's two other formulations on the same workload (single
+    level): the first-order one (58 variables evolved, red terms) and the
+    second-order one with the reconstruction sweep of the auxiliary
+    variables, K RK4 steps after W warm-up steps each; ms per step."""
+    import torch
+    g = C.Grid.from_config(cfg)
+    U, G = I.fo_initial_state(cfg)
+    P = C.make_params(**cfg.params)
+    out = {}
+    for variant in ("fo", "so-recon"):
+        fo = C.FirstOrder(g, variant)
+        fo.upload(U, G)
+        if g.n_ghost:
+            fo.upload(U, G, buf="INI")
+        fo.step(P, cfg.dt, W, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fo.step(P, cfg.dt, K, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[variant] = e0.elapsed_time(e1) / K
+        fo.close()
+    g.close()
+    return out
+
+
 def max_over_ranks(x, dist, device):
     """The largest value of x over the ranks (the slowest rank sets the job time)."""
     import torch
@@ -525,6 +553,18 @@ def run_gb300(args):
                  "fp64_flops_per_point_stage": flm["fp64"], "fp32_flops_per_point_stage": flm["fp32"]}
         del g64, gmx
 
+    first_order = None
+    if not args.no_mixed and args.precision == "fp64" and getattr(cfg, "level", None) is None:
+        fo_ms = time_first_order(C, I, cfg, K, args.warmup, stream)
+        first_order = {
+            variant: {"value": world * cfg.n_points * 4 / (t * 1e-3), "unit": UNIT, "ms_per_step": t,
+                      "vs_second_order_path": (ms / K) / t}
+            for variant, t in fo_ms.items()}
+        first_order["how"] = ("ccz4_fo_step on the same workload and steps: 'fo' the first-order formulation "
+                              "(58 variables evolved, red terms), 'so-recon' the second-order formulation over "
+                              "the 58 variables with the auxiliary variables reconstructed before every stage; "
+                              "vs_second_order_path = this build's second-order step time / this one's (>1: faster)")
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -572,6 +612,8 @@ def run_gb300(args):
     }
     if mixed is not None:
         line["mixed"] = mixed
+    if first_order is not None:
+        line["first_order"] = first_order
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(workload=args.workload)
     print(json.dumps(line), flush=True)
