@@ -7,7 +7,10 @@
  * removed) on p^3 Cartesian patches with a halo of width 3 -- one uniform
  * level, or a statically refined mesh of ratio-3 levels -- discretised by fourth-order central finite differences with
  * Kreiss-Oliger dissipation (appendix "Formulation for the kernel FD4
- * Solver") and classic RK4 in time (Sec. "Finite Differences"). All work
+ * Solver") and classic RK4 in time (Sec. "Finite Differences"). Beside it:
+ * the first-order formulation and the second order with reconstructed
+ * auxiliary variables over 58 variables (ccz4_fo_*), particle tracers and
+ * puncture trackers (ccz4_tracers_*), and the constraint monitors. All work
  * runs in CUDA kernels on the current device; there is no CPU fallback.
  *
  * Conventions for every call
@@ -115,7 +118,7 @@ typedef struct {
 /* Physical and numerical parameters (appendix "Spacetime foliation":
    kappa1, kappa2, kappa3, e, c, tau, mu, f, eta, s, K0; Eq. exa_fd4_ko:
    the dissipation strength epsilon). mu enters only the first-order
-   formulation and is unused here. somm_speed is the wave speed c of the
+   formulation (ccz4_fo_*). somm_speed is the wave speed c of the
    Sommerfeld condition per field. */
 typedef struct {
   double kappa1, kappa2, kappa3, e, c, tau, mu, f, eta, s, K0, ko_eps;
@@ -246,6 +249,22 @@ ccz4_status ccz4_enforce(ccz4_grid *g, int buf, void *stream);
    out[4] > 0 (out is still filled). */
 ccz4_status ccz4_constraints(ccz4_grid *g, int buf, double out[5], double *dev_H, double *dev_M,
                              void *stream);
+
+/* The constraint norms away from the punctures (Sec. "Gauge Wave" for the
+   L2 norm; the puncture region r < 1 of Sec. "Single black hole" left
+   out): from the per-point H [n_points] and M [3][n_points] on the device,
+   as ccz4_constraints writes them for this grid, the L2 norms of H and |M|
+   (sqrt of the mean of the squares), max |H| and max |M| over the interior
+   points of leaf patches whose cell centre lies at a distance of at least
+   `radius` from every one of the n_centres centres (host [n_centres][3],
+   at most CCZ4_MAX_EXCLUDED), and in out[4] the number of those points.
+   Points with a non-finite H or M are left out. The reduction runs in a
+   fixed order (repeated calls agree bit for bit). Synchronises the stream.
+   CCZ4_ERR_INVALID for missing arrays, too many centres or a negative
+   radius. */
+#define CCZ4_MAX_EXCLUDED 8
+ccz4_status ccz4_constraints_excluding(ccz4_grid *g, const double *dev_H, const double *dev_M, int n_centres,
+                                       const double *centres, double radius, double out[5], void *stream);
 
 /* Constraint monitors for callers that cannot allocate device memory (a
    host framework that owns all device memory and forbids other

@@ -85,6 +85,8 @@ def lib():
         L.og_fo_reconstruct.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p]
         L.og_fo_rk4_step.argtypes = [ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_int, ctypes.c_double,
                                      _dbl_p, _dbl_p, _dbl_p]
+        L.og_constraints_excluding.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, ctypes.c_int, _dbl_p,
+                                               ctypes.c_double, _dbl_p]
         L.og_tracers_step.restype = ctypes.c_long
         L.og_tracers_step.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, ctypes.c_long, _dbl_p, ctypes.c_double,
                                       ctypes.c_int, ctypes.c_double, _dbl_p]
@@ -211,6 +213,16 @@ class Grid:
         out = np.empty(5)
         lib().og_constraints(self._h, _d(U), _d(G), _d(H), _d(M), _d(out))
         return H, M, out
+
+    def constraints_excluding(self, H, M, centres, radius):
+        """Norms of H and |M| over leaf points at distance >= radius from
+        every centre: (L2 H, L2 |M|, max |H|, max |M|, count)."""
+        H = _f64(H, self.ushape[1:])
+        M = _f64(M, (3,) + self.ushape[1:])
+        c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
+        out = np.empty(5)
+        lib().og_constraints_excluding(self._h, _d(H), _d(M), len(c), _d(c), float(radius), _d(out))
+        return out
 
     def rhs_points(self, P, U, G, pts):
         U = _f64(U, self.ushape)

@@ -1849,3 +1849,54 @@ int og_fo_rk4_step(const og_grid *g, const og_params *P, int variant, double dt,
   free(Y); free(YG);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* constraint norms away from the punctures                                 */
+/* ------------------------------------------------------------------------ */
+
+/* The L2 norms of Sec. "Gauge Wave" (sqrt of the mean of H^2 and of |M|^2)
+   over the interior points of leaf patches whose cell centre lies at a
+   distance of at least `radius` from every one of the n_c centres[3 n_c],
+   from the per-point H[pts] and M[3][pts] of og_constraints (the norm that
+   leaves out the region r < 1 around the punctures). out = L2 of H, L2 of
+   |M|, max |H|, max |M| over those points, and their count; points with a
+   non-finite H or M are left out. */
+int og_constraints_excluding(const og_grid *g, const double *H, const double *M, int n_c, const double *centres,
+                             double radius, double out[5]) {
+  const int p = g->p;
+  const long pts = n_interior(g);
+  double sH = 0.0, sM = 0.0, mH = 0.0, mM = 0.0, count = 0.0;
+  for (int n = 0; n < g->n_patches; ++n) {
+    if (g->nchild[n] != 0) continue;
+    const double h = g->dxl[g->lev[n]];
+    for (int z = 0; z < p; ++z)
+      for (int y = 0; y < p; ++y)
+        for (int x = 0; x < p; ++x) {
+          const double pos[3] = {g->origin[0] + (g->ijk[3 * n] * p + x + 0.5) * h,
+                                 g->origin[1] + (g->ijk[3 * n + 1] * p + y + 0.5) * h,
+                                 g->origin[2] + (g->ijk[3 * n + 2] * p + z + 0.5) * h};
+          int near = 0;
+          for (int c = 0; c < n_c; ++c) {
+            double r2 = 0.0;
+            for (int d = 0; d < 3; ++d) r2 += (pos[d] - centres[3 * c + d]) * (pos[d] - centres[3 * c + d]);
+            if (r2 < radius * radius) near = 1;
+          }
+          if (near) continue;
+          const long li = (long)n * p * p * p + ((long)z * p + y) * p + x;
+          const double hv = H[li];
+          const double m2 = M[li] * M[li] + M[pts + li] * M[pts + li] + M[2 * pts + li] * M[2 * pts + li];
+          if (!isfinite(hv) || !isfinite(m2)) continue;
+          sH += hv * hv;
+          sM += m2;
+          if (fabs(hv) > mH) mH = fabs(hv);
+          if (sqrt(m2) > mM) mM = sqrt(m2);
+          count += 1.0;
+        }
+  }
+  out[0] = count > 0.0 ? sqrt(sH / count) : 0.0;
+  out[1] = count > 0.0 ? sqrt(sM / count) : 0.0;
+  out[2] = mH;
+  out[3] = mM;
+  out[4] = count;
+  return 0;
+}

@@ -85,6 +85,12 @@ int og_point_derivs(const og_grid *g, const double *U, const double *G, long pt,
                     double ko_eps, double *d1 /* [25][3] */, double *d2 /* [25][3][3] */,
                     double *ko /* [25] */);
 
+/* L2 norms of H and |M| over the interior points of leaf patches at a
+   distance >= radius from every one of the n_c centres (from og_constraints'
+   per-point H and M): out = L2 H, L2 |M|, max |H|, max |M|, point count. */
+int og_constraints_excluding(const og_grid *g, const double *H, const double *M, int n_c, const double *centres,
+                             double radius, double out[5]);
+
 /* First-order formulation (Eq. first-order-variables): arrays of 58
    fields, the 25 primaries followed by A_k (25..27), B_k^i (28 + 3k + i),
    D_kij (37 + 6k + pair(i,j)) and P_k (55..57), in the layouts above with

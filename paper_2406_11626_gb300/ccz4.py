@@ -109,6 +109,8 @@ def lib():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    L.ccz4_constraints_excluding.argtypes = [vp, vp, vp, ctypes.c_int, _dbl_p, ctypes.c_double, _dbl_p, vp]
+    L.ccz4_constraints_excluding.restype = ctypes.c_int
     L.ccz4_tracers_new.argtypes = [vp, ctypes.c_int, _dbl_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(vp)]
     L.ccz4_tracers_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, vp]
     L.ccz4_tracers_read.argtypes = [vp, _dbl_p, _dbl_p, vp]
@@ -373,6 +375,16 @@ class Grid:
         if code == ERR_NONFINITE and not raise_nonfinite:
             return out
         _check(code)
+        return out
+
+    def constraints_excluding(self, dev_H, dev_M, centres, radius=1.0, stream=None):
+        """Norms of the per-point H and M (device pointers, as constraints()
+        writes them) over leaf points at a distance >= radius from every
+        centre: (L2 H, L2 |M|, max |H|, max |M|, point count)."""
+        c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
+        out = np.empty(5)
+        _check(lib().ccz4_constraints_excluding(self._h, ctypes.c_void_p(dev_H), ctypes.c_void_p(dev_M), len(c),
+                                                _d(c), float(radius), _d(out), _stream(stream)))
         return out
 
 

@@ -24,6 +24,10 @@ void set_error(const char *fmt, ...) {
 }
 
 int constraint_blocks(long long n_points);
+// constraint norms over the leaf points outside n_centres balls (constraints.cu)
+cudaError_t launch_constraints_excluded(const GridView &g, const double *H, const double *M, int n_centres,
+                                        const double *centres, double radius, double *partial, int blocks,
+                                        double *out5, cudaStream_t s);
 
 }  // namespace ccz4
 
@@ -704,6 +708,25 @@ extern "C" ccz4_status ccz4_constraints(ccz4_grid *g, int buf, double out[5], do
     set_error("%.0f points have non-finite constraint values", out[4]);
     return CCZ4_ERR_NONFINITE;
   }
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_constraints_excluding(ccz4_grid *g, const double *dev_H, const double *dev_M,
+                                                  int n_centres, const double *centres, double radius,
+                                                  double out[5], void *stream) {
+  if (check_grid(g)) return CCZ4_ERR_INVALID;
+  if (!dev_H || !dev_M || !out || n_centres < 0 || n_centres > CCZ4_MAX_EXCLUDED || (n_centres > 0 && !centres) ||
+      !(radius >= 0.0)) {
+    set_error("constraints_excluding: dev_H, dev_M and out must be given, 0 <= n_centres <= %d, radius >= 0",
+              CCZ4_MAX_EXCLUDED);
+    return CCZ4_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(launch_constraints_excluded(g->v, dev_H, dev_M, n_centres, centres, radius, g->red_partial,
+                                       g->red_blocks, g->red_out, s));
+  CUDA_TRY(cudaMemcpyAsync(g->host_out, g->red_out, sizeof(double) * 5, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  memcpy(out, g->host_out, sizeof(double) * 5);
   return CCZ4_OK;
 }
 

@@ -295,6 +295,96 @@ __global__ void __launch_bounds__(RED_THREADS) reduce_partials(const double *par
   }
 }
 
+// Centres and radius of the regions left out of the constraint norms.
+struct Excl {
+  int n;
+  double c[CCZ4_MAX_EXCLUDED][3];
+  double r2;
+};
+
+// Per-block partial sums of H^2 and |M|^2, maxima of |H| and |M| and the
+// count over the interior points of leaf patches outside every ball.
+__global__ void __launch_bounds__(RED_THREADS) excluded_kernel(GridView g, Excl E, const double *__restrict__ H,
+                                                               const double *__restrict__ M, double *partial) {
+  __shared__ double sh[5][RED_THREADS];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (i < g.n_points) {
+    const int p = g.p;
+    const int p3 = p * p * p;
+    const int n = (int)i / p3;
+    const int r = (int)i - n * p3;
+    const int z = r / (p * p), y = (r / p) % p, x = r % p;
+    const double h = g.ldx[patch_level(g, n)];
+    const double pos[3] = {g.origin[0] + (__ldg(g.ijk + 3 * n) * p + x + 0.5) * h,
+                           g.origin[1] + (__ldg(g.ijk + 3 * n + 1) * p + y + 0.5) * h,
+                           g.origin[2] + (__ldg(g.ijk + 3 * n + 2) * p + z + 0.5) * h};
+    bool near = false;
+    for (int c = 0; c < E.n; ++c) {
+      const double d0 = pos[0] - E.c[c][0], d1 = pos[1] - E.c[c][1], d2 = pos[2] - E.c[c][2];
+      near = near || d0 * d0 + d1 * d1 + d2 * d2 < E.r2;
+    }
+    const bool counted = (!g.leaf || __ldg(g.leaf + n)) && !near;
+    const double hv = H[i];
+    const double m2 = M[i] * M[i] + M[g.n_points + i] * M[g.n_points + i] + M[2 * g.n_points + i] * M[2 * g.n_points + i];
+    if (counted && isfinite(hv) && isfinite(m2)) {
+      v[0] = hv * hv;
+      v[1] = m2;
+      v[2] = fabs(hv);
+      v[3] = sqrt(m2);
+      v[4] = 1.0;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] = v[q];
+  __syncthreads();
+  for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+      sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + w]);
+      sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + w]);
+      sh[4][threadIdx.x] += sh[4][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) partial[blockIdx.x * 5 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// Folds the partials in a fixed order; the norms divide by the point count.
+__global__ void __launch_bounds__(RED_THREADS) reduce_excluded(const double *partial, int blocks, double *out) {
+  __shared__ double sh[5][RED_THREADS];
+  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < blocks; b += RED_THREADS) {
+    v[0] += partial[b * 5 + 0];
+    v[1] += partial[b * 5 + 1];
+    v[2] = fmax(v[2], partial[b * 5 + 2]);
+    v[3] = fmax(v[3], partial[b * 5 + 3]);
+    v[4] += partial[b * 5 + 4];
+  }
+#pragma unroll
+  for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] = v[q];
+  __syncthreads();
+  for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+      sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + w]);
+      sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + w]);
+      sh[4][threadIdx.x] += sh[4][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double cnt = sh[4][0];
+    out[0] = cnt > 0.0 ? sqrt(sh[0][0] / cnt) : 0.0;
+    out[1] = cnt > 0.0 ? sqrt(sh[1][0] / cnt) : 0.0;
+    out[2] = sh[2][0];
+    out[3] = sh[3][0];
+    out[4] = cnt;
+  }
+}
+
 __global__ void __launch_bounds__(256) enforce_kernel(GridView g, double *U) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n_points) return;
@@ -332,6 +422,23 @@ cudaError_t launch_constraints(const GridView &g, const double *tile, double *H,
     if (e != cudaSuccess) return e;
   }
   reduce_partials<<<1, RED_THREADS, 0, s>>>(partial, blocks, (double)g.n_leaf_points, out5);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_constraints_excluded(const GridView &g, const double *H, const double *M, int n_centres,
+                                        const double *centres, double radius, double *partial, int blocks,
+                                        double *out5, cudaStream_t s) {
+  Excl E;
+  E.n = n_centres;
+  for (int c = 0; c < n_centres; ++c)
+    for (int d = 0; d < 3; ++d) E.c[c][d] = centres[3 * c + d];
+  E.r2 = radius * radius;
+  if (blocks > 0) {
+    excluded_kernel<<<blocks, RED_THREADS, 0, s>>>(g, E, H, M, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  reduce_excluded<<<1, RED_THREADS, 0, s>>>(partial, blocks, out5);
   return cudaGetLastError();
 }
 

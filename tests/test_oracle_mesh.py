@@ -365,3 +365,37 @@ def test_a_step_on_a_symmetric_mesh_is_rotation_covariant(R):
     expect = _rotate_levels(U1, g, lev, ijk, R)
     np.testing.assert_allclose(Ur1, expect, rtol=0, atol=1e-12 * np.abs(U1).max())
     assert np.abs(U1 - U).max() > 1e-6  # the step did move the data
+
+
+def test_constraint_norms_away_from_the_punctures():
+    """The norms that leave out the balls r < radius around the punctures:
+    radius 0 gives the monitor's own leaf-point norms; otherwise they equal
+    a brute-force mean over the leaf points outside every ball (positions
+    from the cell centres of each level); a ball over everything leaves no
+    point."""
+    lev, ijk = I.refined_mesh((4, 4, 4), [((1, 1, 1), (3, 3, 3))], permute_seed=6)
+    p, origin, dx = 6, (-2.0, -2.0, -2.0), 1.0 / 6.0
+    g = O.Grid(p, (4, 4, 4), ijk, origin, dx, "sommerfeld", level=lev)
+    x, y, z = I.mesh_point_coords(p, lev, ijk, origin, dx)
+    U = I.smooth_perturbation(x, y, z, seed=4, amp=1e-2, box=4.0,
+                              base=I.brill_lindquist(x, y, z, (0.5, 0.5), ((-0.7, 0.1, 0.0), (0.7, -0.1, 0.0))))
+    gx, gy, gz = I.ghost_positions((24, 24, 24), origin, dx)
+    G = I.brill_lindquist(gx, gy, gz, (0.5, 0.5), ((-0.7, 0.1, 0.0), (0.7, -0.1, 0.0)))
+    H, M, out = g.constraints(U, G)
+    centres = [(-0.7, 0.1, 0.0), (0.7, -0.1, 0.0)]
+    e0 = g.constraints_excluding(H, M, centres, 0.0)
+    np.testing.assert_allclose(e0[:4], out[:4], rtol=1e-13)
+    # brute force: leaf patches (no children) and the points outside both balls
+    kids = {tuple(c // 3) for c in ijk[lev == 1]}
+    leaf = np.array([not (l == 0 and tuple(c) in kids) for l, c in zip(lev, ijk)])
+    for radius in (0.5, 1.0):
+        far = np.ones(x.shape, dtype=bool)
+        for c in centres:
+            far &= (x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2 >= radius ** 2
+        sel = far & leaf[:, None, None, None]
+        h, m2 = H[sel], (M ** 2).sum(axis=0)[sel]
+        e = g.constraints_excluding(H, M, centres, radius)
+        assert e[4] == sel.sum() and 0 < e[4] < leaf.sum() * p ** 3
+        np.testing.assert_allclose(e[:4], [np.sqrt(np.mean(h ** 2)), np.sqrt(np.mean(m2)), np.abs(h).max(),
+                                           np.sqrt(m2).max()], rtol=1e-12)
+    assert g.constraints_excluding(H, M, centres, 100.0)[4] == 0.0
