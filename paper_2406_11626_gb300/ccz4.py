@@ -88,6 +88,7 @@ def lib():
         "ccz4_mesh_info": [vp, ctypes.POINTER(ctypes.c_int), ll_p],
         "ccz4_restrict": [vp, ctypes.c_int, vp],
         "ccz4_set_launch": [vp, ctypes.c_int],
+        "ccz4_set_tuning": [vp, ctypes.c_int, ctypes.c_int],
         "ccz4_mesh_plan": [ctypes.POINTER(MeshDesc), ll_p, ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_int)],
     }
@@ -274,6 +275,12 @@ class Grid:
     def set_launch(self, mode):
         """'flat' (default) or 'queue' launch of the stage kernel."""
         _check(lib().ccz4_set_launch(self._h, {"flat": 0, "queue": 1}[mode] if isinstance(mode, str) else int(mode)))
+
+    def set_tuning(self, stage_shape=0, fill_shape=0):
+        """Launch shapes of the flat stage kernel (0 default, 1 one resident
+        block more, 2 one fewer) and of the halo fill (0 default, 1 512
+        threads, 2 16 loads per thread, 3 128 threads); results are identical."""
+        _check(lib().ccz4_set_tuning(self._h, int(stage_shape), int(fill_shape)))
 
     def restrict(self, buf="U", stream=None):
         """Coarse points under refined patches <- mean of their 27 fine cells."""

@@ -559,6 +559,21 @@ extern "C" ccz4_status ccz4_set_launch(ccz4_grid *g, int mode) {
   return CCZ4_OK;
 }
 
+extern "C" ccz4_status ccz4_set_tuning(ccz4_grid *g, int stage_shape, int fill_shape) {
+  if (check_grid(g)) return CCZ4_ERR_INVALID;
+  if (stage_shape < 0 || stage_shape > 2 || fill_shape < 0 || fill_shape > 3) {
+    set_error("set_tuning: stage shape must be 0..2 and fill shape 0..3 (got %d, %d)", stage_shape, fill_shape);
+    return CCZ4_ERR_INVALID;
+  }
+  if ((stage_shape != g->v.stage_shape || fill_shape != g->v.fill_shape) && g->step_exec) {
+    cudaGraphExecDestroy(g->step_exec);  // the captured step used the other shapes
+    g->step_exec = nullptr;
+  }
+  g->v.stage_shape = stage_shape;
+  g->v.fill_shape = fill_shape;
+  return CCZ4_OK;
+}
+
 extern "C" ccz4_status ccz4_restrict(ccz4_grid *g, int buf, void *stream) {
   if (check_grid(g)) return CCZ4_ERR_INVALID;
   if (!state_buffer(buf) || !g->buf[buf]) {

@@ -110,6 +110,8 @@ struct GridView {
   const unsigned char *leaf;   // [n_patches] 1 if the patch has no children
   double ldx[MAX_LEVELS];      // spacing of each level (ldx[0] = dx)
   unsigned long long *queue;   // work counter of the queue launch of the stage kernel, or nullptr (flat)
+  int stage_shape;             // launch shape of the flat stage kernel (CCZ4_STAGE_SHAPE_*)
+  int fill_shape;              // launch shape of the halo fill (CCZ4_FILL_SHAPE_*)
 };
 
 // Level of patch n (0 on a single level).

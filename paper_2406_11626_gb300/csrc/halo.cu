@@ -30,17 +30,12 @@
 namespace ccz4 {
 namespace {
 
-#ifndef CCZ4_FILL_THREADS
-#define CCZ4_FILL_THREADS 256
-#endif
-#ifndef CCZ4_FILL_GATHER_BATCH
-#define CCZ4_FILL_GATHER_BATCH 8
-#endif
-#ifndef CCZ4_FILL_MIN_BLOCKS
-#define CCZ4_FILL_MIN_BLOCKS 4
-#endif
-constexpr int FILL_THREADS = CCZ4_FILL_THREADS;
-constexpr int GATHER_BATCH = CCZ4_FILL_GATHER_BATCH;
+// Launch shapes of the fill (threads per block, independent loads per
+// thread in the gather), chosen per grid (CCZ4_FILL_SHAPE_*): 0 the
+// default 256 threads and 8 loads, 1 512 threads, 2 16 loads, 3 128
+// threads. Each asks for 1024 threads' worth of resident blocks.
+constexpr int FILL_SHAPE_THREADS[4] = {256, 512, 256, 128};
+constexpr int FILL_SHAPE_BATCH[4] = {8, 8, 16, 8};
 constexpr size_t FILL_SMEM_LIMIT = 227 * 1024;  // dynamic shared memory one block may use
 
 // Whether the d_z pass of the mixed derivatives fits on the region widened
@@ -145,10 +140,12 @@ __device__ __forceinline__ double lerp3(int r, double a, double b) {
 // MESH: the tile sources come from the host-built table of a refined mesh
 // (and may be interpolations); otherwise they are resolved here. F32W: FP32
 // weights for the mixed derivatives (see mixed_out).
-template <bool MESH, bool F32W>
-__global__ void __launch_bounds__(FILL_THREADS, CCZ4_FILL_MIN_BLOCKS) fill_halos_kernel(GridView g, const double *__restrict__ src,
-                                                                  double *__restrict__ tile,
-                                                                  double *__restrict__ mix, LevelScale ls) {
+template <bool MESH, bool F32W, int SHAPE>
+__global__ void __launch_bounds__(FILL_SHAPE_THREADS[SHAPE], 1024 / FILL_SHAPE_THREADS[SHAPE])
+    fill_halos_kernel(GridView g, const double *__restrict__ src, double *__restrict__ tile,
+                      double *__restrict__ mix, LevelScale ls) {
+  constexpr int FILL_THREADS = FILL_SHAPE_THREADS[SHAPE];
+  constexpr int GATHER_BATCH = FILL_SHAPE_BATCH[SHAPE];
   extern __shared__ double smem[];
   const int n = blockIdx.x;
   const int p = g.p, T = g.T;
@@ -315,15 +312,40 @@ size_t fill_smem_bytes(int p) {
 
 // Raises the kernel's dynamic shared-memory limit for patch edge p (once per
 // grid, outside any stream capture).
-cudaError_t prepare_fill_halos(int p) {
-  const int bytes = (int)fill_smem_bytes(MAX_P > p ? MAX_P : p);
-  const void *kernels[4] = {(const void *)fill_halos_kernel<false, false>, (const void *)fill_halos_kernel<false, true>,
-                            (const void *)fill_halos_kernel<true, false>, (const void *)fill_halos_kernel<true, true>};
+template <int SHAPE>
+cudaError_t prepare_shape(int bytes) {
+  const void *kernels[4] = {(const void *)fill_halos_kernel<false, false, SHAPE>,
+                            (const void *)fill_halos_kernel<false, true, SHAPE>,
+                            (const void *)fill_halos_kernel<true, false, SHAPE>,
+                            (const void *)fill_halos_kernel<true, true, SHAPE>};
   for (const void *k : kernels) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t prepare_fill_halos(int p) {
+  const int bytes = (int)fill_smem_bytes(MAX_P > p ? MAX_P : p);
+  cudaError_t e = prepare_shape<0>(bytes);
+  if (e == cudaSuccess) e = prepare_shape<1>(bytes);
+  if (e == cudaSuccess) e = prepare_shape<2>(bytes);
+  if (e == cudaSuccess) e = prepare_shape<3>(bytes);
+  return e;
+}
+
+template <int SHAPE>
+void launch_fill_shape(const GridView &g, const double *src, double *tile, double *mix, cudaStream_t s,
+                       bool fp32_weights, size_t bytes, const LevelScale &ls) {
+  const dim3 grid(g.n_patches), block(FILL_SHAPE_THREADS[SHAPE]);
+  if (g.src && fp32_weights)
+    fill_halos_kernel<true, true, SHAPE><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
+  else if (g.src)
+    fill_halos_kernel<true, false, SHAPE><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
+  else if (fp32_weights)
+    fill_halos_kernel<false, true, SHAPE><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
+  else
+    fill_halos_kernel<false, false, SHAPE><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
 }
 
 cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile, double *mix, cudaStream_t s,
@@ -335,15 +357,12 @@ cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile
     ls.cmix[l] = 1.0 / (144.0 * g.ldx[l] * g.ldx[l]);
     ls.cmixf[l] = (float)ls.cmix[l];
   }
-  const dim3 grid(g.n_patches), block(FILL_THREADS);
-  if (g.src && fp32_weights)
-    fill_halos_kernel<true, true><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
-  else if (g.src)
-    fill_halos_kernel<true, false><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
-  else if (fp32_weights)
-    fill_halos_kernel<false, true><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
-  else
-    fill_halos_kernel<false, false><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
+  switch (g.fill_shape) {
+    case 1: launch_fill_shape<1>(g, src, tile, mix, s, fp32_weights, bytes, ls); break;
+    case 2: launch_fill_shape<2>(g, src, tile, mix, s, fp32_weights, bytes, ls); break;
+    case 3: launch_fill_shape<3>(g, src, tile, mix, s, fp32_weights, bytes, ls); break;
+    default: launch_fill_shape<0>(g, src, tile, mix, s, fp32_weights, bytes, ls); break;
+  }
   return cudaGetLastError();
 }
 

@@ -77,6 +77,26 @@ struct StageArgs {
 };
 
 
+// Stencil coefficients of every level, in the differencing type (double)
+// and in the algebra type R.
+template <class R>
+struct LevelCoef {
+  StencilCoef<double> C[MAX_LEVELS];
+  StencilCoef<R> CR[MAX_LEVELS];
+};
+
+// Flat stage-kernel launches of the shapes other than the default (one
+// resident block more or fewer, CCZ4_STAGE_SHAPE_*), RK4 stages 0..3 only;
+// instantiated in rhs_shapes.cu (single level) and rhs_mesh_shapes.cu.
+cudaError_t launch_shaped_uniform(const GridView &g, int stage, const Phys<double> &ph, const LevelCoef<double> &LC,
+                                  const double *tile, const double *mix, const StageArgs &a, cudaStream_t s);
+cudaError_t launch_shaped_uniform(const GridView &g, int stage, const Phys<float> &ph, const LevelCoef<float> &LC,
+                                  const double *tile, const double *mix, const StageArgs &a, cudaStream_t s);
+cudaError_t launch_shaped_mesh(const GridView &g, int stage, const Phys<double> &ph, const LevelCoef<double> &LC,
+                               const double *tile, const double *mix, const StageArgs &a, cudaStream_t s);
+cudaError_t launch_shaped_mesh(const GridView &g, int stage, const Phys<float> &ph, const LevelCoef<float> &LC,
+                               const double *tile, const double *mix, const StageArgs &a, cudaStream_t s);
+
 // Launches stage `stage` (-1: plain RHS) with the kernels of a single level
 // (rhs.cu) or of a refined mesh (rhs_mesh.cu).
 cudaError_t launch_stage_uniform(const GridView &g, const ccz4_params &P, int stage, const double *tile,
@@ -150,21 +170,13 @@ struct StageSink {
   }
 };
 
-// Stencil coefficients of every level, in the differencing type (double)
-// and in the algebra type R.
-template <class R>
-struct LevelCoef {
-  StencilCoef<double> C[MAX_LEVELS];
-  StencilCoef<R> CR[MAX_LEVELS];
-};
-
-template <class R>
+// Resident blocks of 128 threads per SM that a launch shape asks of the
+// stage kernel: the default of the precision, one more (shape 1) or one
+// fewer (shape 2).
+template <class R, int SHAPE>
 struct StageBlocks {
-  static constexpr int value = CCZ4_INTERIOR_MIN_BLOCKS;
-};
-template <>
-struct StageBlocks<float> {
-  static constexpr int value = CCZ4_INTERIOR_MIN_BLOCKS_MIXED;
+  static constexpr int base = std::is_same<R, float>::value ? CCZ4_INTERIOR_MIN_BLOCKS_MIXED : CCZ4_INTERIOR_MIN_BLOCKS;
+  static constexpr int value = SHAPE == 1 ? base + 1 : SHAPE == 2 ? (base > 1 ? base - 1 : 1) : base;
 };
 
 // One interior point of the stage.
@@ -212,8 +224,8 @@ __device__ __forceinline__ long long next_item(const GridView &g, int lane) {
 // takes 32-point items from the device counter g.queue until none is left,
 // so no block waits for a wave to drain; nothing waits on another thread.
 // The two are separate instances: the loop costs the flat kernel registers.
-template <int MODE, class R, bool MESH, bool QUEUE>
-__global__ void __launch_bounds__(128, StageBlocks<R>::value) interior_kernel(GridView g, Phys<R> P, LevelCoef<R> LC,
+template <int MODE, class R, bool MESH, bool QUEUE, int SHAPE = 0>
+__global__ void __launch_bounds__(128, (StageBlocks<R, SHAPE>::value)) interior_kernel(GridView g, Phys<R> P, LevelCoef<R> LC,
                                                           const double *__restrict__ tile,
                                                           const double *__restrict__ mix, StageArgs a) {
 #if CCZ4_SMEM_SPILL
@@ -301,11 +313,17 @@ cudaError_t launch_mode(const GridView &g, const ccz4_params &P, const double *t
       LC.C[l] = C;
       LC.CR[l] = StencilCoef<R>{R(C.c1), R(C.c2), R(C.c3), R(C.cko)};
     }
-    if (g.queue)
+    cudaError_t e;
+    if (g.queue) {
       interior_kernel<MODE, R, MESH, true><<<(unsigned)blocks, 128, 0, s>>>(g, make_phys<R>(P), LC, tile, mix, a);
-    else
+      e = cudaGetLastError();
+    } else if (MODE >= 0 && g.stage_shape != 0) {
+      e = MESH ? launch_shaped_mesh(g, MODE, make_phys<R>(P), LC, tile, mix, a, s)
+               : launch_shaped_uniform(g, MODE, make_phys<R>(P), LC, tile, mix, a, s);
+    } else {
       interior_kernel<MODE, R, MESH, false><<<(unsigned)blocks, 128, 0, s>>>(g, make_phys<R>(P), LC, tile, mix, a);
-    cudaError_t e = cudaGetLastError();
+      e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
   }
   if (g.n_ghost > 0) {
@@ -336,6 +354,29 @@ cudaError_t launch_stage(const GridView &g, const ccz4_params &P, int stage, con
     case 3: return launch_prec<3, MESH>(g, P, tile, mix, in, ini, a, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// Flat launch of stage MODE (0..3) in launch shape SHAPE.
+template <class R, bool MESH, int SHAPE>
+cudaError_t launch_flat_shape(const GridView &g, int stage, const Phys<R> &ph, const LevelCoef<R> &LC,
+                              const double *tile, const double *mix, const StageArgs &a, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((g.n_points + 127) / 128);
+  switch (stage) {
+    case 0: interior_kernel<0, R, MESH, false, SHAPE><<<blocks, 128, 0, s>>>(g, ph, LC, tile, mix, a); break;
+    case 1: interior_kernel<1, R, MESH, false, SHAPE><<<blocks, 128, 0, s>>>(g, ph, LC, tile, mix, a); break;
+    case 2: interior_kernel<2, R, MESH, false, SHAPE><<<blocks, 128, 0, s>>>(g, ph, LC, tile, mix, a); break;
+    case 3: interior_kernel<3, R, MESH, false, SHAPE><<<blocks, 128, 0, s>>>(g, ph, LC, tile, mix, a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <class R, bool MESH>
+cudaError_t launch_shaped(const GridView &g, int stage, const Phys<R> &ph, const LevelCoef<R> &LC, const double *tile,
+                          const double *mix, const StageArgs &a, cudaStream_t s) {
+  if (g.stage_shape == 1) return launch_flat_shape<R, MESH, 1>(g, stage, ph, LC, tile, mix, a, s);
+  if (g.stage_shape == 2) return launch_flat_shape<R, MESH, 2>(g, stage, ph, LC, tile, mix, a, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace

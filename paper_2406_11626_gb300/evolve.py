@@ -57,7 +57,9 @@ def puncture_positions(cfg):
 def run(workload="gauge_wave", steps=10, every=1, precision="fp64", launch="flat", log=None, track=False):
     """Returns the reports: step 0 and every `every` steps up to `steps`,
     each {"step", "time", "L2_H", "L2_M", "max_H", "max_M", "nonfinite",
-    "wall_s"}, and with track=True "punctures" (tracker positions)."""
+    "wall_s"}, for puncture workloads the same norms over the points at
+    r >= 1 from every puncture ("..._r1"), and with track=True "punctures"
+    (tracker positions, which then also centre the r >= 1 norms)."""
     import torch
     from . import ccz4 as C
     if steps < 0 or every < 1:
@@ -72,12 +74,27 @@ def run(workload="gauge_wave", steps=10, every=1, precision="fp64", launch="flat
     if track and puncture_positions(cfg):
         tracker = C.Tracers(g, puncture_positions(cfg), velocity="shift")
 
+    centres = puncture_positions(cfg)
+    if centres:
+        # per-point monitors, for the norms away from the punctures
+        H = torch.empty(g.n_points, dtype=torch.float64, device="cuda")
+        M = torch.empty(3 * g.n_points, dtype=torch.float64, device="cuda")
+
     def report(n, wall):
-        out = g.constraints("U", raise_nonfinite=False)
+        nonlocal centres
+        if centres:
+            out = g.constraints("U", H.data_ptr(), M.data_ptr(), raise_nonfinite=False)
+        else:
+            out = g.constraints("U", raise_nonfinite=False)
         r = {"step": n, "time": n * cfg.dt, "L2_H": out[0], "L2_M": out[1], "max_H": out[2], "max_M": out[3],
              "nonfinite": out[4], "wall_s": wall}
         if tracker is not None:
             r["punctures"] = tracker.read()[0].tolist()
+            centres = r["punctures"]
+        if centres:
+            # the norms without the points within r < 1 of a puncture (at its tracked position)
+            ex = g.constraints_excluding(H.data_ptr(), M.data_ptr(), centres, 1.0)
+            r.update({"L2_H_r1": ex[0], "L2_M_r1": ex[1], "max_H_r1": ex[2], "max_M_r1": ex[3]})
         reports.append(r)
         if log:
             log(r)

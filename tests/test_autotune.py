@@ -1,5 +1,6 @@
-"""The patch-edge autotuner: candidate layouts, choice and JSON cache (host
-logic with a fake timer), and one small sweep on the GPU."""
+"""The autotuner: candidate layouts, the coordinate descent over patch edge,
+launch and launch shapes, the per-workload JSON cache (host logic with a
+fake timer), and one small sweep on the GPU."""
 import json
 
 import pytest
@@ -13,31 +14,92 @@ def test_layouts_match_the_target_size():
     assert all(p <= 18 for p, _ in A.layouts(100, candidates=(6, 19, 25)))
 
 
-def test_tune_picks_the_fastest_and_caches(tmp_path):
+def test_workload_configurations():
+    uni = A.workload_configs("puncture144")
+    assert sorted(c.p for c in uni) == [6, 9, 12, 17, 18]
+    assert all(abs(c.dx - 1.0 / 9.0) < 1e-15 for c in uni)
+    m3, = A.workload_configs("puncture3level")
+    bi, = A.workload_configs("binary")
+    assert m3.n_levels == 3 and bi.n_levels == 4 and m3.p == bi.p == 9
+    U, G = A.timing_state(bi)      # closed-form data on the binary mesh, no solve needed
+    assert U.shape[1] == bi.n_patches and G.shape[1] > 0
+    with pytest.raises(ValueError):
+        A.workload_configs("nope")
+
+
+def _fake(calls):
+    def fake(cfg, precision, steps, warmup, launch, stage_shape, fill_shape):
+        calls.append((cfg.p, launch, stage_shape, fill_shape))
+        pts = cfg.n_points
+        # a cost model with a minimum at p = 12, the queue launch 1 % faster, stage shape 2 3 % faster,
+        # fill shape 1 2 % faster (on the flat launch only for the stage shape)
+        c = 1.0 + (cfg.p - 12) ** 2 / 50.0
+        c *= 0.99 if launch == "queue" else 1.0
+        c *= 0.97 if stage_shape == 2 else 1.0
+        c *= 0.98 if fill_shape == 1 else 1.0
+        return pts * c * 1e-9, pts
+    return fake
+
+
+def test_tune_descends_each_coordinate_and_caches(tmp_path):
     calls = []
-
-    def fake(p, n_side, h, precision, steps, warmup, launch):
-        calls.append(p)
-        pts = (p * n_side) ** 3
-        # a cost model with a minimum at p = 12, the queue launch 1 % faster
-        return pts * (1.0 + (p - 12) ** 2 / 50.0) * (0.99 if launch == "queue" else 1.0) * 1e-9, pts
-
     cache = str(tmp_path / "tune.json")
-    r = A.tune(144, timer=fake, key_extra="fake-gpu", cache=cache)
-    assert r["p"] == 12 and r["n_side"] == 12 and r["launch"] == "queue"
-    assert sorted(calls) == [6, 6, 9, 9, 12, 12, 17, 17, 18, 18]
-    r2 = A.tune(144, timer=fake, key_extra="fake-gpu", cache=cache)
-    assert r2 == r and len(calls) == 10         # served from the cache
-    A.tune(144, timer=fake, key_extra="fake-gpu", cache=cache, refresh=True)
-    assert len(calls) == 20
-    A.tune(144, timer=fake, key_extra="other-gpu", cache=cache)
+    r = A.tune("puncture144", timer=_fake(calls), key_extra="fake-gpu", cache=cache)
+    # the queue launch wins the first coordinate, so the stage shape (a flat-launch knob) is not swept
+    assert (r["p"], r["launch"], r["stage_shape"], r["fill_shape"]) == (12, "queue", 0, 1)
+    assert len(calls) == 10 + 3     # 5 edges x 2 launches, then 3 more fill shapes
+    assert A.tune("puncture144", timer=_fake(calls), key_extra="fake-gpu", cache=cache) == r
+    assert len(calls) == 13         # served from the cache
+    r2 = A.tune("puncture144", timer=_fake(calls), key_extra="fake-gpu", cache=cache, launches=("flat",))
+    assert (r2["p"], r2["launch"], r2["stage_shape"], r2["fill_shape"]) == (12, "flat", 2, 1)
+    assert len(calls) == 13 + 5 + 2 + 3
+    A.tune("puncture144", timer=_fake(calls), key_extra="fake-gpu", cache=cache, refresh=True)
+    assert len(calls) == 23 + 13
     assert len(json.load(open(cache))) == 2     # one entry per key
+
+
+def test_mesh_workloads_keep_their_patch_edge(tmp_path):
+    calls = []
+    for w in ("puncture3level", "binary"):
+        r = A.tune(w, "mixed", timer=_fake(calls), key_extra="fake-gpu", cache=str(tmp_path / "t.json"),
+                   launches=("flat",))
+        assert r["p"] == 9 and r["stage_shape"] == 2 and r["fill_shape"] == 1 and r["workload"] == w
+    assert {c[0] for c in calls} == {9}
+    assert len(json.load(open(str(tmp_path / "t.json")))) == 2
 
 
 @pytest.mark.gpu
 def test_tune_on_the_gpu(tmp_path):
     import torch
     assert torch.cuda.is_available()
-    r = A.tune(36, steps=1, warmup=1, cache=str(tmp_path / "t.json"))
+    r = A.tune("puncture144", n_target=36, steps=1, warmup=1, cache=str(tmp_path / "t.json"))
     assert r["p"] in A.CANDIDATES and r["launch"] in A.LAUNCHES
+    assert r["stage_shape"] in A.STAGE_SHAPES and r["fill_shape"] in A.FILL_SHAPES
     assert all(v["point_stages_per_s"] > 0 for v in r["results"].values())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("stage_shape,fill_shape", [(1, 1), (2, 2), (0, 3)])
+def test_launch_shapes_give_identical_steps(stage_shape, fill_shape):
+    """Every launch shape computes the same step bit for bit (FP64 and
+    mixed, single level and mesh)."""
+    import numpy as np
+    from paper_2406_11626_gb300 import ccz4 as C
+    from paper_2406_11626_gb300 import inputs as I
+    for cfg in (I.single_puncture_config(p=6, n_side=3, half_width=1.5),
+                I.multilevel_puncture_config(p=6, n_side=4, half_width=2.0, boxes=[((1, 1, 1), (3, 3, 3))])):
+        U, G = I.initial_state(cfg)
+        for prec in ("fp64", "mixed"):
+            out = []
+            for shapes in ((0, 0), (stage_shape, fill_shape)):
+                g = C.Grid.from_config(cfg)
+                g.set_tuning(*shapes)
+                g.upload(U, G)
+                g.upload(U, G, buf="INI")
+                g.step_graph(C.make_params(**cfg.params, precision=prec), cfg.dt, 2)
+                out.append(g.download("U"))
+                g.close()
+            assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    g = C.Grid.from_config(I.single_puncture_config(p=6, n_side=2, half_width=1.0))
+    with pytest.raises(C.CCZ4Error):
+        g.set_tuning(3, 0)
