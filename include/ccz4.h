@@ -482,11 +482,15 @@ ccz4_status ccz4_tracers_free(ccz4_tracers *t);
    kernel asks the default number of resident 128-thread blocks per SM
    (CCZ4_STAGE_SHAPE_DEFAULT: 4 in FP64, 3 in the mixed precision), one
    more (MORE_BLOCKS, fewer registers per thread) or one fewer
-   (FEWER_BLOCKS, more registers); the halo fill runs 256 threads per
+   (FEWER_BLOCKS, more registers), or, for the mixed precision (FP64 keeps
+   its default), two phases in one launch (SPLIT: every thread first takes
+   all the stencil values of its point into its own shared-memory slots,
+   then evaluates the algebra and the update from them); the halo fill runs 256 threads per
    patch with 8 independent loads per thread in its gather (DEFAULT), 512
    threads (WIDE), 16 loads (DEEP) or 128 threads (NARROW). Drops a
    captured step graph. CCZ4_ERR_INVALID for an unknown shape. */
-enum { CCZ4_STAGE_SHAPE_DEFAULT = 0, CCZ4_STAGE_SHAPE_MORE_BLOCKS = 1, CCZ4_STAGE_SHAPE_FEWER_BLOCKS = 2 };
+enum { CCZ4_STAGE_SHAPE_DEFAULT = 0, CCZ4_STAGE_SHAPE_MORE_BLOCKS = 1, CCZ4_STAGE_SHAPE_FEWER_BLOCKS = 2,
+       CCZ4_STAGE_SHAPE_SPLIT = 3 };
 enum { CCZ4_FILL_SHAPE_DEFAULT = 0, CCZ4_FILL_SHAPE_WIDE = 1, CCZ4_FILL_SHAPE_DEEP = 2, CCZ4_FILL_SHAPE_NARROW = 3 };
 ccz4_status ccz4_set_tuning(ccz4_grid *g, int stage_shape, int fill_shape);
 

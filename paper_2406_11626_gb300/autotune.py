@@ -9,7 +9,9 @@ The cost of a step depends on
   persistent launch whose warps take 32-point items from a device queue;
 - the stage kernel's launch shape: the default number of resident
   128-thread blocks per SM, one more (fewer registers per thread, more
-  warps to hide latency, more register spills) or one fewer;
+  warps to hide latency, more register spills), one fewer, or (mixed
+  precision) two phases in one launch, the stencil values of each point
+  parked in shared memory before the algebra runs on them;
 - the halo fill's launch shape: threads per patch block and the number of
   independent loads per thread in its gather.
 The tuner times one RK4 step (replays of the step captured as a CUDA graph,
@@ -38,7 +40,7 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ccz4_gb300", "a
 # the patch edges of the paper's patch-size study, plus the largest edge the fill kernel takes
 CANDIDATES = (6, 9, 12, 17, 18)
 LAUNCHES = ("flat", "queue")
-STAGE_SHAPES = (0, 1, 2)      # default, one resident block more, one fewer
+STAGE_SHAPES = (0, 1, 2, 3)   # default, one resident block more, one fewer, two phases (mixed)
 FILL_SHAPES = (0, 1, 2, 3)    # 256 threads x 8 loads, 512 x 8, 256 x 16, 128 x 8
 WORKLOADS = ("puncture144", "puncture3level", "binary")
 

@@ -278,7 +278,7 @@ class Grid:
 
     def set_tuning(self, stage_shape=0, fill_shape=0):
         """Launch shapes of the flat stage kernel (0 default, 1 one resident
-        block more, 2 one fewer) and of the halo fill (0 default, 1 512
+        block more, 2 one fewer, 3 two phases (mixed precision)) and of the halo fill (0 default, 1 512
         threads, 2 16 loads per thread, 3 128 threads); results are identical."""
         _check(lib().ccz4_set_tuning(self._h, int(stage_shape), int(fill_shape)))
 

@@ -551,8 +551,10 @@ __host__ __device__ __forceinline__ T sym_inverse(const T g[6], T ig[6]) {
 // known, in the order g~, A~, alpha, phi, K, Theta, Gamma-hat, beta, b; the
 // work is ordered so that every derivative is taken right before its first
 // use, which keeps the number of live values (and so register spills) low.
-template <class D, class R, class Sink>
-__host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, const Nbhd &N, const StencilCoef<D> &C,
+// NB: the neighbourhood (Nbhd), or a type that supplies the same stencil
+// values another way (the two-phase stage kernel's DerivTap).
+template <class D, class R, class Sink, class NB>
+__host__ __device__ __forceinline__ void ccz4_rhs_point(const Phys<R> &P, NB &N, const StencilCoef<D> &C,
                                                         const StencilCoef<R> &CR, Sink &sink) {
   constexpr bool SAME = std::is_same<D, R>::value;
   // ---- conformal metric, its inverse and its first derivatives ----------------

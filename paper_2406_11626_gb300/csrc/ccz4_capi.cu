@@ -24,6 +24,9 @@ void set_error(const char *fmt, ...) {
 }
 
 int constraint_blocks(long long n_points);
+// shared-memory limits of the two-phase stage kernels (rhs_shapes.cu, rhs_mesh_shapes.cu)
+cudaError_t prepare_shaped_uniform();
+cudaError_t prepare_shaped_mesh();
 // constraint norms over the leaf points outside n_centres balls (constraints.cu)
 cudaError_t launch_constraints_excluded(const GridView &g, const double *H, const double *M, int n_centres,
                                         const double *centres, double radius, double *partial, int blocks,
@@ -306,6 +309,8 @@ static ccz4_status create_grid(const ccz4_grid_desc *d, const std::vector<int> &
     }
   }
   prepare_fill_halos(v.p);
+  if (mesh) prepare_shaped_mesh();
+  else prepare_shaped_uniform();
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     set_error("grid set-up failed: %s", cudaGetErrorString(e));
@@ -561,8 +566,8 @@ extern "C" ccz4_status ccz4_set_launch(ccz4_grid *g, int mode) {
 
 extern "C" ccz4_status ccz4_set_tuning(ccz4_grid *g, int stage_shape, int fill_shape) {
   if (check_grid(g)) return CCZ4_ERR_INVALID;
-  if (stage_shape < 0 || stage_shape > 2 || fill_shape < 0 || fill_shape > 3) {
-    set_error("set_tuning: stage shape must be 0..2 and fill shape 0..3 (got %d, %d)", stage_shape, fill_shape);
+  if (stage_shape < 0 || stage_shape > 3 || fill_shape < 0 || fill_shape > 3) {
+    set_error("set_tuning: stage shape must be 0..3 and fill shape 0..3 (got %d, %d)", stage_shape, fill_shape);
     return CCZ4_ERR_INVALID;
   }
   if ((stage_shape != g->v.stage_shape || fill_shape != g->v.fill_shape) && g->step_exec) {

@@ -15,4 +15,6 @@ cudaError_t launch_shaped_mesh(const GridView &g, int stage, const Phys<float> &
   return launch_shaped<float, true>(g, stage, ph, LC, tile, mix, a, s);
 }
 
+cudaError_t prepare_shaped_mesh() { return prepare_split<true>(); }
+
 }  // namespace ccz4

@@ -15,4 +15,6 @@ cudaError_t launch_shaped_uniform(const GridView &g, int stage, const Phys<float
   return launch_shaped<float, false>(g, stage, ph, LC, tile, mix, a, s);
 }
 
+cudaError_t prepare_shaped_uniform() { return prepare_split<false>(); }
+
 }  // namespace ccz4

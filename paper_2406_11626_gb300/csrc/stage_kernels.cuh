@@ -17,6 +17,7 @@
 #pragma once
 
 #include "ccz4_algebra.cuh"
+#include "deriv_tap.cuh"
 
 // Minimum resident blocks of 128 threads per SM requested for the stage
 // kernel. 4 caps ptxas at 128 registers per thread (16 warps per SM): the
@@ -96,6 +97,11 @@ cudaError_t launch_shaped_mesh(const GridView &g, int stage, const Phys<double> 
                                const double *tile, const double *mix, const StageArgs &a, cudaStream_t s);
 cudaError_t launch_shaped_mesh(const GridView &g, int stage, const Phys<float> &ph, const LevelCoef<float> &LC,
                                const double *tile, const double *mix, const StageArgs &a, cudaStream_t s);
+
+// Raise the shared-memory limits of the two-phase kernels (rhs_shapes.cu,
+// rhs_mesh_shapes.cu); once per grid, outside any stream capture.
+cudaError_t prepare_shaped_uniform();
+cudaError_t prepare_shaped_mesh();
 
 // Launches stage `stage` (-1: plain RHS) with the kernels of a single level
 // (rhs.cu) or of a refined mesh (rhs_mesh.cu).
@@ -179,6 +185,25 @@ struct StageBlocks {
   static constexpr int value = SHAPE == 1 ? base + 1 : SHAPE == 2 ? (base > 1 ? base - 1 : 1) : base;
 };
 
+// Neighbourhood of interior point i of patch n in the tile and mixed-derivative buffers.
+__device__ __forceinline__ Nbhd point_nbhd(const GridView &g, const double *tile, const double *mix, long long i, int n) {
+  const int p = g.p, T = g.T;
+  const int p3 = p * p * p;
+  const int r = (int)(i - n * p3);
+  const int z = r / (p * p), y = (r / p) % p, x = r % p;
+  Nbhd N;
+  N.c = tile + n * g.T3 + ((long long)(z + HALO) * T + (y + HALO)) * T + (x + HALO);
+  N.fs = (long long)g.n_patches * g.T3;
+  N.st[0] = 1;
+  N.st[1] = T;
+  N.st[2] = T * T;
+  N.mix = mix + i;
+  N.ms = g.n_points;
+  N.mixf = reinterpret_cast<const float *>(mix) + i;
+  N.msf = g.n_points;
+  return N;
+}
+
 // One interior point of the stage.
 template <int MODE, class R, bool MESH>
 __device__ __forceinline__ void stage_point(const GridView &g, const Phys<R> &P, const LevelCoef<R> &LC,
@@ -210,6 +235,45 @@ __device__ __forceinline__ void stage_point(const GridView &g, const Phys<R> &P,
   ccz4_rhs_point<double, R>(P, N, C, CR, sink);
   sink.finish();
 }
+
+// The two-phase launch shape of the mixed-precision stage kernel
+// (CCZ4_STAGE_SHAPE_SPLIT): each thread first takes all the stencil values
+// of its point and parks them in its shared-memory slots (DerivTap,
+// recording with a sink that discards the right-hand side, so the algebra
+// is dead code), then, after a barrier, evaluates the right-hand side and
+// the stage update reading them back. The first phase holds few values
+// live and keeps many tile loads in flight; the second has none in flight.
+// 2 resident blocks of 128 threads: 255 registers and 76 KB of slots each.
+template <int MODE, bool MESH>
+__global__ void __launch_bounds__(128, 2) split_kernel(GridView g, Phys<float> P, LevelCoef<float> LC,
+                                                       const double *__restrict__ tile, const double *__restrict__ mix,
+                                                       StageArgs a) {
+  extern __shared__ double tap_slots[];
+  double *sd = tap_slots + threadIdx.x;
+  float *sf = reinterpret_cast<float *>(tap_slots + TAP_DOUBLES * blockDim.x) + threadIdx.x;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = i < g.n_points;
+  const int n = active ? (int)i / (g.p * g.p * g.p) : 0;
+  const int lev = MESH ? patch_level(g, n) : 0;
+  const StencilCoef<double> C = MESH ? LC.C[lev] : LC.C[0];
+  const StencilCoef<float> CR = MESH ? LC.CR[lev] : LC.CR[0];
+  if (active) {
+    const Nbhd N = point_nbhd(g, tile, mix, i, n);
+    DerivTap<TAP_RECORD> T(N, sf, sd, blockDim.x);
+    NullSink none;
+    ccz4_rhs_point<double, float>(P, T, C, CR, none);
+  }
+  __syncthreads();
+  if (active) {
+    const Nbhd N = point_nbhd(g, tile, mix, i, n);
+    DerivTap<TAP_REPLAY> T(N, sf, sd, blockDim.x);
+    StageSink<MODE> sink{g, i, a};
+    ccz4_rhs_point<double, float>(P, T, C, CR, sink);
+    sink.finish();
+  }
+}
+
+constexpr size_t SPLIT_SMEM = (sizeof(double) * TAP_DOUBLES + sizeof(float) * TAP_FLOATS) * 128;
 
 // Next 32-point work item of a warp from the device queue (g.queue).
 __device__ __forceinline__ long long next_item(const GridView &g, int lane) {
@@ -371,11 +435,43 @@ cudaError_t launch_flat_shape(const GridView &g, int stage, const Phys<R> &ph, c
   return cudaGetLastError();
 }
 
+template <bool MESH>
+cudaError_t launch_split(const GridView &g, int stage, const Phys<float> &ph, const LevelCoef<float> &LC,
+                         const double *tile, const double *mix, const StageArgs &a, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((g.n_points + 127) / 128);
+  switch (stage) {
+    case 0: split_kernel<0, MESH><<<blocks, 128, SPLIT_SMEM, s>>>(g, ph, LC, tile, mix, a); break;
+    case 1: split_kernel<1, MESH><<<blocks, 128, SPLIT_SMEM, s>>>(g, ph, LC, tile, mix, a); break;
+    case 2: split_kernel<2, MESH><<<blocks, 128, SPLIT_SMEM, s>>>(g, ph, LC, tile, mix, a); break;
+    case 3: split_kernel<3, MESH><<<blocks, 128, SPLIT_SMEM, s>>>(g, ph, LC, tile, mix, a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// Raises the shared-memory limit of the two-phase kernels (once per grid,
+// outside any stream capture).
+template <bool MESH>
+cudaError_t prepare_split() {
+  const void *k[4] = {(const void *)split_kernel<0, MESH>, (const void *)split_kernel<1, MESH>,
+                      (const void *)split_kernel<2, MESH>, (const void *)split_kernel<3, MESH>};
+  for (const void *f : k) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPLIT_SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 template <class R, bool MESH>
 cudaError_t launch_shaped(const GridView &g, int stage, const Phys<R> &ph, const LevelCoef<R> &LC, const double *tile,
                           const double *mix, const StageArgs &a, cudaStream_t s) {
   if (g.stage_shape == 1) return launch_flat_shape<R, MESH, 1>(g, stage, ph, LC, tile, mix, a, s);
   if (g.stage_shape == 2) return launch_flat_shape<R, MESH, 2>(g, stage, ph, LC, tile, mix, a, s);
+  if (g.stage_shape == 3) {
+    // the two-phase shape exists for the mixed path; the FP64 path keeps its default
+    if constexpr (std::is_same<R, float>::value) return launch_split<MESH>(g, stage, ph, LC, tile, mix, a, s);
+    else return launch_flat_shape<R, MESH, 0>(g, stage, ph, LC, tile, mix, a, s);
+  }
   return cudaErrorInvalidValue;
 }
 

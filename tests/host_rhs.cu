@@ -10,12 +10,16 @@
 // field but alpha and phi are turned into split FP32 pairs (hi = u rounded
 // to FP32, lo = u - hi rounded to FP32), and the mixed derivatives of g~ and
 // beta into FP32 slots, as the mixed halo fill lays them out.
+// mixed = 2: the mixed path in two phases (DerivTap: the stencil values
+// recorded into slots with the algebra discarded, then replayed), as the
+// two-phase launch shape of the stage kernel evaluates it.
 // Output: d_t Q, [25][n_patches * p^3].
 #include <string.h>
 
 #include <vector>
 
 #include "../paper_2406_11626_gb300/csrc/ccz4_algebra.cuh"
+#include "../paper_2406_11626_gb300/csrc/deriv_tap.cuh"
 
 namespace ccz4 {
 void count_mark(const char *) {}
@@ -100,9 +104,48 @@ extern "C" void host_rhs(const double *tiles, int p, int n_patches, double dx, c
           N.mixf = mixf.data() + i;
           N.msf = np;
           auto sink = [&](int v, double k) { out[v * np + i] = k; };
-          if (mixed)
+          if (mixed == 2) {
+            float sf[TAP_FLOATS];
+            double sd[TAP_DOUBLES];
+            DerivTap<TAP_RECORD> rec(N, sf, sd, 1);
+            NullSink none;
+            ccz4_rhs_point<double, float>(make_phys<float>(*P), rec, C, CF, none);
+            DerivTap<TAP_REPLAY> rep(N, sf, sd, 1);
+            ccz4_rhs_point<double, float>(make_phys<float>(*P), rep, C, CF, sink);
+          } else if (mixed) {
             ccz4_rhs_point<double, float>(make_phys<float>(*P), N, C, CF, sink);
-          else
+          } else {
             ccz4_rhs_point<double, double>(make_phys<double>(*P), N, C, C, sink);
+          }
         }
+}
+
+// Slots the two-phase evaluation asks for at one point with parameters P:
+// *nf floats and *nd doubles (must not exceed TAP_FLOATS, TAP_DOUBLES).
+extern "C" void host_tap_slots(const ccz4_params *P, int *nf, int *nd, int *max_f, int *max_d) {
+  const int T = 7;
+  std::vector<double> tile(NV * T * T * T, 1.0);
+  std::vector<double> mix(NMIX, 0.0);
+  std::vector<float> mixf(NMIXF, 0.0f);
+  Nbhd N;
+  N.c = tile.data() + (3 * T + 3) * T + 3;
+  N.fs = T * T * T;
+  N.st[0] = 1;
+  N.st[1] = T;
+  N.st[2] = T * T;
+  N.mix = mix.data();
+  N.ms = 1;
+  N.mixf = mixf.data();
+  N.msf = 1;
+  StencilCoef<double> C{1.0, 1.0, 1.0, 0.1};
+  const StencilCoef<float> CF{1.0f, 1.0f, 1.0f, 0.1f};
+  float sf[TAP_FLOATS];
+  double sd[TAP_DOUBLES];
+  DerivTap<TAP_RECORD> rec(N, sf, sd, 1);
+  NullSink none;
+  ccz4_rhs_point<double, float>(make_phys<float>(*P), rec, C, CF, none);
+  *nf = rec.kf;
+  *nd = rec.kd;
+  *max_f = TAP_FLOATS;
+  *max_d = TAP_DOUBLES;
 }

@@ -79,10 +79,11 @@ def test_tune_on_the_gpu(tmp_path):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("stage_shape,fill_shape", [(1, 1), (2, 2), (0, 3)])
+@pytest.mark.parametrize("stage_shape,fill_shape", [(1, 1), (2, 2), (0, 3), (3, 0)])
 def test_launch_shapes_give_identical_steps(stage_shape, fill_shape):
     """Every launch shape computes the same step bit for bit (FP64 and
-    mixed, single level and mesh)."""
+    mixed, single level and mesh; the two-phase shape evaluates the same
+    expressions from parked stencil values)."""
     import numpy as np
     from paper_2406_11626_gb300 import ccz4 as C
     from paper_2406_11626_gb300 import inputs as I
@@ -102,4 +103,4 @@ def test_launch_shapes_give_identical_steps(stage_shape, fill_shape):
             assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     g = C.Grid.from_config(I.single_puncture_config(p=6, n_side=2, half_width=1.0))
     with pytest.raises(C.CCZ4Error):
-        g.set_tuning(3, 0)
+        g.set_tuning(4, 0)

@@ -95,3 +95,35 @@ def test_mixed_templates_keep_fp64_differences_on_a_large_offset(host_lib):
         b1, _ = ko_pieces(tiles, v, p)
         bar = 4.0 * 2.0 ** -24 * 144.0 * cko * b1
         assert np.abs(out[v] - ref[v]).max() <= bar, name
+
+
+@pytest.mark.parametrize("bc,base,gauge,p,npv", CASES)
+def test_two_phase_evaluation_equals_the_one_phase_one(host_lib, bc, base, gauge, p, npv):
+    """The two-phase launch shape of the mixed stage kernel (stencil values
+    recorded into per-thread slots, then the algebra replayed from them)
+    computes the same right-hand side bit for bit as the one-phase one."""
+    dx = 1.0 / (npv[0] * p) if base == "flat" else 0.45
+    origin = (-0.5 * npv[0] * p * dx, -0.5 * npv[1] * p * dx - 0.013, -0.5 * npv[2] * p * dx + 0.021)
+    ijk = I.patch_ijk(npv, 2)
+    og = O.Grid(p, npv, ijk, origin, dx, bc)
+    U, G = random_state(p, npv, origin, dx, ijk, seed=p + 1, bc=bc, base=base)
+    tiles = np.ascontiguousarray(og.fill_tiles(U, G))
+    P = C.make_params(**dict(I.PUNCTURE_PARAMS, slicing=gauge[0], shift=gauge[1]))
+    outs = []
+    for mode in (1, 2):
+        out = np.empty(og.ushape)
+        host_lib.host_rhs(tiles.ctypes.data_as(ctypes.c_void_p), ctypes.c_int(p), ctypes.c_int(og.n_patches),
+                          ctypes.c_double(dx), ctypes.byref(P), ctypes.c_int(mode), out.ctypes.data_as(ctypes.c_void_p))
+        outs.append(out)
+    assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("shift", ["zero", "gamma-driver"])
+def test_two_phase_slots_fit(host_lib, shift):
+    """The stencil values one point asks for fit the kernel's slots."""
+    nf, nd, mf, md = (ctypes.c_int() for _ in range(4))
+    P = C.make_params(**dict(I.PUNCTURE_PARAMS, shift=shift))
+    host_lib.host_tap_slots(ctypes.byref(P), ctypes.byref(nf), ctypes.byref(nd), ctypes.byref(mf), ctypes.byref(md))
+    assert 0 < nf.value <= mf.value and 0 < nd.value <= md.value, (nf.value, nd.value)
+    if shift == "gamma-driver":   # the larger case (the b equation's differences): not much room wasted
+        assert mf.value - nf.value < 8 and md.value - nd.value < 4, (nf.value, nd.value)
