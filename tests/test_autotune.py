@@ -52,9 +52,9 @@ def test_tune_descends_each_coordinate_and_caches(tmp_path):
     assert len(calls) == 13         # served from the cache
     r2 = A.tune("puncture144", timer=_fake(calls), key_extra="fake-gpu", cache=cache, launches=("flat",))
     assert (r2["p"], r2["launch"], r2["stage_shape"], r2["fill_shape"]) == (12, "flat", 2, 1)
-    assert len(calls) == 13 + 5 + 2 + 3
+    assert len(calls) == 13 + 5 + 3 + 3     # 5 edges, 3 more stage shapes, 3 more fill shapes
     A.tune("puncture144", timer=_fake(calls), key_extra="fake-gpu", cache=cache, refresh=True)
-    assert len(calls) == 23 + 13
+    assert len(calls) == 24 + 13
     assert len(json.load(open(cache))) == 2     # one entry per key
 
 
