@@ -215,14 +215,16 @@ def lr_at(k, steps, lr, lr_final=None):
 
 def train(mlp, u_store, draws, n, L, steps, batch=16384, lr=1e-3, seed=1, log_every=0, lr_final=None):
     """Adam on uniformly drawn (solution, cell) rows, learning rate from
-    lr_at; returns the loss history."""
+    lr_at; returns the loss history. The rows are drawn on the device (a
+    seeded CUDA generator), so a step makes no host-device copy."""
     import torch
-    rng = np.random.default_rng(seed)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
     p5 = torch.as_tensor(np.asarray(draws, dtype=np.float32), device="cuda").contiguous()
     n3 = n ** 3
     hist = []
     for k in range(steps):
-        idx = torch.as_tensor(rng.integers(0, len(draws) * n3, batch, dtype=np.int64), device="cuda")
+        idx = torch.randint(0, len(draws) * n3, (batch,), generator=gen, device="cuda", dtype=torch.int64)
         x, t = features_sample(n, L, p5, u_store, idx)
         loss = mlp.loss_grad(x, t)
         mlp.adam(lr_at(k, steps, lr, lr_final))

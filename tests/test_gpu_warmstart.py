@@ -127,7 +127,7 @@ def test_trained_network_saves_sweeps_on_held_out_draws():
     assert (sweeps > 0).all()
     net = W.MLP(8, 128, 4, 16384)
     net.set_params(W.init_params(seed=0))
-    W.train(net, store, draws[:24], n, L, steps=1500, batch=8192, lr=1e-3)
+    W.train(net, store, draws[:24], n, L, steps=3000, batch=8192, lr=2e-3, lr_final=1e-5)
     res = W.evaluate(net, draws[24:], n, L, tol=1e-9, check=10, omega=W.optimal_omega(n))
     assert (res[:, 0] > 0).all() and (res[:, 1] > 0).all()
     assert res[:, 1].mean() < 0.9 * res[:, 0].mean(), res
