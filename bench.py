@@ -282,7 +282,8 @@ def workload_config(g, precision="fp64", K=None, workload="puncture144"):
         cfg = I.binary_puncture_config()
         name = ("rotating binary puncture: bare masses 0.487 at x = -3, +3, momenta (0, -+0.0934, 0), no spin, "
                 "Bowen-York data (u by the plain relaxation solve, over-relaxed by 1.98, on 192^3 cells of "
-                "[-32,32]^3 to residual 1e-10); [-32,32]^3 on 4 ratio-3 levels of 9^3 patches (4096/5832/3456/6912, dx 4/9 .. 4/243); "
+                "[-32,32]^3, then on nested boxes of h = 1/8, 1/16, 1/64 around the punctures, each to residual "
+                "1e-10); [-32,32]^3 on 4 ratio-3 levels of 9^3 patches (4096/5832/3456/6912, dx 4/9 .. 4/243); "
                 "1+log, Gamma-driver f=0.75 eta=1, KO 0.1, Sommerfeld, RK4 dt=0.1 dx_finest")
     elif workload == "puncture3level":
         cfg = I.multilevel_puncture_config()
@@ -364,10 +365,10 @@ def init_state(C, I, cfg, g):
     if cfg.name == "binary_puncture":
         from paper_2406_11626_gb300 import initial_data as ID
         if "binary" not in _ID_CACHE:
-            _ID_CACHE["binary"] = ID.solve_config(cfg)
-        s, B, _ = _ID_CACHE["binary"]
-        s.assemble(B, g, "U")
-        s.assemble(B, g, "INI")
+            _ID_CACHE["binary"] = ID.solve_nested(cfg)
+        solvers, B, _ = _ID_CACHE["binary"]
+        ID.assemble_nested(solvers, B, g, "U")
+        ID.assemble_nested(solvers, B, g, "INI")
         return
     U0, G0 = I.initial_state(cfg)
     g.upload(U0, G0)

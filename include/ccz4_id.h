@@ -97,6 +97,30 @@ ccz4_status ccz4_id_solve(ccz4_idsolver *s, double tol, int max_sweeps, int chec
    extrapolates). Asynchronous. */
 ccz4_status ccz4_id_assemble(ccz4_idsolver *s, const ccz4_punctures *B, ccz4_grid *g, int buf, void *stream);
 
+/* Nested boxes (a reading: the paper solves for the conformal factor on
+   its mesh without printing how; a coarse global solve fed to levels 20x
+   finer under-resolves u near the punctures). Makes s a box inside the
+   solver `parent`: from now on the ghost cells of s hold fixed values, the
+   parent's current u interpolated (tricubic, as ccz4_id_assemble) at their
+   centres, and a fixed ghost adds nothing to the Newton derivative. The
+   values are taken now (later changes of the parent's u do not reach s).
+   init_u != 0 also sets u of s to the parent's u interpolated at its cell
+   centres (a first guess). Both solvers need their punctures set; the box
+   [-L, L]^3 of s, ghost cells included (L + h/2 <= L_parent), must lie
+   inside the parent's, else CCZ4_ERR_INVALID. parent NULL restores the 1/r
+   fall-off rule. The ghost array (6 n^2 doubles) is allocated on the first
+   call and owned by s. Asynchronous; synchronises the stream if a
+   captured solve graph must be dropped. */
+ccz4_status ccz4_id_set_parent(ccz4_idsolver *s, const ccz4_idsolver *parent, int init_u, void *stream);
+
+/* As ccz4_id_assemble, but writes only the points (interior and ghost) of
+   g whose every coordinate satisfies |x_d| < L - 3h/2, where the tricubic
+   stencil is centred; other points keep their values. Assembling the
+   outermost solver with ccz4_id_assemble and then each nested box, coarse
+   to fine, with this call gives every point its data from the finest box
+   that covers it. Asynchronous. */
+ccz4_status ccz4_id_assemble_box(ccz4_idsolver *s, const ccz4_punctures *B, ccz4_grid *g, int buf, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

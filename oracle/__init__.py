@@ -345,6 +345,15 @@ def _by_lib():
                                    _dbl_p]
         L.og_by_state.argtypes = [bp, ctypes.c_int, ctypes.c_double, _dbl_p, ctypes.c_long, _dbl_p, _dbl_p, _dbl_p,
                                   _dbl_p]
+        L.og_by_box_ghosts.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, _dbl_p, _dbl_p]
+        L.og_by_cells_from.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, _dbl_p, _dbl_p]
+        L.og_by_residual_box.restype = ctypes.c_double
+        L.og_by_residual_box.argtypes = [bp, ctypes.c_int, ctypes.c_double, _dbl_p, _dbl_p, _dbl_p]
+        L.og_by_sweeps_box.argtypes = [bp, ctypes.c_int, ctypes.c_double, _dbl_p, _dbl_p, ctypes.c_int,
+                                       ctypes.c_double]
+        L.og_by_solve_box.restype = ctypes.c_int
+        L.og_by_solve_box.argtypes = [bp, ctypes.c_int, ctypes.c_double, _dbl_p, _dbl_p, ctypes.c_double,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_double, _dbl_p]
         L._by_ready = True
     return L
 
@@ -386,6 +395,51 @@ def by_solve(B, n, L, u0=None, tol=1e-10, max_sweeps=1000000, check=10, omega=1.
     r = ctypes.c_double()
     k = _by_lib().og_by_solve(ctypes.byref(B), int(n), float(L), _d(u), float(tol), int(max_sweeps), int(check),
                               float(omega), ctypes.byref(r))
+    return u, k, r.value
+
+
+def by_box_ghosts(n, L, np_, Lp, up):
+    """Fixed ghost values (6, n, n) of a box of n^3 cells on [-L, L]^3 from
+    the parent solution up (np_^3 cells of [-Lp, Lp]^3): face 2d / 2d+1 of
+    axis d, then the two other cell indices (the lower axis fastest)."""
+    up = _f64(up, (np_, np_, np_))
+    gb = np.empty((6, n, n))
+    _by_lib().og_by_box_ghosts(int(n), float(L), int(np_), float(Lp), _d(up), _d(gb))
+    return gb
+
+
+def by_cells_from(n, L, np_, Lp, up):
+    """The parent solution interpolated at the box's cell centres (n, n, n)."""
+    up = _f64(up, (np_, np_, np_))
+    u = np.empty((n, n, n))
+    _by_lib().og_by_cells_from(int(n), float(L), int(np_), float(Lp), _d(up), _d(u))
+    return u
+
+
+def by_residual_box(B, n, L, u, gb):
+    u = _f64(u, (n, n, n))
+    gb = None if gb is None else _f64(gb, (6, n, n))
+    res = np.empty((n, n, n))
+    mx = _by_lib().og_by_residual_box(ctypes.byref(B), int(n), float(L), _d(u), _d(gb) if gb is not None else None,
+                                      _d(res))
+    return res, mx
+
+
+def by_sweeps_box(B, n, L, u, gb, n_sweeps, omega=1.0):
+    u = _f64(u, (n, n, n)).copy()
+    gb = _f64(gb, (6, n, n))
+    _by_lib().og_by_sweeps_box(ctypes.byref(B), int(n), float(L), _d(u), _d(gb), int(n_sweeps), float(omega))
+    return u
+
+
+def by_solve_box(B, n, L, gb, u0=None, tol=1e-10, max_sweeps=1000000, check=10, omega=1.0):
+    """Solves a box with fixed ghosts gb from u0 (default 0); returns (u,
+    sweeps or -1, final residual)."""
+    u = np.zeros((n, n, n)) if u0 is None else _f64(u0, (n, n, n)).copy()
+    gb = _f64(gb, (6, n, n))
+    r = ctypes.c_double()
+    k = _by_lib().og_by_solve_box(ctypes.byref(B), int(n), float(L), _d(u), _d(gb), float(tol), int(max_sweeps),
+                                  int(check), float(omega), ctypes.byref(r))
     return u, k, r.value
 
 

@@ -72,6 +72,7 @@ typedef struct {
   int n;
   double L, h;
   double *aa, *psi; /* per cell: Abar.Abar and psi_BL */
+  const double *gb; /* fixed ghost values [6][n][n] (a nested box), or NULL: the 1/r fall-off */
 } grid_t;
 
 static double coord(const grid_t *g, int i) { return -g->L + (i + 0.5) * g->h; }
@@ -80,6 +81,7 @@ static void grid_init(grid_t *g, const og_punctures *B, int n, double L) {
   g->n = n;
   g->L = L;
   g->h = 2.0 * L / n;
+  g->gb = NULL;
   long N = (long)n * n * n;
   g->aa = (double *)malloc(sizeof(double) * (size_t)N);
   g->psi = (double *)malloc(sizeof(double) * (size_t)N);
@@ -98,8 +100,23 @@ static void grid_free(grid_t *g) {
   free(g->psi);
 }
 
+/* Index into a [6][n][n] ghost array of the ghost cell (i, j, k), one cell
+   outside the grid along one axis d: face 2 d (low side) or 2 d + 1 (high
+   side), then the two other cell indices, the lower axis fastest. */
+static long ghost_index(int n, int i, int j, int k) {
+  int I[3] = {i, j, k};
+  for (int d = 0; d < 3; ++d) {
+    if (I[d] < 0 || I[d] >= n) {
+      int a = d == 0 ? 1 : 0, b = d == 2 ? 1 : 2;
+      return ((long)(2 * d + (I[d] >= n)) * n + I[b]) * n + I[a];
+    }
+  }
+  return -1;
+}
+
 /* u at cell (i, j, k), which may be one ghost cell outside along one axis:
-   the 1/r fall-off rule u_ghost = u_cell * r_cell / r_ghost. */
+   the given ghost value of a nested box, else the 1/r fall-off rule
+   u_ghost = u_cell * r_cell / r_ghost. */
 static double u_at(const grid_t *g, const double *u, int i, int j, int k) {
   int n = g->n;
   int ci = i < 0 ? 0 : (i >= n ? n - 1 : i);
@@ -107,6 +124,7 @@ static double u_at(const grid_t *g, const double *u, int i, int j, int k) {
   int ck = k < 0 ? 0 : (k >= n ? n - 1 : k);
   double v = u[((long)ck * n + cj) * n + ci];
   if (ci == i && cj == j && ck == k) return v;
+  if (g->gb) return g->gb[ghost_index(n, i, j, k)];
   double xc = coord(g, ci), yc = coord(g, cj), zc = coord(g, ck);
   double xg = coord(g, i), yg = coord(g, j), zg = coord(g, k);
   double rc = sqrt(xc * xc + yc * yc + zc * zc), rg = sqrt(xg * xg + yg * yg + zg * zg);
@@ -120,8 +138,14 @@ static double laplacian(const grid_t *g, const double *u, int i, int j, int k) {
 }
 
 double og_by_residual(const og_punctures *B, int n, double L, const double *u, double *res) {
+  return og_by_residual_box(B, n, L, u, NULL, res);
+}
+
+double og_by_residual_box(const og_punctures *B, int n, double L, const double *u, const double *gb,
+                          double *res) {
   grid_t g;
   grid_init(&g, B, n, L);
+  g.gb = gb;
   double mx = 0.0;
   for (int k = 0; k < n; ++k)
     for (int j = 0; j < n; ++j)
@@ -147,11 +171,12 @@ static void sweeps(const grid_t *g, double *u, int n_sweeps, double omega) {
             long c = ((long)k * n + j) * n + i;
             double q = g->psi[c] + u[c];
             double F = laplacian(g, u, i, j, k) + 0.125 * g->aa[c] * pow(q, -7.0);
-            /* derivative of F with respect to u at this cell (the ghosts of a
-               boundary cell depend on it too: r_cell / r_ghost each) */
+            /* derivative of F with respect to u at this cell (the fall-off
+               ghosts of a boundary cell depend on it too: r_cell / r_ghost
+               each; fixed ghosts do not) */
             double diag = -6.0;
             int idx[3] = {i, j, k};
-            for (int d = 0; d < 3; ++d) {
+            for (int d = 0; d < 3 && !g->gb; ++d) {
               for (int side = -1; side <= 1; side += 2) {
                 int o[3] = {i, j, k};
                 o[d] += side;
@@ -168,23 +193,35 @@ static void sweeps(const grid_t *g, double *u, int n_sweeps, double omega) {
 }
 
 void og_by_sweeps(const og_punctures *B, int n, double L, double *u, int n_sweeps, double omega) {
+  og_by_sweeps_box(B, n, L, u, NULL, n_sweeps, omega);
+}
+
+void og_by_sweeps_box(const og_punctures *B, int n, double L, double *u, const double *gb, int n_sweeps,
+                      double omega) {
   grid_t g;
   grid_init(&g, B, n, L);
+  g.gb = gb;
   sweeps(&g, u, n_sweeps, omega);
   grid_free(&g);
 }
 
 int og_by_solve(const og_punctures *B, int n, double L, double *u, double tol, int max_sweeps, int check,
                 double omega, double *final_res) {
+  return og_by_solve_box(B, n, L, u, NULL, tol, max_sweeps, check, omega, final_res);
+}
+
+int og_by_solve_box(const og_punctures *B, int n, double L, double *u, const double *gb, double tol,
+                    int max_sweeps, int check, double omega, double *final_res) {
   grid_t g;
   grid_init(&g, B, n, L);
+  g.gb = gb;
   if (check < 1) check = 1;
   int done = 0;
-  double r = og_by_residual(B, n, L, u, NULL);
+  double r = og_by_residual_box(B, n, L, u, gb, NULL);
   while (r >= tol && done < max_sweeps) {
     sweeps(&g, u, check, omega);
     done += check;
-    r = og_by_residual(B, n, L, u, NULL);
+    r = og_by_residual_box(B, n, L, u, gb, NULL);
   }
   grid_free(&g);
   if (final_res) *final_res = r;
@@ -261,4 +298,51 @@ void og_by_state(const og_punctures *B, int n, double L, const double *u, long m
     for (int c = 0; c < 6; ++c) Q[(long)(AXX + c) * m + q] = p6 * A[c];
   }
   free(uu);
+}
+
+void og_by_box_ghosts(int n, double L, int np, double Lp, const double *up, double *gb) {
+  double h = 2.0 * L / n;
+  long m = 6L * n * n;
+  double *x = (double *)malloc(sizeof(double) * (size_t)m);
+  double *y = (double *)malloc(sizeof(double) * (size_t)m);
+  double *z = (double *)malloc(sizeof(double) * (size_t)m);
+  for (int d = 0; d < 3; ++d)
+    for (int side = 0; side < 2; ++side)
+      for (int ib = 0; ib < n; ++ib)
+        for (int ia = 0; ia < n; ++ia) {
+          /* the ghost cell: index -1 or n along d, (ia, ib) along the two other axes */
+          int I[3];
+          int a = d == 0 ? 1 : 0, b = d == 2 ? 1 : 2;
+          I[d] = side ? n : -1;
+          I[a] = ia;
+          I[b] = ib;
+          long q = ((long)(2 * d + side) * n + ib) * n + ia;
+          x[q] = -L + (I[0] + 0.5) * h;
+          y[q] = -L + (I[1] + 0.5) * h;
+          z[q] = -L + (I[2] + 0.5) * h;
+        }
+  og_by_interp(np, Lp, up, m, x, y, z, gb);
+  free(x);
+  free(y);
+  free(z);
+}
+
+void og_by_cells_from(int n, double L, int np, double Lp, const double *up, double *u) {
+  double h = 2.0 * L / n;
+  long m = (long)n * n * n;
+  double *x = (double *)malloc(sizeof(double) * (size_t)m);
+  double *y = (double *)malloc(sizeof(double) * (size_t)m);
+  double *z = (double *)malloc(sizeof(double) * (size_t)m);
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        long c = ((long)k * n + j) * n + i;
+        x[c] = -L + (i + 0.5) * h;
+        y[c] = -L + (j + 0.5) * h;
+        z[c] = -L + (k + 0.5) * h;
+      }
+  og_by_interp(np, Lp, up, m, x, y, z, u);
+  free(x);
+  free(y);
+  free(z);
 }

@@ -70,6 +70,26 @@ void og_by_sweeps(const og_punctures *B, int n, double L, double *u, int n_sweep
 int og_by_solve(const og_punctures *B, int n, double L, double *u, double tol, int max_sweeps, int check,
                 double omega, double *final_res);
 
+/* Nested boxes (a reading; the paper prints none): a finer solve on n^3
+   cells of a box [-L, L]^3 inside a coarser (parent) solve on np^3 cells
+   of [-Lp, Lp]^3 takes fixed (Dirichlet) ghost values, the parent's u
+   interpolated (og_by_interp) at the centres of its ghost cells; a fixed
+   ghost adds nothing to the Newton derivative. Ghost arrays are
+   gb[6][n][n]: face 2 d (the ghosts at index -1 along axis d) or 2 d + 1
+   (index n), then the two other cell indices, the lower axis fastest. */
+void og_by_box_ghosts(int n, double L, int np, double Lp, const double *up, double *gb);
+/* The parent's u interpolated at the n^3 cell centres of the box (a first
+   guess). */
+void og_by_cells_from(int n, double L, int np, double Lp, const double *up, double *u);
+/* og_by_residual, og_by_sweeps and og_by_solve of a box with fixed ghosts
+   gb (NULL: the 1/r fall-off rule, as the functions above). */
+double og_by_residual_box(const og_punctures *B, int n, double L, const double *u, const double *gb,
+                          double *res);
+void og_by_sweeps_box(const og_punctures *B, int n, double L, double *u, const double *gb, int n_sweeps,
+                      double omega);
+int og_by_solve_box(const og_punctures *B, int n, double L, double *u, const double *gb, double tol,
+                    int max_sweeps, int check, double omega, double *final_res);
+
 /* Tricubic Lagrange interpolation of u (n^3 cells of [-L, L]^3) at m
    points: along each axis the four cell centres around the point (the
    stencil is shifted inwards at the faces), weights of the cubic through

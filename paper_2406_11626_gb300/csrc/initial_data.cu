@@ -9,6 +9,11 @@
 // small (96^3 cells are 7 MB per field) and stays in L2 across sweeps, so a
 // sweep costs about two kernel launches; the solve replays a CUDA graph of
 // `check` sweeps between residual checks.
+//
+// Nested boxes: a solver may take fixed ghost values from a coarser solver
+// (its parent), interpolated once at its ghost-cell centres; a chain of
+// boxes around the punctures then resolves u at the spacing of the finest
+// box, each box's boundary data coming from the box around it.
 #include <string.h>
 
 #include "../../include/ccz4_id.h"
@@ -28,6 +33,7 @@ struct ccz4_idsolver {
   int exec_check;
   double omega;         // relaxation factor
   double *gwt;          // [n_shell][6] 1/r ghost weights of the boundary-shell cells
+  double *gb;           // [6][n][n] fixed ghost values of a nested box, or NULL: the 1/r fall-off
 };
 
 namespace {
@@ -43,6 +49,14 @@ struct PunctureSet {
 };
 
 __device__ __forceinline__ double cell_coord(double L, double h, int i) { return -L + (i + 0.5) * h; }
+
+// Index into the [6][n][n] fixed ghost values of the ghost at index o
+// (-1 or n) along axis d of cell I: face 2 d (low side) or 2 d + 1, then the
+// two other cell indices, the lower axis fastest.
+__device__ __forceinline__ long long ghost_slot(int n, const int I[3], int d, int o) {
+  const int a = d == 0 ? 1 : 0, b = d == 2 ? 1 : 2;
+  return ((long long)(2 * d + (o >= n)) * n + I[b]) * n + I[a];
+}
 
 // 1/d for positive or negative normal d of moderate size: an FP32
 // reciprocal (conversions by integer bit operations) refined by two
@@ -97,12 +111,12 @@ __device__ __forceinline__ double ghost_weight(double L, double h, const double 
 }
 
 // Laplacian neighbour sum of a cell on the boundary of the grid, where
-// one or more neighbours are 1/r ghosts; adds the ghosts' weights
-// r_cell / r_ghost to *ghost_w. Kept out of line so that the interior cells
+// one or more neighbours are ghosts: fixed values (gb), else 1/r ghosts
+// whose weights r_cell / r_ghost go to *ghost_w. Kept out of line so that the interior cells
 // (94 % of a 96^3 grid) do not pay for its coordinates, roots and
 // divisions.
-__device__ __noinline__ double boundary_sum(int n, double L, double h, const double *u, int i, int j, int k,
-                                            double uc, double *ghost_w) {
+__device__ __noinline__ double boundary_sum(int n, double L, double h, const double *u, const double *gb, int i,
+                                            int j, int k, double uc, double *ghost_w) {
   const long long c = ((long long)k * n + j) * n + i;
   const int I[3] = {i, j, k};
   const long long st[3] = {1, n, (long long)n * n};
@@ -114,6 +128,8 @@ __device__ __noinline__ double boundary_sum(int n, double L, double h, const dou
       const int o = I[d] + side;
       if (o >= 0 && o < n) {
         s += u[c + side * st[d]];
+      } else if (gb) {
+        s += gb[ghost_slot(n, I, d, o)];
       } else {
         const double w = ghost_weight(L, h, X, rc, d, o);
         s += uc * w;
@@ -126,15 +142,15 @@ __device__ __noinline__ double boundary_sum(int n, double L, double h, const dou
 
 // Laplacian neighbour sum of cell (i, j, k) with the 1/r ghosts; returns
 // the sum and sets *ghost_w to the ghosts' weights (0 inside).
-__device__ __forceinline__ double neighbour_sum(int n, double L, double h, const double *u, int i, int j, int k,
-                                                double uc, double *ghost_w) {
+__device__ __forceinline__ double neighbour_sum(int n, double L, double h, const double *u, const double *gb, int i,
+                                                int j, int k, double uc, double *ghost_w) {
   if (i > 0 && i < n - 1 && j > 0 && j < n - 1 && k > 0 && k < n - 1) {
     const long long c = ((long long)k * n + j) * n + i;
     const long long nn = (long long)n * n;
     *ghost_w = 0.0;
     return ((u[c - 1] + u[c + 1]) + (u[c - n] + u[c + n])) + (u[c - nn] + u[c + nn]);
   }
-  return boundary_sum(n, L, h, u, i, j, k, uc, ghost_w);
+  return boundary_sum(n, L, h, u, gb, i, j, k, uc, ghost_w);
 }
 
 // Threads of one half-sweep: the interior cells of the colour first, then
@@ -199,7 +215,8 @@ __global__ void __launch_bounds__(ID_THREADS) ghost_table_kernel(int n, double L
 __global__ void __launch_bounds__(ID_THREADS) sweep_kernel(int n, double ih2, int color, double omega,
                                                             const double *__restrict__ aa,
                                                             const double *__restrict__ psi,
-                                                            const double *__restrict__ gwt, double *u) {
+                                                            const double *__restrict__ gwt,
+                                                            const double *__restrict__ gb, double *u) {
   // 32-bit index arithmetic (n <= 1024)
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int n_int = sweep_interior_threads(n);
@@ -238,6 +255,8 @@ __global__ void __launch_bounds__(ID_THREADS) sweep_kernel(int n, double ih2, in
         const int o = I[d] + (side ? 1 : -1);
         if (o >= 0 && o < n) {
           s += u[c + (side ? st[d] : -st[d])];
+        } else if (gb) {  // a nested box: a fixed ghost, no derivative
+          s += __ldg(gb + ghost_slot(n, I, d, o));
         } else {
           const double w = __ldg(gwt + 6 * b + 2 * d + side);
           s += uc * w;
@@ -256,7 +275,8 @@ __global__ void __launch_bounds__(ID_THREADS) sweep_kernel(int n, double ih2, in
 __global__ void __launch_bounds__(ID_THREADS) residual_kernel(int n, double L, double h, double ih2,
                                                                const double *__restrict__ aa,
                                                                const double *__restrict__ psi,
-                                                               const double *__restrict__ u, double *res,
+                                                               const double *__restrict__ u,
+                                                               const double *__restrict__ gb, double *res,
                                                                double *partial) {
   __shared__ double sh[ID_THREADS];
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -265,7 +285,7 @@ __global__ void __launch_bounds__(ID_THREADS) residual_kernel(int n, double L, d
     const int i = c % n, j = (c / n) % n, k = c / (n * n);
     const double uc = u[c];
     double gw;
-    const double s = neighbour_sum(n, L, h, u, i, j, k, uc, &gw);
+    const double s = neighbour_sum(n, L, h, u, gb, i, j, k, uc, &gw);
     const double iq = recip(psi[c] + uc);
     const double iq2 = iq * iq, iq4 = iq2 * iq2;
     const double F = (s - 6.0 * uc) * ih2 + 0.125 * aa[c] * (iq4 * iq2 * iq);
@@ -312,26 +332,8 @@ __device__ __forceinline__ void cubic_stencil(int n, double L, double h, double 
   *t = s - k;
 }
 
-// State of the data at one point (see ccz4_id_assemble).
-__global__ void __launch_bounds__(ID_THREADS) assemble_kernel(ccz4::GridView g, int n, double L, double h,
-                                                               PunctureSet B, const double *__restrict__ u,
-                                                               double *state) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= g.n_points + g.n_ghost) return;
-  double X[3];
-  if (e < g.n_points) {
-    const int p = g.p;
-    const long long p3 = (long long)p * p * p;
-    const int pn = (int)e / (int)p3;  // state indices are below 2^31
-    const int q = (int)(e - pn * p3);
-    const int loc[3] = {q % p, (q / p) % p, q / (p * p)};
-    const double dx = g.ldx[g.plev ? __ldg(g.plev + pn) : 0];
-    for (int d = 0; d < 3; ++d) X[d] = g.origin[d] + ((double)__ldg(g.ijk + 3 * pn + d) * p + loc[d] + 0.5) * dx;
-  } else {
-    const long long id = e - g.n_points;
-    for (int d = 0; d < 3; ++d) X[d] = g.origin[d] + (__ldg(g.gcoord + 3 * id + d) + 0.5) * g.dx;
-  }
-  // u by tricubic interpolation
+// u of a solver grid at X by tricubic interpolation (see ccz4_id_assemble).
+__device__ double interp_u(int n, double L, double h, const double *__restrict__ u, const double X[3]) {
   int k[3];
   double w[3][4];
   for (int d = 0; d < 3; ++d) {
@@ -349,6 +351,59 @@ __global__ void __launch_bounds__(ID_THREADS) assemble_kernel(ccz4::GridView g, 
     }
     uz += w[2][c] * uy;
   }
+  return uz;
+}
+
+// A nested box's fixed ghost values: the parent's u (np^3 cells of
+// [-Lp, Lp]^3) at the centres of the box's ghost cells, in the [6][n][n]
+// order of ghost_slot.
+__global__ void __launch_bounds__(ID_THREADS) box_ghost_kernel(int n, double L, double h, int np, double Lp,
+                                                                double hp, const double *__restrict__ up,
+                                                                double *gb) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 6 * n * n) return;
+  const int f = q / (n * n), ib = (q / n) % n, ia = q % n;
+  const int d = f / 2, a = d == 0 ? 1 : 0, b = d == 2 ? 1 : 2;
+  int I[3];
+  I[d] = (f & 1) ? n : -1;
+  I[a] = ia;
+  I[b] = ib;
+  const double X[3] = {cell_coord(L, h, I[0]), cell_coord(L, h, I[1]), cell_coord(L, h, I[2])};
+  gb[q] = interp_u(np, Lp, hp, up, X);
+}
+
+// A nested box's first guess: the parent's u at the box's cell centres.
+__global__ void __launch_bounds__(ID_THREADS) box_cells_kernel(int n, double L, double h, int np, double Lp,
+                                                                double hp, const double *__restrict__ up,
+                                                                double *u) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n * n * n) return;
+  const double X[3] = {cell_coord(L, h, c % n), cell_coord(L, h, (c / n) % n), cell_coord(L, h, c / (n * n))};
+  u[c] = interp_u(np, Lp, hp, up, X);
+}
+
+// State of the data at one point (see ccz4_id_assemble); with lim > 0 only
+// the points with every |X_d| < lim are written.
+__global__ void __launch_bounds__(ID_THREADS) assemble_kernel(ccz4::GridView g, int n, double L, double h,
+                                                               PunctureSet B, const double *__restrict__ u,
+                                                               double lim, double *state) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.n_points + g.n_ghost) return;
+  double X[3];
+  if (e < g.n_points) {
+    const int p = g.p;
+    const long long p3 = (long long)p * p * p;
+    const int pn = (int)e / (int)p3;  // state indices are below 2^31
+    const int q = (int)(e - pn * p3);
+    const int loc[3] = {q % p, (q / p) % p, q / (p * p)};
+    const double dx = g.ldx[g.plev ? __ldg(g.plev + pn) : 0];
+    for (int d = 0; d < 3; ++d) X[d] = g.origin[d] + ((double)__ldg(g.ijk + 3 * pn + d) * p + loc[d] + 0.5) * dx;
+  } else {
+    const long long id = e - g.n_points;
+    for (int d = 0; d < 3; ++d) X[d] = g.origin[d] + (__ldg(g.gcoord + 3 * id + d) + 0.5) * g.dx;
+  }
+  if (lim > 0.0 && !(fabs(X[0]) < lim && fabs(X[1]) < lim && fabs(X[2]) < lim)) return;
+  const double uz = interp_u(n, L, h, u, X);
   // curvature, Brill-Lindquist factor
   double A[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
   double sbl = 0.0;
@@ -388,7 +443,7 @@ cudaError_t launch_sweeps(const ccz4_idsolver *s, int n_sweeps, cudaStream_t st)
   const double ih2 = 1.0 / (s->h * s->h);
   for (int k = 0; k < n_sweeps; ++k)
     for (int color = 0; color < 2; ++color) {
-      sweep_kernel<<<grid, ID_THREADS, 0, st>>>(n, ih2, color, s->omega, s->aa, s->psi, s->gwt, s->u);
+      sweep_kernel<<<grid, ID_THREADS, 0, st>>>(n, ih2, color, s->omega, s->aa, s->psi, s->gwt, s->gb, s->u);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
@@ -417,6 +472,7 @@ static void id_release(ccz4_idsolver *s) {
   cudaFree(s->partial);
   cudaFree(s->dev_max);
   cudaFree(s->gwt);
+  cudaFree(s->gb);
   cudaFreeHost(s->host_max);
   free(s);
 }
@@ -528,7 +584,7 @@ extern "C" ccz4_status ccz4_id_sweeps(ccz4_idsolver *s, int n_sweeps, void *stre
 
 static ccz4_status residual(ccz4_idsolver *s, double *max_res, double *res_dev, cudaStream_t st) {
   const double ih2 = 1.0 / (s->h * s->h);
-  residual_kernel<<<s->blocks, ID_THREADS, 0, st>>>(s->n, s->L, s->h, ih2, s->aa, s->psi, s->u, res_dev,
+  residual_kernel<<<s->blocks, ID_THREADS, 0, st>>>(s->n, s->L, s->h, ih2, s->aa, s->psi, s->u, s->gb, res_dev,
                                                      s->partial);
   ID_TRY(cudaGetLastError());
   max_kernel<<<1, ID_THREADS, 0, st>>>(s->partial, s->blocks, s->dev_max);
@@ -600,11 +656,11 @@ extern "C" ccz4_status ccz4_id_solve(ccz4_idsolver *s, double tol, int max_sweep
   return CCZ4_OK;
 }
 
-extern "C" ccz4_status ccz4_id_assemble(ccz4_idsolver *s, const ccz4_punctures *B, ccz4_grid *g, int buf,
-                                        void *stream) {
+static ccz4_status assemble(ccz4_idsolver *s, const ccz4_punctures *B, ccz4_grid *g, int buf, double lim,
+                           void *stream, const char *who) {
   if (!s || !B || !g || B->n < 1 || B->n > CCZ4_ID_MAX_PUNCTURES || s->n < 4 || buf < CCZ4_BUF_U ||
       buf > CCZ4_BUF_INI || !g->buf[buf]) {
-    set_error("id_assemble: need a solver (n >= 4), 1..%d punctures, a grid and one of its state buffers",
+    set_error("%s: need a solver (n >= 4), 1..%d punctures, a grid and one of its state buffers", who,
               CCZ4_ID_MAX_PUNCTURES);
     return CCZ4_ERR_INVALID;
   }
@@ -622,7 +678,63 @@ extern "C" ccz4_status ccz4_id_assemble(ccz4_idsolver *s, const ccz4_punctures *
   const long long total = g->v.n_points + g->v.n_ghost;
   if (total == 0) return CCZ4_OK;
   assemble_kernel<<<(unsigned)((total + ID_THREADS - 1) / ID_THREADS), ID_THREADS, 0, (cudaStream_t)stream>>>(
-      g->v, s->n, s->L, s->h, P, s->u, g->buf[buf]);
+      g->v, s->n, s->L, s->h, P, s->u, lim, g->buf[buf]);
   ID_TRY(cudaGetLastError());
+  return CCZ4_OK;
+}
+
+extern "C" ccz4_status ccz4_id_assemble(ccz4_idsolver *s, const ccz4_punctures *B, ccz4_grid *g, int buf,
+                                        void *stream) {
+  return assemble(s, B, g, buf, 0.0, stream, "id_assemble");
+}
+
+extern "C" ccz4_status ccz4_id_assemble_box(ccz4_idsolver *s, const ccz4_punctures *B, ccz4_grid *g, int buf,
+                                            void *stream) {
+  if (!s) {
+    set_error("id_assemble_box: NULL solver");
+    return CCZ4_ERR_INVALID;
+  }
+  return assemble(s, B, g, buf, s->L - 1.5 * s->h, stream, "id_assemble_box");
+}
+
+extern "C" ccz4_status ccz4_id_set_parent(ccz4_idsolver *s, const ccz4_idsolver *parent, int init_u,
+                                          void *stream) {
+  if (!s || s == parent) {
+    set_error("id_set_parent: need a solver other than the parent");
+    return CCZ4_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (s->exec) {  // the captured sweeps carry the old boundary rule
+    ID_TRY(cudaStreamSynchronize(st));
+    cudaGraphExecDestroy(s->exec);
+    s->exec = nullptr;
+  }
+  const int n = s->n;
+  if (!parent) {
+    if (s->gb) {
+      ID_TRY(cudaStreamSynchronize(st));
+      cudaFree(s->gb);
+      s->gb = nullptr;
+    }
+    return CCZ4_OK;
+  }
+  if (parent->n < 4 || !(s->L + 0.5 * s->h <= parent->L)) {
+    set_error("id_set_parent: the box [-%g, %g]^3 and its ghost cells must lie inside the parent's [-%g, %g]^3 "
+              "(parent n >= 4)", s->L, s->L, parent->L, parent->L);
+    return CCZ4_ERR_INVALID;
+  }
+  if (!s->gb && cudaMalloc(&s->gb, sizeof(double) * 6 * (size_t)n * n) != cudaSuccess) {
+    s->gb = nullptr;
+    set_error("id_set_parent: device allocation failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return CCZ4_ERR_NOMEM;
+  }
+  box_ghost_kernel<<<(6 * n * n + ID_THREADS - 1) / ID_THREADS, ID_THREADS, 0, st>>>(
+      n, s->L, s->h, parent->n, parent->L, parent->h, parent->u, s->gb);
+  ID_TRY(cudaGetLastError());
+  if (init_u) {
+    box_cells_kernel<<<s->blocks, ID_THREADS, 0, st>>>(n, s->L, s->h, parent->n, parent->L, parent->h, parent->u,
+                                                        s->u);
+    ID_TRY(cudaGetLastError());
+  }
   return CCZ4_OK;
 }

@@ -32,10 +32,14 @@ def initial_state(cfg, g):
     assembled on the device from the initial-data solve."""
     if cfg.name == "binary_puncture":
         from . import initial_data as ID
-        s, B, sweeps = ID.solve_config(cfg)
-        s.assemble(B, g, "U")
-        s.assemble(B, g, "INI")
-        return {"initial_data_sweeps": sweeps}
+        t0 = time.perf_counter()
+        solvers, B, sweeps = ID.solve_nested(cfg)
+        ID.assemble_nested(solvers, B, g, "U")
+        ID.assemble_nested(solvers, B, g, "INI")
+        for s in solvers:
+            s.close()
+        return {"initial_data_sweeps": sweeps, "initial_data_boxes": [list(b) for b in cfg.extra["id_boxes"]],
+                "initial_data_seconds": time.perf_counter() - t0}
     U0, G0 = I.initial_state(cfg)
     g.upload(U0, G0)
     if g.n_ghost:
@@ -54,17 +58,22 @@ def puncture_positions(cfg):
     return []
 
 
-def run(workload="gauge_wave", steps=10, every=1, precision="fp64", launch="flat", log=None, track=False):
+def run(workload="gauge_wave", steps=10, every=1, precision="fp64", launch="flat", log=None, track=False,
+        id_boxes=None):
     """Returns the reports: step 0 and every `every` steps up to `steps`,
     each {"step", "time", "L2_H", "L2_M", "max_H", "max_M", "nonfinite",
     "wall_s"}, for puncture workloads the same norms over the points at
     r >= 1 from every puncture ("..._r1"), and with track=True "punctures"
-    (tracker positions, which then also centre the r >= 1 norms)."""
+    (tracker positions, which then also centre the r >= 1 norms). id_boxes
+    replaces the binary's nested initial-data boxes (() for the single
+    global solve)."""
     import torch
     from . import ccz4 as C
     if steps < 0 or every < 1:
         raise ValueError("steps must be >= 0 and every >= 1")
     cfg = WORKLOADS[workload]()
+    if id_boxes is not None and "id_boxes" in cfg.extra:
+        cfg.extra["id_boxes"] = tuple(id_boxes)
     g = C.Grid.from_config(cfg)
     g.set_launch(launch)
     extra = initial_state(cfg, g)
@@ -132,9 +141,11 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--launch", default="flat", choices=["flat", "queue"])
     ap.add_argument("--track", action="store_true", help="follow the punctures with puncture trackers")
+    ap.add_argument("--single-id-solve", action="store_true",
+                    help="binary: initial data from the global solve alone, without the nested boxes")
     a = ap.parse_args(argv)
     reps = run(a.workload, a.steps, a.every, a.precision, a.launch, log=lambda r: print(json.dumps(r), flush=True),
-               track=a.track)
+               track=a.track, id_boxes=() if a.single_id_solve else None)
     return 0 if reps and reps[-1]["nonfinite"] == 0 else 1
 
 

@@ -2,6 +2,7 @@
 argument marshalling only; every step runs in the CUDA kernels of the
 library (no CPU fallback)."""
 import ctypes
+import math
 
 import numpy as np
 
@@ -52,6 +53,8 @@ def _sig():
         "ccz4_id_residual": [vp, dp, dp, vp],
         "ccz4_id_solve": [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, vp],
         "ccz4_id_assemble": [vp, ctypes.POINTER(Punctures), vp, ctypes.c_int, vp],
+        "ccz4_id_assemble_box": [vp, ctypes.POINTER(Punctures), vp, ctypes.c_int, vp],
+        "ccz4_id_set_parent": [vp, vp, ctypes.c_int, vp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -131,6 +134,18 @@ class Solver:
         from .ccz4 import _buf
         _check(_sig().ccz4_id_assemble(self._h, ctypes.byref(B), grid._h, _buf(buf), _stream(stream)))
 
+    def assemble_box(self, B, grid, buf="U", stream=None):
+        """As assemble, for the points with every |x_d| < L - 3h/2 only."""
+        from .ccz4 import _buf
+        _check(_sig().ccz4_id_assemble_box(self._h, ctypes.byref(B), grid._h, _buf(buf), _stream(stream)))
+
+    def set_parent(self, parent, init_u=True, stream=None):
+        """Makes this solver a box nested in `parent` (fixed ghost values from
+        the parent's current u; with init_u also the first guess), or with
+        parent None restores the 1/r fall-off ghosts."""
+        _check(_sig().ccz4_id_set_parent(self._h, parent._h if parent is not None else None, int(bool(init_u)),
+                                         _stream(stream)))
+
 
 def solve_config(cfg, stream=None):
     """The solver of a binary-puncture config after its plain solve from
@@ -144,6 +159,46 @@ def solve_config(cfg, stream=None):
     if k < 0:
         raise RuntimeError("initial-data solve did not reach %g (residual %g)" % (e["id_tol"], r))
     return s, B, k
+
+
+def box_omega(n):
+    """Over-relaxation factor of a box with fixed ghosts: Young's optimum
+    for the 7-point Laplacian on n cells per axis with Dirichlet data,
+    2 / (1 + sin(pi / (n + 1)))."""
+    return 2.0 / (1.0 + math.sin(math.pi / (n + 1)))
+
+
+def solve_nested(cfg, stream=None, log=None):
+    """The initial-data solve of a binary-puncture config on its nested
+    boxes: the global solve (solve_config), then each box of
+    cfg.extra["id_boxes"] ((n, L) pairs, outermost first) from its parent's
+    interpolated u with fixed ghosts from it, to the same tolerance.
+    Returns (solvers, punctures, sweeps per solver)."""
+    s, B, k = solve_config(cfg, stream)
+    solvers, sweeps = [s], [k]
+    e = cfg.extra
+    for n, L in e.get("id_boxes", ()):
+        b = Solver(n, L)
+        b.set_punctures(B, stream)
+        b.set_parent(solvers[-1], init_u=True, stream=stream)
+        b.set_relaxation(box_omega(n))
+        kb, r = b.solve(tol=e["id_tol"], check=e.get("id_check", 200), stream=stream)
+        if kb < 0:
+            raise RuntimeError("initial-data box (n=%d, L=%g) did not reach %g (residual %g)"
+                               % (n, L, e["id_tol"], r))
+        if log:
+            log("initial-data box n=%d L=%g h=%.4g: %d sweeps, residual %.2e" % (n, L, 2.0 * L / n, kb, r))
+        solvers.append(b)
+        sweeps.append(kb)
+    return solvers, B, sweeps
+
+
+def assemble_nested(solvers, B, grid, buf="U", stream=None):
+    """The CCZ4 state from nested solvers: the outermost everywhere, then
+    each box, coarse to fine, where its stencil is centred."""
+    solvers[0].assemble(B, grid, buf, stream)
+    for b in solvers[1:]:
+        b.assemble_box(B, grid, buf, stream)
 
 
 def _as_tensor(a):

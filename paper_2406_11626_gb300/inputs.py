@@ -400,11 +400,20 @@ def multilevel_puncture_config(p=9, n_side=16, half_width=8.0, boxes=None, steps
 BINARY_PARAMS = dict(PUNCTURE_PARAMS, eta=1.0)
 
 
-def binary_puncture_config(p=9, steps=500, cfl=0.1, id_n=192, id_tol=1e-10, id_omega=1.98):
+BINARY_ID_BOXES = ((208, 13.0), (192, 6.0), (512, 4.0))
+
+
+def binary_puncture_config(p=9, steps=500, cfl=0.1, id_n=192, id_tol=1e-10, id_omega=1.98,
+                           id_boxes=BINARY_ID_BOXES):
     """Two punctures of bare mass 0.487 at x = -3 and +3 with momenta
     (0, -0.0934, 0) and (0, +0.0934, 0), no spin (Bowen-York data, u from the
     plain relaxation solve on id_n^3 cells of [-32, 32]^3 to a max residual
-    of id_tol, over-relaxed by id_omega); [-32, 32]^3 with four ratio-3 levels of 9^3 patches: 16^3
+    of id_tol, over-relaxed by id_omega, then on the nested boxes id_boxes,
+    (n, L) pairs outermost first, each with fixed ghosts from the box around
+    it and solved to id_tol: by default h = 1/8 on [-13, 13]^3 (level 1),
+    1/16 on [-6, 6]^3 (level 2) and 1/64 on [-4, 4]^3 (about the finest
+    level's spacing, 4/243); () keeps the single solve);
+    [-32, 32]^3 with four ratio-3 levels of 9^3 patches: 16^3
     level-0 patches (dx = 4/9), [-12, 12]^3 refined (5832 patches),
     [-5.33, 5.33] x [-2.67, 2.67]^2 refined (3456), [-3.56, 3.56] x
     [-0.89, 0.89]^2 refined (6912): 20296 patches, 14.8M points. 1+log,
@@ -417,7 +426,7 @@ def binary_puncture_config(p=9, steps=500, cfl=0.1, id_n=192, id_tol=1e-10, id_o
     return MeshConfig("binary_puncture", p, (16, 16, 16), (-32.0, -32.0, -32.0), dx, "sommerfeld",
                       dict(BINARY_PARAMS), cfl * h[-1], steps, None,
                       dict(m1=0.487, m2=0.487, d=6.0, P=0.0934, S=0.0, id_n=id_n, id_L=32.0, id_tol=id_tol,
-                           id_omega=id_omega),
+                           id_omega=id_omega, id_boxes=tuple(id_boxes)),
                       level, ijk)
 
 

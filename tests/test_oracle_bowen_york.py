@@ -170,3 +170,73 @@ def test_assembled_state_maps_the_conformal_factor():
         assert (Q[I.IDX[f]] == 1.0).all()
     for f in ("gxy", "betax", "K", "Theta", "Ghatx", "bx"):
         assert (Q[I.IDX[f]] == 0.0).all()
+
+
+def _ghost_centres(n, L):
+    """Centres (6, n, n) of the ghost cells of a box, in the ghost-array
+    order: face 2d (index -1 along axis d) / 2d+1 (index n), then the two
+    other cell indices, the lower axis fastest."""
+    h = 2.0 * L / n
+    X = np.empty((3, 6, n, n))
+    ib, ia = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    for d in range(3):
+        a, b = [e for e in range(3) if e != d]
+        for side in range(2):
+            X[d, 2 * d + side] = -L + ((n if side else -1) + 0.5) * h
+            X[a, 2 * d + side] = -L + (ia + 0.5) * h
+            X[b, 2 * d + side] = -L + (ib + 0.5) * h
+    return X
+
+
+def test_box_ghosts_take_the_parent_at_the_ghost_centres():
+    """Nested boxes: the fixed ghost values of a box are the parent's u
+    interpolated at the box's ghost-cell centres, in the documented face and
+    index order; with a parent that holds a cubic, exactly that cubic. The
+    first guess is the same interpolation at the box's cells."""
+    def f(x, y, z):
+        return 0.3 + x - 0.5 * y ** 2 + 0.2 * x * y * z + z ** 3 / 7.0 - 0.1 * x ** 2 * y
+    np_, Lp, n, L = 12, 3.0, 6, 1.2
+    up = f(*O.by_cell_coords(np_, Lp))
+    gb = O.by_box_ghosts(n, L, np_, Lp, up)
+    X = _ghost_centres(n, L)
+    np.testing.assert_allclose(gb, f(X[0], X[1], X[2]), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(O.by_cells_from(n, L, np_, Lp, up), f(*O.by_cell_coords(n, L)), rtol=1e-12,
+                               atol=1e-12)
+
+
+def test_fixed_ghosts_enter_the_discrete_operator():
+    """With no curvature source the residual is the 7-point Laplacian, exact
+    for a quadratic: a box holding q at its cells and ghosts has residual
+    Lap q = 4 at every cell, faces and corners included (the fall-off rule
+    would not give it there)."""
+    B = O.make_punctures([0.5], [(5.1, 0.3, 0.2)])     # no momentum or spin: Abar = 0
+    n, L = 6, 1.2
+
+    def q(x, y, z):
+        return x ** 2 + 2 * y ** 2 - z ** 2 + x * y - 0.3 * z + 1.0
+    u = q(*O.by_cell_coords(n, L))
+    X = _ghost_centres(n, L)
+    res, mx = O.by_residual_box(B, n, L, u, q(X[0], X[1], X[2]))
+    np.testing.assert_allclose(res, 4.0, rtol=0, atol=1e-11)
+    res0, _ = O.by_residual(B, n, L, u)
+    assert np.abs(res0 - 4.0).max() > 1.0
+
+
+def test_box_solve_reproduces_the_parent_on_coinciding_cells():
+    """A box whose cells and ghost cells are cells of the parent (the same
+    spacing) has the parent's solution restricted to it as its discrete
+    solution: solved from zero with ghosts from the parent, it returns that
+    restriction (so the ghost order, the fixed-ghost derivative and the box
+    geometry all agree)."""
+    B = O.make_punctures([0.4, 0.35], [(1.1, 0.0, 0.0), (-1.1, 0.0, 0.0)], [(0, 0.2, 0.05), (0, -0.2, 0)],
+                         [(0, 0, 0.1), (0, 0, 0)])
+    np_, Lp, n, L = 24, 6.0, 12, 3.0
+    up, k, r = O.by_solve(B, np_, Lp, tol=1e-12, check=20, omega=1.8)
+    assert k > 0
+    gb = O.by_box_ghosts(n, L, np_, Lp, up)
+    u, k2, r2 = O.by_solve_box(B, n, L, gb, tol=1e-12, check=20, omega=1.7)
+    assert k2 > 0 and r2 < 1e-12
+    np.testing.assert_allclose(u, up[6:18, 6:18, 6:18], rtol=0, atol=1e-11)
+    # starting from the parent's interpolation, it is already solved
+    u0 = O.by_cells_from(n, L, np_, Lp, up)
+    assert O.by_residual_box(B, n, L, u0, gb)[1] < 1e-11
