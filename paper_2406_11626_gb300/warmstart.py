@@ -254,8 +254,8 @@ def evaluate(mlp, draws, n, L, tol=1e-10, check=100, max_sweeps=2000000, omega=1
     return np.array(out)
 
 
-def run_experiment(n=96, L=16.0, n_train=2000, n_test=200, steps=160000, batch=65536, lr=1e-3, tol=1e-10,
-                   check=20, seed=0, omega=None, gs_draws=10, log=print, lr_final=None):
+def run_experiment(n=96, L=16.0, n_train=2000, n_test=200, steps=400000, batch=65536, lr=1e-3, tol=1e-10,
+                   check=20, seed=0, omega=None, gs_draws=10, log=print, lr_final=1e-6):
     """The whole experiment; returns a JSON-ready report."""
     import torch
     draws = sobol_draws(n_train + n_test, seed=seed)
@@ -322,11 +322,11 @@ def main(argv=None):
     ap.add_argument("--L", type=float, default=16.0)
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--test", type=int, default=200)
-    ap.add_argument("--steps", type=int, default=160000)
+    ap.add_argument("--steps", type=int, default=400000)
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--lr-final", type=float, default=None,
-                    help="end of a cosine learning-rate decay (default: constant rate)")
+    ap.add_argument("--lr-final", type=float, default=1e-6,
+                    help="end of a cosine learning-rate decay (a negative value: a constant rate)")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--omega", type=float, default=None,
                     help="relaxation factor (default: the fastest of a short scan; 1 = Gauss-Seidel)")
@@ -336,7 +336,8 @@ def main(argv=None):
     ap.add_argument("--out", default=None, help="write the report as JSON here")
     a = ap.parse_args(argv)
     rep = run_experiment(a.n, a.L, a.train, a.test, a.steps, a.batch, a.lr, a.tol, check=a.check, omega=a.omega,
-                         gs_draws=a.gs_draws, log=lambda s: print(s, flush=True), lr_final=a.lr_final)
+                         gs_draws=a.gs_draws, log=lambda s: print(s, flush=True),
+                         lr_final=a.lr_final if a.lr_final >= 0 else None)
     if a.out:
         with open(a.out, "w") as f:
             json.dump(rep, f, indent=1)
