@@ -139,8 +139,10 @@ __device__ __forceinline__ double lerp3(int r, double a, double b) {
 
 // MESH: the tile sources come from the host-built table of a refined mesh
 // (and may be interpolations); otherwise they are resolved here. F32W: FP32
-// weights for the mixed derivatives (see mixed_out).
-template <bool MESH, bool F32W, int SHAPE>
+// weights for the mixed derivatives (see mixed_out). PF > 0: the patch edge
+// is PF (the grid's p must equal it), so the index divisions of the tile
+// and of the widened regions are by compile-time constants.
+template <bool MESH, bool F32W, int SHAPE, int PF = 0>
 __global__ void __launch_bounds__(FILL_SHAPE_THREADS[SHAPE], 1024 / FILL_SHAPE_THREADS[SHAPE])
     fill_halos_kernel(GridView g, const double *__restrict__ src, double *__restrict__ tile,
                       double *__restrict__ mix, LevelScale ls) {
@@ -148,8 +150,8 @@ __global__ void __launch_bounds__(FILL_SHAPE_THREADS[SHAPE], 1024 / FILL_SHAPE_T
   constexpr int GATHER_BATCH = FILL_SHAPE_BATCH[SHAPE];
   extern __shared__ double smem[];
   const int n = blockIdx.x;
-  const int p = g.p, T = g.T;
-  const int T3 = (int)g.T3;
+  const int p = PF > 0 ? PF : g.p, T = PF > 0 ? PF + 2 * HALO : g.T;
+  const int T3 = PF > 0 ? T * T * T : (int)g.T3;
   const int pe = p + 4;             // patch edge widened by two points on each side
   const int next = pe * p * p;      // widened region of one first-derivative pass
   const bool wide = fill_wide(p);   // room for the region widened along two axes
@@ -177,10 +179,10 @@ __global__ void __launch_bounds__(FILL_SHAPE_THREADS[SHAPE], 1024 / FILL_SHAPE_T
       for (int k = 0; k < 8; ++k) c[k] = __ldg(&ep->src[k]);
       const int r = __ldg(&ep->r), t = __ldg(&ep->t);
       const int rx = r & 3, ry = (r >> 2) & 3, rz = (r >> 4) & 3;
-      double *tp = tile + (long long)n * g.T3 + t;
+      double *tp = tile + (long long)n * T3 + t;
 #pragma unroll 5
       for (int v = 0; v < NV; ++v)
-        __stcs(tp + (long long)v * g.n_patches * g.T3, tile_enc(interp_value(c, rx, ry, rz, src + v * g.S), split_field(F32W, v)));
+        __stcs(tp + (long long)v * g.n_patches * T3, tile_enc(interp_value(c, rx, ry, rz, src + v * g.S), split_field(F32W, v)));
     }
   } else {
     for (int t = threadIdx.x; t < T3; t += blockDim.x) {
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(FILL_SHAPE_THREADS[SHAPE], 1024 / FILL_SHAPE_T
   constexpr int JM = (1 << JOB_BITS) - 1;
   for (int v = 0; v < NV; ++v) {
     const double *sv = src + v * g.S;
-    double *tv = tile + ((long long)v * g.n_patches + n) * g.T3;
+    double *tv = tile + ((long long)v * g.n_patches + n) * T3;
     const int slot = mix_slot(v);
     const bool sp = split_field(F32W, v);
     if (MESH && nx > 0) {
@@ -314,10 +316,14 @@ size_t fill_smem_bytes(int p) {
 // grid, outside any stream capture).
 template <int SHAPE>
 cudaError_t prepare_shape(int bytes) {
-  const void *kernels[4] = {(const void *)fill_halos_kernel<false, false, SHAPE>,
+  const void *kernels[8] = {(const void *)fill_halos_kernel<false, false, SHAPE>,
                             (const void *)fill_halos_kernel<false, true, SHAPE>,
                             (const void *)fill_halos_kernel<true, false, SHAPE>,
-                            (const void *)fill_halos_kernel<true, true, SHAPE>};
+                            (const void *)fill_halos_kernel<true, true, SHAPE>,
+                            (const void *)fill_halos_kernel<false, false, SHAPE, 9>,
+                            (const void *)fill_halos_kernel<false, true, SHAPE, 9>,
+                            (const void *)fill_halos_kernel<true, false, SHAPE, 9>,
+                            (const void *)fill_halos_kernel<true, true, SHAPE, 9>};
   for (const void *k : kernels) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
@@ -334,18 +340,28 @@ cudaError_t prepare_fill_halos(int p) {
   return e;
 }
 
+template <int SHAPE, int PF>
+void launch_fill_edge(const GridView &g, const double *src, double *tile, double *mix, cudaStream_t s,
+                      bool fp32_weights, size_t bytes, const LevelScale &ls) {
+  const dim3 grid(g.n_patches), block(FILL_SHAPE_THREADS[SHAPE]);
+  if (g.src && fp32_weights)
+    fill_halos_kernel<true, true, SHAPE, PF><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
+  else if (g.src)
+    fill_halos_kernel<true, false, SHAPE, PF><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
+  else if (fp32_weights)
+    fill_halos_kernel<false, true, SHAPE, PF><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
+  else
+    fill_halos_kernel<false, false, SHAPE, PF><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
+}
+
+// p = 9 (the paper's patch edge) takes the fill compiled for that edge.
 template <int SHAPE>
 void launch_fill_shape(const GridView &g, const double *src, double *tile, double *mix, cudaStream_t s,
                        bool fp32_weights, size_t bytes, const LevelScale &ls) {
-  const dim3 grid(g.n_patches), block(FILL_SHAPE_THREADS[SHAPE]);
-  if (g.src && fp32_weights)
-    fill_halos_kernel<true, true, SHAPE><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
-  else if (g.src)
-    fill_halos_kernel<true, false, SHAPE><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
-  else if (fp32_weights)
-    fill_halos_kernel<false, true, SHAPE><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
+  if (g.p == 9)
+    launch_fill_edge<SHAPE, 9>(g, src, tile, mix, s, fp32_weights, bytes, ls);
   else
-    fill_halos_kernel<false, false, SHAPE><<<grid, block, bytes, s>>>(g, src, tile, mix, ls);
+    launch_fill_edge<SHAPE, 0>(g, src, tile, mix, s, fp32_weights, bytes, ls);
 }
 
 cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile, double *mix, cudaStream_t s,

@@ -204,12 +204,15 @@ __device__ __forceinline__ Nbhd point_nbhd(const GridView &g, const double *tile
   return N;
 }
 
-// One interior point of the stage.
-template <int MODE, class R, bool MESH>
+// One interior point of the stage. PF > 0: the patch edge is PF (the
+// grid's p must equal it), so the tile strides and the index divisions are
+// compile-time constants (immediate offsets in the loads, multiply-shift
+// divisions, no registers holding strides).
+template <int MODE, class R, bool MESH, int PF = 0>
 __device__ __forceinline__ void stage_point(const GridView &g, const Phys<R> &P, const LevelCoef<R> &LC,
                                             const double *__restrict__ tile, const double *__restrict__ mix,
                                             const StageArgs &a, long long i) {
-  const int p = g.p, T = g.T;
+  const int p = PF > 0 ? PF : g.p, T = PF > 0 ? PF + 2 * HALO : g.T;
   // 32-bit division (every state index is below 2^31): a 64-bit integer
   // division is a long software sequence
   const int p3 = p * p * p;
@@ -222,8 +225,9 @@ __device__ __forceinline__ void stage_point(const GridView &g, const Phys<R> &P,
   const int r = (int)(i - n * p3);
   const int z = r / (p * p), y = (r / p) % p, x = r % p;
   Nbhd N;
-  N.c = tile + n * g.T3 + ((long long)(z + HALO) * T + (y + HALO)) * T + (x + HALO);
-  N.fs = (long long)g.n_patches * g.T3;
+  const int T3 = PF > 0 ? T * T * T : g.T3;
+  N.c = tile + (long long)n * T3 + ((long long)(z + HALO) * T + (y + HALO)) * T + (x + HALO);
+  N.fs = (long long)g.n_patches * T3;
   N.st[0] = 1;
   N.st[1] = T;
   N.st[2] = T * T;
@@ -288,7 +292,7 @@ __device__ __forceinline__ long long next_item(const GridView &g, int lane) {
 // takes 32-point items from the device counter g.queue until none is left,
 // so no block waits for a wave to drain; nothing waits on another thread.
 // The two are separate instances: the loop costs the flat kernel registers.
-template <int MODE, class R, bool MESH, bool QUEUE, int SHAPE = 0>
+template <int MODE, class R, bool MESH, bool QUEUE, int SHAPE = 0, int PF = 0>
 __global__ void __launch_bounds__(128, (StageBlocks<R, SHAPE>::value)) interior_kernel(GridView g, Phys<R> P, LevelCoef<R> LC,
                                                           const double *__restrict__ tile,
                                                           const double *__restrict__ mix, StageArgs a) {
@@ -297,13 +301,13 @@ __global__ void __launch_bounds__(128, (StageBlocks<R, SHAPE>::value)) interior_
 #endif
   if (!QUEUE) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < g.n_points) stage_point<MODE, R, MESH>(g, P, LC, tile, mix, a, i);
+    if (i < g.n_points) stage_point<MODE, R, MESH, PF>(g, P, LC, tile, mix, a, i);
     return;
   }
   const int lane = threadIdx.x & 31;
   for (long long item = next_item(g, lane); item * 32 < g.n_points; item = next_item(g, lane)) {
     const long long i = item * 32 + lane;
-    if (i < g.n_points) stage_point<MODE, R, MESH>(g, P, LC, tile, mix, a, i);
+    if (i < g.n_points) stage_point<MODE, R, MESH, PF>(g, P, LC, tile, mix, a, i);
   }
 }
 
@@ -384,6 +388,10 @@ cudaError_t launch_mode(const GridView &g, const ccz4_params &P, const double *t
     } else if (MODE >= 0 && g.stage_shape != 0) {
       e = MESH ? launch_shaped_mesh(g, MODE, make_phys<R>(P), LC, tile, mix, a, s)
                : launch_shaped_uniform(g, MODE, make_phys<R>(P), LC, tile, mix, a, s);
+    } else if (g.p == 9) {  // the paper's patch edge, with its strides compiled in
+      interior_kernel<MODE, R, MESH, false, 0, 9><<<(unsigned)blocks, 128, 0, s>>>(g, make_phys<R>(P), LC, tile,
+                                                                                   mix, a);
+      e = cudaGetLastError();
     } else {
       interior_kernel<MODE, R, MESH, false><<<(unsigned)blocks, 128, 0, s>>>(g, make_phys<R>(P), LC, tile, mix, a);
       e = cudaGetLastError();

@@ -311,6 +311,34 @@ def test_queue_launch_is_bit_identical_to_flat(mesh):
         np.testing.assert_array_equal(o[1], out[0][1])
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("mesh", [False, True])
+def test_fixed_edge_stage_kernel_is_bit_identical_to_the_general_one(prec, mesh):
+    """Grids of 9^3 patches take the stage kernel compiled for that edge on
+    the flat default launch; the queue launch and the other launch shapes
+    take the general one. Both compute the same steps bit for bit."""
+    from paper_2406_11626_gb300 import ccz4 as C
+    if mesh:
+        cfg = I.multilevel_puncture_config(p=9, n_side=4, half_width=2.0, boxes=[((1, 1, 1), (3, 3, 3))])
+    else:
+        cfg = I.single_puncture_config(p=9, n_side=3, half_width=1.5)
+    U, G = I.initial_state(cfg)
+    P = C.make_params(**cfg.params, precision=prec)
+    out = []
+    for launch, shape in (("flat", 0), ("queue", 0), ("flat", 1)):
+        g = C.Grid.from_config(cfg)
+        g.set_launch(launch)
+        g.set_tuning(shape, 0)
+        g.upload(U, G)
+        g.upload(U, G, buf="INI")
+        g.step_graph(P, cfg.dt, 2)
+        out.append(g.download("U"))
+        g.close()
+    for o in out[1:]:
+        np.testing.assert_array_equal(o[0], out[0][0])
+        np.testing.assert_array_equal(o[1], out[0][1])
+
+
 def test_constraint_norms_away_from_the_punctures_match_oracle():
     """ccz4_constraints_excluding on the per-point monitors of a shuffled
     three-level mesh against og_constraints_excluding: the point counts are
