@@ -14,6 +14,8 @@ positions.
 import json
 import time
 
+import numpy as np
+
 from . import inputs as I
 
 WORKLOADS = {
@@ -47,6 +49,65 @@ def initial_state(cfg, g):
     return {}
 
 
+def interface_mask(cfg):
+    """(leaf, near) per interior point, each (n_patches, p, p, p) in the
+    state's order (z, y, x within a patch): leaf marks the points of leaf
+    patches (those the constraint norms run over); near marks the leaf
+    points whose stencil (three points along each axis) reaches a halo point
+    that the mesh interpolates from the coarser level, i.e. a neighbouring
+    patch slot of the same level inside the domain that holds no patch. On a
+    single level nothing is near."""
+    p = cfg.p
+    lev = np.asarray(getattr(cfg, "level", None) if getattr(cfg, "level", None) is not None
+                     else np.zeros(cfg.n_patches, int))
+    ijk = np.asarray(cfg.ijk()).reshape(-1, 3)
+    nl = int(lev.max()) + 1
+    slots = [set(map(tuple, ijk[lev == l])) for l in range(nl)]
+    extent = [np.asarray(cfg.np) * 3 ** l for l in range(nl)]
+    leaf = np.ones((len(lev), p, p, p), bool)
+    near = np.zeros((len(lev), p, p, p), bool)
+    loc = np.arange(p)
+    side = {-1: loc < 3, 0: np.ones(p, bool), 1: loc > p - 4}
+    for n in range(len(lev)):
+        l = int(lev[n])
+        if l + 1 < nl and tuple(3 * ijk[n]) in slots[l + 1]:
+            leaf[n] = False
+            continue
+        if l == 0:
+            continue
+        for ox in (-1, 0, 1):
+            for oy in (-1, 0, 1):
+                for oz in (-1, 0, 1):
+                    nb = ijk[n] + (ox, oy, oz)
+                    if (ox, oy, oz) == (0, 0, 0) or tuple(nb) in slots[l]:
+                        continue
+                    if (nb < 0).any() or (nb >= extent[l]).any():
+                        continue  # the domain's ghost shell, not an interpolation
+                    near[n] |= side[oz][:, None, None] & side[oy][None, :, None] & side[ox][None, None, :]
+    return leaf, near
+
+
+def interface_split(cfg, H, masks=None, centres=(), radius=1.0):
+    """The L2 norm of H (sqrt of the mean of H^2, as the monitor) over the
+    leaf points near a coarse-fine interface, over the others, and over the
+    others at distance >= radius from every centre."""
+    leaf, near = masks if masks is not None else interface_mask(cfg)
+    h = np.asarray(H).reshape(leaf.shape)
+    far = leaf & ~near
+    out = {"L2_H_cf": float(np.sqrt((h[near] ** 2).mean())) if near.any() else 0.0,
+           "L2_H_off_cf": float(np.sqrt((h[far] ** 2).mean())) if far.any() else 0.0,
+           "points_cf": int(near.sum()), "points_off_cf": int(far.sum())}
+    if centres:
+        x, y, z = I.mesh_point_coords(cfg.p, cfg.level, cfg.ijk(), cfg.origin, cfg.dx) \
+            if getattr(cfg, "level", None) is not None else I.point_coords(cfg.p, cfg.ijk(), cfg.origin, cfg.dx)
+        r = np.full(leaf.shape, np.inf)
+        for c in centres:
+            r = np.minimum(r, np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2).reshape(leaf.shape))
+        m = far & (r >= radius)
+        out["L2_H_off_cf_r1"] = float(np.sqrt((h[m] ** 2).mean())) if m.any() else 0.0
+    return out
+
+
 def puncture_positions(cfg):
     """Initial puncture positions of a workload: the binary's two punctures
     at x = -d/2 and +d/2, the single puncture at the origin."""
@@ -59,14 +120,16 @@ def puncture_positions(cfg):
 
 
 def run(workload="gauge_wave", steps=10, every=1, precision="fp64", launch="flat", log=None, track=False,
-        id_boxes=None):
+        id_boxes=None, split=False):
     """Returns the reports: step 0 and every `every` steps up to `steps`,
     each {"step", "time", "L2_H", "L2_M", "max_H", "max_M", "nonfinite",
     "wall_s"}, for puncture workloads the same norms over the points at
     r >= 1 from every puncture ("..._r1"), and with track=True "punctures"
     (tracker positions, which then also centre the r >= 1 norms). id_boxes
     replaces the binary's nested initial-data boxes (() for the single
-    global solve)."""
+    global solve). split=True adds the L2 norm of H near and away from the
+    coarse-fine interfaces (interface_split) to every report of a puncture
+    workload."""
     import torch
     from . import ccz4 as C
     if steps < 0 or every < 1:
@@ -84,6 +147,7 @@ def run(workload="gauge_wave", steps=10, every=1, precision="fp64", launch="flat
         tracker = C.Tracers(g, puncture_positions(cfg), velocity="shift")
 
     centres = puncture_positions(cfg)
+    masks = interface_mask(cfg) if split and centres else None
     if centres:
         # per-point monitors, for the norms away from the punctures
         H = torch.empty(g.n_points, dtype=torch.float64, device="cuda")
@@ -104,6 +168,8 @@ def run(workload="gauge_wave", steps=10, every=1, precision="fp64", launch="flat
             # the norms without the points within r < 1 of a puncture (at its tracked position)
             ex = g.constraints_excluding(H.data_ptr(), M.data_ptr(), centres, 1.0)
             r.update({"L2_H_r1": ex[0], "L2_M_r1": ex[1], "max_H_r1": ex[2], "max_M_r1": ex[3]})
+            if split:
+                r.update(interface_split(cfg, H.cpu().numpy(), masks, centres))
         reports.append(r)
         if log:
             log(r)
@@ -143,9 +209,11 @@ def main(argv=None):
     ap.add_argument("--track", action="store_true", help="follow the punctures with puncture trackers")
     ap.add_argument("--single-id-solve", action="store_true",
                     help="binary: initial data from the global solve alone, without the nested boxes")
+    ap.add_argument("--interface-split", action="store_true",
+                    help="puncture workloads: L2 of H near and away from the coarse-fine interfaces")
     a = ap.parse_args(argv)
     reps = run(a.workload, a.steps, a.every, a.precision, a.launch, log=lambda r: print(json.dumps(r), flush=True),
-               track=a.track, id_boxes=() if a.single_id_solve else None)
+               track=a.track, id_boxes=() if a.single_id_solve else None, split=a.interface_split)
     return 0 if reps and reps[-1]["nonfinite"] == 0 else 1
 
 

@@ -46,3 +46,33 @@ def test_puncture_tracker_follows_the_opposite_shift_on_a_mesh():
     assert [r["step"] for r in reps] == [0, 2, 4]
     assert all(len(r["punctures"]) == 1 for r in reps)
     assert max(abs(c) for c in reps[-1]["punctures"][0]) < 1e-12
+
+
+@pytest.mark.parametrize("box,want_near,n_kids", [(((1, 1, 1), (2, 2, 2)), 27 ** 3 - 21 ** 3, 27),
+                                                   (((1, 1, 1), (3, 2, 2)), 54 * 27 * 27 - 48 * 21 * 21, 54)])
+def test_interface_mask_marks_the_three_points_next_to_a_refined_block(box, want_near, n_kids):
+    """A block of refined patches (one parent's 27 children, or two
+    parents' 54) inside a 4^3 level-0 grid of 9^3 patches: the points of the
+    block within three points of its outer faces reach interpolated halo
+    points (the block's point count less its core shrunk by three on every
+    side); the refined parents are not leaves; level 0 has no interface."""
+    import numpy as np
+    from paper_2406_11626_gb300 import inputs as I
+    cfg = I.multilevel_puncture_config(p=9, n_side=4, half_width=2.0, boxes=[box])
+    leaf, near = E.interface_mask(cfg)
+    assert near.sum() == want_near
+    lev = np.asarray(cfg.level)
+    assert (lev == 1).sum() == n_kids
+    assert not near[lev == 0].any() and (~leaf).sum() == (n_kids // 27) * 729
+    assert leaf[lev == 1].all()
+    # the split of a norm: H = 1 near the interface, 0 elsewhere
+    H = near.astype(float)
+    out = E.interface_split(cfg, H, (leaf, near), centres=[(0.0, 0.0, 0.0)], radius=0.5)
+    assert out["L2_H_cf"] == 1.0 and out["L2_H_off_cf"] == 0.0 and out["L2_H_off_cf_r1"] == 0.0
+    assert out["points_cf"] + out["points_off_cf"] == leaf.sum()
+
+
+def test_a_single_level_has_no_interface():
+    from paper_2406_11626_gb300 import inputs as I
+    leaf, near = E.interface_mask(I.single_puncture_config(p=6, n_side=3, half_width=1.5))
+    assert leaf.all() and not near.any()
