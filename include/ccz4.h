@@ -266,6 +266,24 @@ ccz4_status ccz4_constraints(ccz4_grid *g, int buf, double out[5], double *dev_H
 ccz4_status ccz4_constraints_excluding(ccz4_grid *g, const double *dev_H, const double *dev_M, int n_centres,
                                        const double *centres, double radius, double out[5], void *stream);
 
+/* Where lattice points live in a state buffer: for each of n points given
+   by their global lattice indices (x, y, z) (single uniform level; point
+   (x, y, z) is the cell centre origin + (x + 1/2, y + 1/2, z + 1/2) dx),
+   index[q] receives the position of the point's value within a field of a
+   state buffer: field v of buffer b at (field_ptr of b) + v * field_stride
+   + index[q]. Points outside the domain resolve as the halo fill resolves
+   them (Sec. "Spatial Discretisation": periodic grids wrap, copy grids
+   clamp, Sommerfeld grids map the HALO = 3 layers outside the domain to
+   their ghost cells). A point that resolves to nothing (beyond a
+   Sommerfeld grid's ghost shell) gets -1; the call then fills every other
+   entry and returns CCZ4_ERR_BOUNDS, raised by the same device-side bounds
+   check that guards the halo fill, with a status word of its own (the
+   grid's own status, which ccz4_constraints reports, is not touched).
+     xyz    host [n][3] ints; index host [n]; 0 <= n <= 2^20.
+   A refined mesh or invalid arguments: CCZ4_ERR_INVALID. Allocates and
+   frees device memory for the points; synchronises the stream. */
+ccz4_status ccz4_point_index(ccz4_grid *g, int n, const int *xyz, long long *index, void *stream);
+
 /* Constraint monitors for callers that cannot allocate device memory (a
    host framework that owns all device memory and forbids other
    allocations, or a time loop that must not allocate once running). The

@@ -89,6 +89,7 @@ def lib():
         "ccz4_restrict": [vp, ctypes.c_int, vp],
         "ccz4_set_launch": [vp, ctypes.c_int],
         "ccz4_set_tuning": [vp, ctypes.c_int, ctypes.c_int],
+        "ccz4_point_index": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ll_p, vp],
         "ccz4_mesh_plan": [ctypes.POINTER(MeshDesc), ll_p, ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_int)],
     }
@@ -382,6 +383,18 @@ class Grid:
         if code == ERR_NONFINITE and not raise_nonfinite:
             return out
         _check(code)
+        return out
+
+    def point_index(self, xyz, stream=None, raise_bounds=True):
+        """Index within a field of a state buffer of each lattice point
+        (x, y, z) (ccz4_point_index): -1 for a point beyond the ghost shell,
+        which raises CCZ4Error (ERR_BOUNDS) unless raise_bounds is False."""
+        q = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+        out = np.empty(len(q), dtype=np.int64)
+        code = lib().ccz4_point_index(self._h, len(q), q.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), _stream(stream))
+        if code != ERR_BOUNDS or raise_bounds:
+            _check(code)
         return out
 
     def constraints_excluding(self, dev_H, dev_M, centres, radius=1.0, stream=None):

@@ -704,6 +704,70 @@ extern "C" ccz4_status ccz4_enforce(ccz4_grid *g, int buf, void *stream) {
   return CCZ4_OK;
 }
 
+namespace {
+// One thread per queried lattice point: its index within a field of a
+// state buffer, resolved as the halo fill resolves tile points (locate);
+// points beyond the ghost shell set the bounds bit of v.status.
+__global__ void __launch_bounds__(256) point_index_kernel(ccz4::GridView v, int n, const int *__restrict__ xyz,
+                                                          long long *__restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  out[q] = ccz4::locate(v, xyz[3 * q], xyz[3 * q + 1], xyz[3 * q + 2]);
+}
+}  // namespace
+
+extern "C" ccz4_status ccz4_point_index(ccz4_grid *g, int n, const int *xyz, long long *index, void *stream) {
+  if (check_grid(g)) return CCZ4_ERR_INVALID;
+  if (n < 0 || n > (1 << 20) || (n > 0 && (!xyz || !index))) {
+    set_error("point_index: need 0 <= n <= 2^20 points and host arrays xyz and index");
+    return CCZ4_ERR_INVALID;
+  }
+  if (g->v.n_levels > 1 || g->v.src) {
+    set_error("point_index: lattice indices address a single uniform level, not a refined mesh");
+    return CCZ4_ERR_INVALID;
+  }
+  if (n == 0) return CCZ4_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int *d_xyz = nullptr;
+  long long *d_idx = nullptr;
+  unsigned *d_st = nullptr;
+  if (cudaMalloc(&d_xyz, sizeof(int) * 3 * (size_t)n) != cudaSuccess ||
+      cudaMalloc(&d_idx, sizeof(long long) * (size_t)n) != cudaSuccess ||
+      cudaMalloc(&d_st, sizeof(unsigned)) != cudaSuccess) {
+    set_error("point_index: device allocation failed: %s", cudaGetErrorString(cudaGetLastError()));
+    cudaFree(d_xyz);
+    cudaFree(d_idx);
+    cudaFree(d_st);
+    return CCZ4_ERR_NOMEM;
+  }
+  ccz4::GridView v = g->v;
+  v.status = d_st;  // this call's own bounds status
+  unsigned status = 0;
+  cudaError_t e = cudaMemsetAsync(d_st, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_xyz, xyz, sizeof(int) * 3 * (size_t)n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    point_index_kernel<<<(n + 255) / 256, 256, 0, s>>>(v, n, d_xyz, d_idx);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(index, d_idx, sizeof(long long) * (size_t)n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_st, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_xyz);
+  cudaFree(d_idx);
+  cudaFree(d_st);
+  if (e != cudaSuccess) {
+    set_error("point_index: %s", cudaGetErrorString(e));
+    return CCZ4_ERR_CUDA;
+  }
+  if (status & STATUS_BOUNDS) {
+    long long bad = 0;
+    for (int q = 0; q < n; ++q) bad += index[q] < 0;
+    set_error("point_index: %lld of %d points lie outside the grid and its ghost shell", bad, n);
+    return CCZ4_ERR_BOUNDS;
+  }
+  return CCZ4_OK;
+}
+
 extern "C" ccz4_status ccz4_constraints(ccz4_grid *g, int buf, double out[5], double *dev_H, double *dev_M,
                                         void *stream) {
   if (check_grid(g)) return CCZ4_ERR_INVALID;
