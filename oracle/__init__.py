@@ -75,6 +75,7 @@ def lib():
         L.og_rk4_step.argtypes = [ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_double, _dbl_p, _dbl_p, _dbl_p]
         L.og_enforce.argtypes = [ctypes.c_void_p, _dbl_p]
         L.og_constraints.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, _dbl_p, _dbl_p, _dbl_p]
+        L.og_psi4.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, _dbl_p, _dbl_p]
         L.og_rhs_points.argtypes = [ctypes.c_void_p, ctypes.POINTER(Params), _dbl_p, _dbl_p,
                                     ctypes.c_long, _lng_p, _dbl_p]
         L.og_constraints_points.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p, ctypes.c_long, _lng_p, _dbl_p]
@@ -213,6 +214,16 @@ class Grid:
         out = np.empty(5)
         lib().og_constraints(self._h, _d(U), _d(G), _d(H), _d(M), _d(out))
         return H, M, out
+
+    def psi4(self, U, G=None, centre=(0.0, 0.0, 0.0)):
+        """psi_4 at every interior point, (2, n_patches, p, p, p): real and
+        imaginary parts, the tetrad centred at `centre`."""
+        U = _f64(U, self.ushape)
+        G = self._g(G)
+        c = np.ascontiguousarray(centre, dtype=np.float64).reshape(3)
+        out = np.empty((2,) + self.ushape[1:])
+        lib().og_psi4(self._h, _d(U), _d(G), _d(c), _d(out))
+        return out
 
     def constraints_excluding(self, H, M, centres, radius):
         """Norms of H and |M| over leaf points at distance >= radius from

@@ -1900,3 +1900,255 @@ int og_constraints_excluding(const og_grid *g, const double *H, const double *M,
   out[4] = count;
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* psi_4 (appendix "psi_4 in ExaGRyPE")                                       */
+/* ------------------------------------------------------------------------ */
+
+static double levi(int i, int j, int k) {
+  return (double)((i - j) * (j - k) * (k - i)) / 2.0;
+}
+
+/* psi_4 = (E_ij - i B_ij) mbar^i mbar^j (Eq. eq_NR_psi_code_implementation)
+   at one point from its state q, derivatives d1, d2 and position X relative
+   to the tetrad's centre. Written from the appendix:
+   - E_ij = (R_ij - K^m_i K_jm + K_ij (K - Theta) + D_(i Z_j))^TF
+     (Eq. eq_NR_psi4_E_ij, vacuum), R_ij the physical Ricci tensor of the
+     metric, K_ij = (A~_ij + g~_ij K / 3) / phi^2 the physical extrinsic
+     curvature, Z_i = 1/2 g~_ij (Gamma-hat^j - G~^j) as in the evolution;
+   - B_ij = 1/2 (eps_mni D^m K_j^n + eps_mnj D^m K_i^n)^TF
+     (Eq. eq_NR_psi4_B_ij), eps the Levi-Civita tensor of the physical metric;
+   - TF the trace-free part with the physical metric;
+   - the tetrad: v = (-y, x, 0), u = (x, y, z), w^i = gamma^ij eps_jkl v^k u^l,
+     orthonormalised in that order by Gram-Schmidt with the physical metric;
+     mbar = (w - i v) / sqrt 2 (Eq. eq_NR_psi4_m_conj).
+   out[0] = Re psi_4, out[1] = Im psi_4. */
+static void point_psi4(const double q[OG_NV], const double d1[OG_NV][3], const double d2[OG_NV][3][3],
+                       const double X[3], double out[2]) {
+  geom G;
+  build_geom(q, d1, d2, &G);
+  double (*g)[3] = G.g, (*ig)[3] = G.ig;
+  const double ph = G.ph;
+  /* physical metric and inverse */
+  double gam[3][3], igam[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      gam[i][j] = g[i][j] / (ph * ph);
+      igam[i][j] = ph * ph * ig[i][j];
+    }
+  const double sdet = sqrt(G.det) / (ph * ph * ph); /* sqrt(det gamma) */
+  /* D_k^{ml} = g~^ma g~^lb D_kab (= -1/2 d_k g~^ml) */
+  double Dup[3][3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int m = 0; m < 3; ++m)
+      for (int l = 0; l < 3; ++l) {
+        double s = 0.0;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) s += ig[m][a] * ig[l][b] * G.D[k][a][b];
+        Dup[k][m][l] = s;
+      }
+  double dD[3][3][3][3]; /* d_k D_ijl */
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        for (int l = 0; l < 3; ++l) dD[k][i][j][l] = 0.5 * d2[GXX + SYM[j][l]][k][i];
+  /* physical Ricci tensor from the derivatives of the physical Christoffel
+     symbols (the same route as the constraint monitor) */
+  double dPG[3][3][3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int m = 0; m < 3; ++m)
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          double s = 0.0;
+          for (int l = 0; l < 3; ++l) {
+            s += -2.0 * Dup[k][m][l] * (G.D[i][j][l] + G.D[j][i][l] - G.D[l][i][j]);
+            s += ig[m][l] * (dD[k][i][j][l] + dD[k][j][i][l] - dD[k][l][i][j]);
+            s += 2.0 / ph * Dup[k][m][l] * (g[j][l] * G.P[i] + g[i][l] * G.P[j] - g[i][j] * G.P[l]);
+            s += -2.0 / ph * ig[m][l] * (G.D[k][j][l] * G.P[i] + G.D[k][i][l] * G.P[j] - G.D[k][i][j] * G.P[l]);
+            s += -1.0 / ph * ig[m][l] * (g[j][l] * G.ddph[k][i] + g[i][l] * G.ddph[k][j] - g[i][j] * G.ddph[k][l]);
+            s += 1.0 / (ph * ph) * ig[m][l] *
+                 (g[j][l] * G.P[i] * G.P[k] + g[i][l] * G.P[j] * G.P[k] - g[i][j] * G.P[k] * G.P[l]);
+          }
+          dPG[k][m][i][j] = s;
+        }
+  double Ric[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double r = 0.0;
+      for (int m = 0; m < 3; ++m) {
+        r += dPG[m][m][i][j] - dPG[j][m][i][m];
+        for (int l = 0; l < 3; ++l) r += G.PGam[l][i][j] * G.PGam[m][l][m] - G.PGam[l][i][m] * G.PGam[m][l][j];
+      }
+      Ric[i][j] = r;
+    }
+  /* Z_i and its covariant derivative: d_k G~^j from d_k of g~^lm G~^j_lm */
+  double dGt[3][3]; /* dGt[k][j] = d_k G~^j */
+  for (int k = 0; k < 3; ++k)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < 3; ++l)
+        for (int m = 0; m < 3; ++m) {
+          double dGjlm = 0.0; /* d_k G~^j_lm */
+          for (int n = 0; n < 3; ++n) {
+            dGjlm += -2.0 * Dup[k][j][n] * (G.D[l][m][n] + G.D[m][l][n] - G.D[n][l][m]);
+            dGjlm += ig[j][n] * (dD[k][l][m][n] + dD[k][m][l][n] - dD[k][n][l][m]);
+          }
+          s += -2.0 * Dup[k][l][m] * G.Gam[j][l][m] + ig[l][m] * dGjlm;
+        }
+      dGt[k][j] = s;
+    }
+  double Gh[3], Zc[3], dZ[3][3];
+  for (int i = 0; i < 3; ++i) Gh[i] = q[GHX + i];
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < 3; ++j) s += 0.5 * g[i][j] * (Gh[j] - G.Gc[j]);
+    Zc[i] = s;
+  }
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < 3; ++j)
+        s += 0.5 * (G.dg[k][i][j] * (Gh[j] - G.Gc[j]) + g[i][j] * (d1[GHX + j][k] - dGt[k][j]));
+      dZ[k][i] = s; /* d_k Z_i */
+    }
+  double DZ[3][3]; /* D_(i Z_j) */
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.5 * (dZ[i][j] + dZ[j][i]);
+      for (int k = 0; k < 3; ++k) s -= G.PGam[k][i][j] * Zc[k];
+      DZ[i][j] = s;
+    }
+  /* extrinsic curvature: K_ij (physical, covariant) and K^n_j (mixed) */
+  const double Kt = q[KTR], Th = q[THETA];
+  double At[3][3], Kd[3][3], Km[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) At[i][j] = q[AXX + SYM[i][j]];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Kd[i][j] = (At[i][j] + g[i][j] * Kt / 3.0) / (ph * ph);
+  for (int n = 0; n < 3; ++n)
+    for (int j = 0; j < 3; ++j) {
+      double s = (n == j) ? Kt / 3.0 : 0.0;
+      for (int k = 0; k < 3; ++k) s += ig[n][k] * At[k][j];
+      Km[n][j] = s;
+    }
+  /* E_ij before the trace-free part */
+  double E[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double kk = 0.0; /* K^m_i K_jm = K_im K^m_j */
+      for (int m = 0; m < 3; ++m) kk += Kd[i][m] * Km[m][j];
+      E[i][j] = Ric[i][j] - kk + Kd[i][j] * (Kt - Th) + DZ[i][j];
+    }
+  /* D_l K^n_j = d_l K^n_j + Gamma^n_lp K^p_j - Gamma^p_lj K^n_p */
+  double DK[3][3][3];
+  for (int l = 0; l < 3; ++l)
+    for (int n = 0; n < 3; ++n)
+      for (int j = 0; j < 3; ++j) {
+        double s = (n == j) ? d1[KTR][l] / 3.0 : 0.0;
+        for (int k = 0; k < 3; ++k) s += -2.0 * Dup[l][n][k] * At[k][j] + ig[n][k] * d1[AXX + SYM[k][j]][l];
+        for (int p = 0; p < 3; ++p) s += G.PGam[n][l][p] * Km[p][j] - G.PGam[p][l][j] * Km[n][p];
+        DK[l][n][j] = s;
+      }
+  /* D^m K^n_j = gamma^ml D_l K^n_j */
+  double DuK[3][3][3];
+  for (int m = 0; m < 3; ++m)
+    for (int n = 0; n < 3; ++n)
+      for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int l = 0; l < 3; ++l) s += igam[m][l] * DK[l][n][j];
+        DuK[m][n][j] = s;
+      }
+  double B[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int m = 0; m < 3; ++m)
+        for (int n = 0; n < 3; ++n)
+          s += sdet * (levi(m, n, i) * DuK[m][n][j] + levi(m, n, j) * DuK[m][n][i]);
+      B[i][j] = 0.5 * s;
+    }
+  /* trace-free parts with the physical metric */
+  double trE = 0.0, trB = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      trE += igam[i][j] * E[i][j];
+      trB += igam[i][j] * B[i][j];
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      E[i][j] -= gam[i][j] * trE / 3.0;
+      B[i][j] -= gam[i][j] * trB / 3.0;
+    }
+  /* the tetrad's spatial vectors */
+  double v[3] = {-X[1], X[0], 0.0}, u[3] = {X[0], X[1], X[2]}, w[3];
+#define DOTG(a, b) (gam[0][0] * a[0] * b[0] + gam[1][1] * a[1] * b[1] + gam[2][2] * a[2] * b[2] + \
+                    gam[0][1] * (a[0] * b[1] + a[1] * b[0]) + gam[0][2] * (a[0] * b[2] + a[2] * b[0]) + \
+                    gam[1][2] * (a[1] * b[2] + a[2] * b[1]))
+  double nv = sqrt(DOTG(v, v));
+  for (int i = 0; i < 3; ++i) v[i] /= nv;
+  double vu = DOTG(v, u);
+  for (int i = 0; i < 3; ++i) u[i] -= vu * v[i];
+  double nu = sqrt(DOTG(u, u));
+  for (int i = 0; i < 3; ++i) u[i] /= nu;
+  double wl[3]; /* eps_jkl v^k u^l */
+  for (int j = 0; j < 3; ++j) {
+    double s = 0.0;
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l) s += sdet * levi(j, k, l) * v[k] * u[l];
+    wl[j] = s;
+  }
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < 3; ++j) s += igam[i][j] * wl[j];
+    w[i] = s;
+  }
+  double vw = DOTG(v, w), uw = DOTG(u, w);
+  for (int i = 0; i < 3; ++i) w[i] -= vw * v[i] + uw * u[i];
+  double nw = sqrt(DOTG(w, w));
+  for (int i = 0; i < 3; ++i) w[i] /= nw;
+#undef DOTG
+  /* (E - i B)_ij mbar^i mbar^j with mbar = (w - i v) / sqrt 2 */
+  double Eww = 0.0, Evv = 0.0, Ewv = 0.0, Bww = 0.0, Bvv = 0.0, Bwv = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      Eww += E[i][j] * w[i] * w[j];
+      Evv += E[i][j] * v[i] * v[j];
+      Ewv += E[i][j] * w[i] * v[j];
+      Bww += B[i][j] * w[i] * w[j];
+      Bvv += B[i][j] * v[i] * v[j];
+      Bwv += B[i][j] * w[i] * v[j];
+    }
+  out[0] = 0.5 * (Eww - Evv) - Bwv;
+  out[1] = -Ewv - 0.5 * (Bww - Bvv);
+}
+
+int og_psi4(const og_grid *g, const double *U, const double *G, const double centre[3], double *out) {
+  int p = g->p, T = g->T;
+  long pts = n_interior(g), T3 = (long)T * T * T;
+  double *tile = (double *)malloc(sizeof(double) * (size_t)T3 * OG_NV);
+  double d1[OG_NV][3], d2[OG_NV][3][3];
+  for (int n = 0; n < g->n_patches; ++n) {
+    const double dx = g->dxl[g->lev[n]];
+    build_tile(g, n, U, G, tile);
+    for (int z = 0; z < p; ++z)
+      for (int y = 0; y < p; ++y)
+        for (int x = 0; x < p; ++x) {
+          tview tv;
+          tv.tile = tile;
+          tv.c = ((long)(z + OG_HALO) * T + (y + OG_HALO)) * T + (x + OG_HALO);
+          tv.st[0] = 1; tv.st[1] = T; tv.st[2] = (long)T * T;
+          double q[OG_NV], X[3], r[2];
+          for (int v = 0; v < OG_NV; ++v) q[v] = tq(&tv, 0, v);
+          point_derivs(&tv, dx, d1, d2);
+          const int loc[3] = {x, y, z};
+          for (int d = 0; d < 3; ++d)
+            X[d] = g->origin[d] + ((double)g->ijk[3 * n + d] * p + loc[d] + 0.5) * dx - centre[d];
+          point_psi4(q, d1, d2, X, r);
+          long li = (long)n * p * p * p + ((long)z * p + y) * p + x;
+          out[li] = r[0];
+          out[pts + li] = r[1];
+        }
+  }
+  free(tile);
+  return 0;
+}

@@ -91,6 +91,13 @@ int og_point_derivs(const og_grid *g, const double *U, const double *G, long pt,
 int og_constraints_excluding(const og_grid *g, const double *H, const double *M, int n_c, const double *centres,
                              double radius, double out[5]);
 
+/* psi_4 at every interior point (appendix "psi_4 in ExaGRyPE": Eqs.
+   eq_NR_psi4_E_ij, eq_NR_psi4_B_ij, eq_NR_psi4_m_conj,
+   eq_NR_psi_code_implementation), the tetrad built from each point's
+   position relative to centre[3]: out[0][n_points] = Re psi_4,
+   out[1][n_points] = Im psi_4. Derivatives as in og_constraints. */
+int og_psi4(const og_grid *g, const double *U, const double *G, const double centre[3], double *out);
+
 /* First-order formulation (Eq. first-order-variables): arrays of 58
    fields, the 25 primaries followed by A_k (25..27), B_k^i (28 + 3k + i),
    D_kij (37 + 6k + pair(i,j)) and P_k (55..57), in the layouts above with
