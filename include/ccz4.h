@@ -266,6 +266,28 @@ ccz4_status ccz4_constraints(ccz4_grid *g, int buf, double out[5], double *dev_H
 ccz4_status ccz4_constraints_excluding(ccz4_grid *g, const double *dev_H, const double *dev_M, int n_centres,
                                        const double *centres, double radius, double out[5], void *stream);
 
+/* psi_4 (appendix "psi_4 in ExaGRyPE"; Sec. "Gravitational waves" for
+   its use): the Newman-Penrose scalar psi_4 = (E_ij - i B_ij) mbar^i mbar^j
+   (Eq. eq_NR_psi_code_implementation) at every interior point of every
+   level, from the state in buffer in_buf, with
+     E_ij = (R_ij - K^m_i K_jm + K_ij (K - Theta) + D_(i Z_j))^TF and
+     B_ij = 1/2 (eps_mni D^m K_j^n + eps_mnj D^m K_i^n)^TF
+   (Eqs. eq_NR_psi4_E_ij, eq_NR_psi4_B_ij, vacuum), R_ij the physical Ricci
+   tensor, K_ij = (A~_ij + g~_ij K / 3) / phi^2, Z_i = 1/2 g~_ij
+   (Gamma-hat^j - G~^j), eps the Levi-Civita tensor and TF the trace-free
+   part, both of the physical metric g~_ij / phi^2; mbar = (w - i v) / sqrt 2
+   with v, u, w the Gram-Schmidt orthonormalisation (physical metric, in
+   that order) of (-y, x, 0), (x, y, z) and gamma^ij eps_jkl v^k u^l, the
+   coordinates taken relative to centre[3] (host). FD4 stencils as in the
+   stage kernel, FP64. Writes Re psi_4 into field 0 and Im psi_4 into field
+   1 of state buffer out_buf at every interior point; its other fields and
+   its ghost cells keep their values (static tracers, vel_field = -1, then
+   sample psi_4 anywhere, e.g. on an extraction sphere). Overwrites
+   CCZ4_BUF_TILE and CCZ4_BUF_MIX (the halo fill of in_buf). in_buf and
+   out_buf must be different state buffers (CCZ4_ERR_INVALID otherwise).
+   Asynchronous. */
+ccz4_status ccz4_psi4(ccz4_grid *g, int in_buf, int out_buf, const double centre[3], void *stream);
+
 /* Where lattice points live in a state buffer: for each of n points given
    by their global lattice indices (x, y, z) (single uniform level; point
    (x, y, z) is the cell centre origin + (x + 1/2, y + 1/2, z + 1/2) dx),

@@ -90,6 +90,7 @@ def lib():
         "ccz4_set_launch": [vp, ctypes.c_int],
         "ccz4_set_tuning": [vp, ctypes.c_int, ctypes.c_int],
         "ccz4_point_index": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ll_p, vp],
+        "ccz4_psi4": [vp, ctypes.c_int, ctypes.c_int, _dbl_p, vp],
         "ccz4_mesh_plan": [ctypes.POINTER(MeshDesc), ll_p, ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_int)],
     }
@@ -384,6 +385,13 @@ class Grid:
             return out
         _check(code)
         return out
+
+    def psi4(self, in_buf="U", out_buf="RHS", centre=(0.0, 0.0, 0.0), stream=None):
+        """psi_4 of the state in in_buf into fields 0 (Re) and 1 (Im) of
+        out_buf at every interior point (ccz4_psi4), the tetrad centred at
+        `centre`."""
+        c = np.ascontiguousarray(centre, dtype=np.float64).reshape(3)
+        _check(lib().ccz4_psi4(self._h, _buf(in_buf), _buf(out_buf), _d(c), _stream(stream)))
 
     def point_index(self, xyz, stream=None, raise_bounds=True):
         """Index within a field of a state buffer of each lattice point

@@ -768,6 +768,19 @@ extern "C" ccz4_status ccz4_point_index(ccz4_grid *g, int n, const int *xyz, lon
   return CCZ4_OK;
 }
 
+extern "C" ccz4_status ccz4_psi4(ccz4_grid *g, int in_buf, int out_buf, const double centre[3], void *stream) {
+  if (check_grid(g)) return CCZ4_ERR_INVALID;
+  if (!state_buffer(in_buf) || !state_buffer(out_buf) || in_buf == out_buf || !g->buf[in_buf] ||
+      !g->buf[out_buf] || !centre || !(centre[0] == centre[0] && centre[1] == centre[1] && centre[2] == centre[2])) {
+    set_error("psi4: need two different state buffers (in=%d out=%d) and a finite centre", in_buf, out_buf);
+    return CCZ4_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(launch_fill_halos(g->v, g->buf[in_buf], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], s));
+  CUDA_TRY(launch_psi4(g->v, g->buf[CCZ4_BUF_TILE], centre, g->buf[out_buf], s));
+  return CCZ4_OK;
+}
+
 extern "C" ccz4_status ccz4_constraints(ccz4_grid *g, int buf, double out[5], double *dev_H, double *dev_M,
                                         void *stream) {
   if (check_grid(g)) return CCZ4_ERR_INVALID;

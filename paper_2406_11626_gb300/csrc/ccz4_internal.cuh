@@ -219,6 +219,9 @@ cudaError_t launch_ghost_setup(const GridView &g, GhostGeo *out, cudaStream_t s)
 cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile, double *mix, cudaStream_t s,
                               bool fp32_weights = false);
 cudaError_t prepare_fill_halos(int p);
+// psi_4 at every interior point from the halo'd tiles: Re into out[0 .. n_points), Im into out[S ..),
+// the tetrad centred at centre (psi4.cu)
+cudaError_t launch_psi4(const GridView &g, const double *tile, const double centre[3], double *out, cudaStream_t s);
 // number of mixed second derivatives kept per point (d_xy, d_xz, d_yz of g~, alpha, beta, phi)
 constexpr int NMIX = 33;
 // largest patch edge whose halo'd tile of one field fits in the fill kernel's shared memory
