@@ -7,7 +7,8 @@ one JSON line per report. With --track, puncture trackers (Sec. "Particle
 tracers": tracers dropped at the black holes that move with the opposite
 shift by explicit Euler steps of the solver's dt, projected by trilinear
 interpolation) follow the punctures, and each report carries their
-positions.
+positions. With --psi4 R1 R2 ..., each report carries the modes of psi_4
+(appendix "psi_4 in ExaGRyPE") on spheres of those radii around the origin.
 
     python -m paper_2406_11626_gb300.evolve --workload binary --steps 500 --every 50 --precision mixed --track
 """
@@ -120,7 +121,7 @@ def puncture_positions(cfg):
 
 
 def run(workload="gauge_wave", steps=10, every=1, precision="fp64", launch="flat", log=None, track=False,
-        id_boxes=None, split=False):
+        id_boxes=None, split=False, psi4_radii=(), psi4_lmax=4):
     """Returns the reports: step 0 and every `every` steps up to `steps`,
     each {"step", "time", "L2_H", "L2_M", "max_H", "max_M", "nonfinite",
     "wall_s"}, for puncture workloads the same norms over the points at
@@ -129,7 +130,9 @@ def run(workload="gauge_wave", steps=10, every=1, precision="fp64", launch="flat
     replaces the binary's nested initial-data boxes (() for the single
     global solve). split=True adds the L2 norm of H near and away from the
     coarse-fine interfaces (interface_split) to every report of a puncture
-    workload."""
+    workload. psi4_radii: for each radius, the modes l <= psi4_lmax of psi_4
+    on the sphere of that radius around the origin (psi4.extract, the RHS
+    buffer as scratch) in every report, as "psi4": {radius: {"l,m": [re, im]}}."""
     import torch
     from . import ccz4 as C
     if steps < 0 or every < 1:
@@ -164,6 +167,12 @@ def run(workload="gauge_wave", steps=10, every=1, precision="fp64", launch="flat
         if tracker is not None:
             r["punctures"] = tracker.read()[0].tolist()
             centres = r["punctures"]
+        if psi4_radii:
+            from . import psi4 as PS
+            r["psi4"] = {}
+            for rad in psi4_radii:
+                md, _ = PS.extract(g, float(rad), "U", "RHS", lmax=psi4_lmax)
+                r["psi4"][str(rad)] = {"%d,%d" % k: [v.real, v.imag] for k, v in md.items()}
         if centres:
             # the norms without the points within r < 1 of a puncture (at its tracked position)
             ex = g.constraints_excluding(H.data_ptr(), M.data_ptr(), centres, 1.0)
@@ -211,9 +220,12 @@ def main(argv=None):
                     help="binary: initial data from the global solve alone, without the nested boxes")
     ap.add_argument("--interface-split", action="store_true",
                     help="puncture workloads: L2 of H near and away from the coarse-fine interfaces")
+    ap.add_argument("--psi4", type=float, nargs="*", default=[],
+                    help="radii of psi_4 extraction spheres around the origin (modes up to l = 4 per report)")
     a = ap.parse_args(argv)
     reps = run(a.workload, a.steps, a.every, a.precision, a.launch, log=lambda r: print(json.dumps(r), flush=True),
-               track=a.track, id_boxes=() if a.single_id_solve else None, split=a.interface_split)
+               track=a.track, id_boxes=() if a.single_id_solve else None, split=a.interface_split,
+               psi4_radii=tuple(a.psi4))
     return 0 if reps and reps[-1]["nonfinite"] == 0 else 1
 
 
