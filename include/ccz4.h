@@ -52,6 +52,8 @@
 #ifndef CCZ4_H
 #define CCZ4_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -135,6 +137,21 @@ typedef struct ccz4_grid ccz4_grid;
    descriptor and its ijk array are copied. Buffers start zeroed. On error
    *out is set to NULL. */
 ccz4_status ccz4_alloc_patches(const ccz4_grid_desc *desc, ccz4_grid **out);
+
+/* Device-memory allocator for the large buffers of grids created from now
+   on (the CCZ4_BUF_* state buffers, the halo tiles and the mixed
+   derivatives of ccz4_alloc_patches and ccz4_alloc_mesh), so that a host
+   framework's caching allocator can supply them: alloc(ctx, bytes, stream)
+   returns a device pointer (aligned to 256 bytes, like cudaMalloc) or NULL
+   on failure; dealloc(ctx, ptr, bytes, stream) releases one. stream is
+   NULL (the legacy default stream): the library synchronises the device
+   before it releases a grid. A grid keeps the allocator it was created with
+   until it is released. Both NULL restores cudaMalloc / cudaFree; one NULL
+   is CCZ4_ERR_INVALID. Process-wide; not to be called while another thread
+   creates a grid. Small tables and scratch keep cudaMalloc. */
+typedef void *(*ccz4_alloc_fn)(void *ctx, size_t bytes, void *stream);
+typedef void (*ccz4_dealloc_fn)(void *ctx, void *ptr, size_t bytes, void *stream);
+ccz4_status ccz4_set_allocator(ccz4_alloc_fn alloc, ccz4_dealloc_fn dealloc, void *ctx);
 
 /* Releases every buffer of the grid (synchronises the device). NULL is a no-op. */
 ccz4_status ccz4_free_patches(ccz4_grid *g);

@@ -91,6 +91,7 @@ def lib():
         "ccz4_set_tuning": [vp, ctypes.c_int, ctypes.c_int],
         "ccz4_point_index": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ll_p, vp],
         "ccz4_psi4": [vp, ctypes.c_int, ctypes.c_int, _dbl_p, vp],
+        "ccz4_set_allocator": [_ALLOC_FN, _DEALLOC_FN, vp],
         "ccz4_mesh_plan": [ctypes.POINTER(MeshDesc), ll_p, ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_int)],
     }
@@ -126,6 +127,35 @@ def lib():
     L.ccz4_last_error.argtypes = []
     _lib = L
     return L
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_DEALLOC_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_TORCH_ALLOCATOR = None   # the callbacks handed to the library, kept alive while it may call them
+
+
+def use_torch_allocator(enable=True):
+    """Grids created from now on take their large buffers (state buffers,
+    halo tiles, mixed derivatives) from PyTorch's caching allocator on the
+    current device (ccz4_set_allocator); enable=False restores cudaMalloc.
+    Grids keep the allocator they were created with."""
+    global _TORCH_ALLOCATOR
+    if not enable:
+        _check(lib().ccz4_set_allocator(_ALLOC_FN(), _DEALLOC_FN(), None))
+        return
+    import torch
+
+    def alloc(ctx, nbytes, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes))
+        except RuntimeError:
+            return None
+
+    def dealloc(ctx, ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(int(ptr))
+    cbs = (_ALLOC_FN(alloc), _DEALLOC_FN(dealloc))
+    _check(lib().ccz4_set_allocator(cbs[0], cbs[1], None))
+    _TORCH_ALLOCATOR = cbs
 
 
 def _check(code):

@@ -3,6 +3,7 @@
 // right-hand side, RK4 stages and constraint monitors. Every compute step
 // runs in the kernels of halo.cu, rhs.cu and constraints.cu.
 #include <stdarg.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -79,10 +80,32 @@ static ccz4_status check_params(const ccz4_params *P) {
   return CCZ4_OK;
 }
 
+// The allocator of the large buffers of grids created from now on (ccz4_set_allocator).
+static ccz4_alloc_fn g_alloc = nullptr;
+static ccz4_dealloc_fn g_dealloc = nullptr;
+static void *g_alloc_ctx = nullptr;
+
+extern "C" ccz4_status ccz4_set_allocator(ccz4_alloc_fn alloc, ccz4_dealloc_fn dealloc, void *ctx) {
+  if ((alloc == nullptr) != (dealloc == nullptr)) {
+    set_error("set_allocator: give both functions or neither");
+    return CCZ4_ERR_INVALID;
+  }
+  g_alloc = alloc;
+  g_dealloc = dealloc;
+  g_alloc_ctx = alloc ? ctx : nullptr;
+  return CCZ4_OK;
+}
+
 static void free_all(ccz4_grid *g) {
   if (g->step_exec) cudaGraphExecDestroy(g->step_exec);
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
-  for (int b = 0; b < 8; ++b) cudaFree(g->buf[b]);
+  for (int b = 0; b < 8; ++b) {
+    if (!g->buf[b]) continue;
+    if (g->dealloc)
+      g->dealloc(g->alloc_ctx, g->buf[b], sizeof(double) * (size_t)g->buf_len[b], nullptr);
+    else
+      cudaFree(g->buf[b]);
+  }
   cudaFree(g->d_ijk);
   cudaFree(g->d_owner);
   cudaFree(g->d_gcoord);
@@ -255,17 +278,35 @@ static ccz4_status create_grid(const ccz4_grid_desc *d, const std::vector<int> &
   const long long lens[8] = {state_len, state_len, state_len, state_len, state_len,
                              d->bc == CCZ4_BC_SOMMERFELD ? state_len : 0,
                              (long long)NV * v.n_patches * v.T3, (long long)NMIX * v.n_points};
+  g->alloc = g_alloc;
+  g->dealloc = g_dealloc;
+  g->alloc_ctx = g_alloc_ctx;
   for (int b = 0; b < 8; ++b) {
     g->buf_len[b] = lens[b];
     if (lens[b] == 0) continue;
-    cudaError_t e = cudaMalloc(&g->buf[b], sizeof(double) * (size_t)lens[b]);
-    if (e != cudaSuccess) {
-      set_error("cudaMalloc of %lld doubles failed: %s", lens[b], cudaGetErrorString(e));
-      cudaGetLastError();
-      free_all(g);
-      return CCZ4_ERR_NOMEM;
+    const size_t bytes = sizeof(double) * (size_t)lens[b];
+    if (g->alloc) {
+      g->buf[b] = (double *)g->alloc(g->alloc_ctx, bytes, nullptr);
+      if (!g->buf[b] || ((uintptr_t)g->buf[b] & 255u)) {
+        set_error("the allocator returned %s for %zu bytes", g->buf[b] ? "an unaligned pointer" : "NULL", bytes);
+        if (g->buf[b]) {
+          g->dealloc(g->alloc_ctx, g->buf[b], bytes, nullptr);
+          g->buf[b] = nullptr;
+        }
+        free_all(g);
+        return CCZ4_ERR_NOMEM;
+      }
+    } else {
+      cudaError_t e = cudaMalloc(&g->buf[b], bytes);
+      if (e != cudaSuccess) {
+        g->buf[b] = nullptr;
+        set_error("cudaMalloc of %lld doubles failed: %s", lens[b], cudaGetErrorString(e));
+        cudaGetLastError();
+        free_all(g);
+        return CCZ4_ERR_NOMEM;
+      }
     }
-    cudaMemset(g->buf[b], 0, sizeof(double) * (size_t)lens[b]);
+    cudaMemset(g->buf[b], 0, bytes);
   }
   g->red_blocks = constraint_blocks(v.n_points);
   bool ok = cudaMalloc(&g->d_ijk, sizeof(int) * 3 * (size_t)d->n_patches) == cudaSuccess &&

@@ -209,6 +209,9 @@ struct ccz4_grid {
   int n_rpar[CCZ4_MAX_LEVELS];
   unsigned long long *d_queue;  // work counter of the queue launch (allocated on first use)
   ccz4::GhostGeo *d_ghost_geo;  // [n_ghost] static geometry of the Sommerfeld ghost cells
+  ccz4_alloc_fn alloc;          // allocator of buf[] (NULL: cudaMalloc), kept for their release
+  ccz4_dealloc_fn dealloc;
+  void *alloc_ctx;
 };
 
 // Kernel launchers (one translation unit each).

@@ -91,3 +91,38 @@ def test_periodic_points_wrap_and_meshes_are_refused():
     with pytest.raises(C.CCZ4Error) as e:
         gm.point_index([[0, 0, 0]])
     assert e.value.code == C.ERR_INVALID
+
+
+def test_grids_can_take_their_buffers_from_torchs_allocator():
+    """ccz4_set_allocator with PyTorch's caching allocator: the grid's large
+    buffers show up in torch's accounting, a step gives the same state bit
+    for bit as a grid on cudaMalloc, and releasing the grid returns them."""
+    import torch
+    from paper_2406_11626_gb300 import ccz4 as C
+    cfg = I.single_puncture_config(p=6, n_side=3, half_width=1.5)
+    U, G = I.initial_state(cfg)
+    P = C.make_params(**cfg.params)
+    out = []
+    for use in (False, True):
+        C.use_torch_allocator(use)
+        try:
+            torch.cuda.synchronize()
+            before = torch.cuda.memory_allocated()
+            g = C.Grid.from_config(cfg)
+            grew = torch.cuda.memory_allocated() - before
+            g.upload(U, G)
+            g.upload(U, G, buf="INI")
+            g.step(P, cfg.dt, 2)
+            out.append(g.download("U"))
+            g.close()
+            torch.cuda.synchronize()
+            back = torch.cuda.memory_allocated() - before
+        finally:
+            C.use_torch_allocator(False)
+        if use:
+            n = cfg.n_patches * cfg.p ** 3
+            assert grew >= 25 * 6 * n * 8 and back == 0, (grew, back)
+        else:
+            assert grew == 0
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
