@@ -447,8 +447,15 @@ ccz4_status ccz4_mesh_plan(const ccz4_mesh_desc *desc, long long *n_interp, int 
    interior points of all levels; CCZ4_LAUNCH_QUEUE, a persistent launch
    sized to the resident blocks whose warps take 32-point items from a
    device work counter (reset by a memset node before each stage) until the
-   points of every level are done. Drops a captured step graph. */
-enum { CCZ4_LAUNCH_FLAT = 0, CCZ4_LAUNCH_QUEUE = 1 };
+   points of every level are done; CCZ4_LAUNCH_FUSED, for grids of 9^3
+   patches only (CCZ4_ERR_INVALID otherwise), runs each RK stage of
+   ccz4_step and ccz4_step_graph as one cooperative launch sized to the
+   resident blocks: the halo fill of every patch, a grid-wide barrier, the
+   interior points of all levels and the Sommerfeld ghost cells (the
+   restriction of a mesh stays a launch of its own; ccz4_rk_stage,
+   ccz4_fill_halos and the tuning shapes keep the separate kernels).
+   Drops a captured step graph. */
+enum { CCZ4_LAUNCH_FLAT = 0, CCZ4_LAUNCH_QUEUE = 1, CCZ4_LAUNCH_FUSED = 2 };
 ccz4_status ccz4_set_launch(ccz4_grid *g, int mode);
 
 /* ---- the first-order formulation and the second order with reconstruction ----

@@ -5,8 +5,9 @@ The cost of a step depends on
   (p+6)^3 points for p^3 interior ones: 8x at p = 6, 4.6x at p = 9, 3.4x
   at p = 12, 2.6x at p = 17, so small patches move more halo data while
   large ones give the halo fill fewer, larger blocks);
-- the launch of the stage kernel: a flat grid of one thread per point, or a
-  persistent launch whose warps take 32-point items from a device queue;
+- the launch of the stage kernel: a flat grid of one thread per point, a
+  persistent launch whose warps take 32-point items from a device queue,
+  or (p = 9) the fill and the stage in one cooperative launch per RK stage;
 - the stage kernel's launch shape: the default number of resident
   128-thread blocks per SM, one more (fewer registers per thread, more
   warps to hide latency, more register spills), one fewer, or (mixed
@@ -39,7 +40,7 @@ from . import inputs as I
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ccz4_gb300", "autotune.json")
 # the patch edges of the paper's patch-size study, plus the largest edge the fill kernel takes
 CANDIDATES = (6, 9, 12, 17, 18)
-LAUNCHES = ("flat", "queue")
+LAUNCHES = ("flat", "queue", "fused")
 STAGE_SHAPES = (0, 1, 2, 3)   # default, one resident block more, one fewer, two phases (mixed)
 FILL_SHAPES = (0, 1, 2, 3)    # 256 threads x 8 loads, 512 x 8, 256 x 16, 128 x 8
 WORKLOADS = ("puncture144", "puncture3level", "binary")
@@ -164,14 +165,15 @@ def tune(workload="puncture144", precision="fp64", n_target=144, h=1.0 / 9.0, ca
         return results[name]["point_stages_per_s"]
 
     # 1. patch edge and launch, shapes at their defaults
-    best = max(((p, l) for p in cfgs for l in launches), key=lambda q: run(q[0], q[1], 0, 0))
+    pairs = [(p, l) for p in cfgs for l in launches if l != "fused" or p == 9]
+    best = max(pairs, key=lambda q: run(q[0], q[1], 0, 0))
     p, launch = best
     # 2. the stage kernel's shape (the shapes apply to the flat launch)
     stage = 0
     if launch == "flat":
         stage = max(stage_shapes, key=lambda s: run(p, launch, s, 0))
-    # 3. the fill's shape
-    fill = max(fill_shapes, key=lambda f: run(p, launch, stage, f))
+    # 3. the fill's shape (the fused launch has its own)
+    fill = 0 if launch == "fused" else max(fill_shapes, key=lambda f: run(p, launch, stage, f))
     win = results[_name(p, launch, stage, fill)]
     entry = {"workload": workload, "precision": precision, "p": p, "n_side": win["n_side"], "launch": launch,
              "stage_shape": stage, "fill_shape": fill, "point_stages_per_s": win["point_stages_per_s"],
@@ -184,6 +186,20 @@ def tune(workload="puncture144", precision="fp64", n_target=144, h=1.0 / 9.0, ca
             json.dump(store, f, indent=1, sort_keys=True)
         os.replace(tmp, cache)
     return entry
+
+
+def compare(workload, precision, launches, p=9, steps=10, warmup=3, repeats=2, timer=None):
+    """Milliseconds per RK4 step of each launch on a workload at patch edge
+    p with the default shapes, timed `repeats` times in turn (graph replay,
+    CUDA events): {"workload", "precision", "p", "points", launch: [ms, ...]}."""
+    timer = timer or time_config
+    cfg = {c.p: c for c in workload_configs(workload, candidates=(p,))}[p]
+    row = {"workload": workload, "precision": precision, "p": p, "points": cfg.n_points}
+    for _ in range(repeats):
+        for launch in launches:
+            sec, _n = timer(cfg, precision, steps, warmup, launch, 0, 0)
+            row.setdefault(launch, []).append(round(sec * 1e3, 3))
+    return row
 
 
 def apply(grid, entry):
@@ -201,7 +217,16 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--cache", default=DEFAULT_CACHE)
     ap.add_argument("--refresh", action="store_true")
+    ap.add_argument("--compare", nargs="+", choices=LAUNCHES, metavar="LAUNCH",
+                    help="no tuning: time these launches at p = 9 with the default shapes")
+    ap.add_argument("--repeats", type=int, default=2)
     a = ap.parse_args(argv)
+    if a.compare:
+        for w in a.workload:
+            for prec in a.precision:
+                print(json.dumps(compare(w, prec, a.compare, steps=a.steps, warmup=a.warmup, repeats=a.repeats)),
+                      flush=True)
+        return 0
     for w in a.workload:
         for prec in a.precision:
             e = tune(w, prec, steps=a.steps, warmup=a.warmup, cache=a.cache, refresh=a.refresh)

@@ -305,8 +305,11 @@ class Grid:
         return cls(cfg.p, cfg.np, cfg.ijk(), cfg.origin, cfg.dx, cfg.bc, level=getattr(cfg, "level", None))
 
     def set_launch(self, mode):
-        """'flat' (default) or 'queue' launch of the stage kernel."""
-        _check(lib().ccz4_set_launch(self._h, {"flat": 0, "queue": 1}[mode] if isinstance(mode, str) else int(mode)))
+        """'flat' (default) or 'queue' launch of the stage kernel, or 'fused'
+        (9^3 patches): the fill and the stage of each RK stage of step and
+        step_graph in one cooperative launch."""
+        m = {"flat": 0, "queue": 1, "fused": 2}[mode] if isinstance(mode, str) else int(mode)
+        _check(lib().ccz4_set_launch(self._h, m))
 
     def set_tuning(self, stage_shape=0, fill_shape=0):
         """Launch shapes of the flat stage kernel (0 default, 1 one resident

@@ -141,6 +141,12 @@ __host__ __device__ constexpr int S6(int i, int j) {
 #else
 #define CCZ4_TLD __ldg
 #endif
+// Loads of the mixed derivatives: through the read-only path, except in a
+// translation unit whose kernel writes them itself before reading them (the
+// fused stage launch defines this as a coherent load before including).
+#ifndef CCZ4_MIX_LOAD
+#define CCZ4_MIX_LOAD __ldg
+#endif
 
 // Read-only view of the halo'd neighbourhood of one point.
 struct Nbhd {
@@ -160,14 +166,14 @@ struct Nbhd {
   }
   __host__ __device__ __forceinline__ double mixed(int slot) const {
 #ifdef __CUDA_ARCH__
-    return __ldg(mix + slot * ms);
+    return CCZ4_MIX_LOAD(mix + slot * ms);
 #else
     return mix[slot * ms];
 #endif
   }
   __host__ __device__ __forceinline__ float mixedf(int fslot) const {
 #ifdef __CUDA_ARCH__
-    return __ldg(mixf + fslot * msf);
+    return CCZ4_MIX_LOAD(mixf + fslot * msf);
 #else
     return mixf[fslot * msf];
 #endif

@@ -350,6 +350,7 @@ static ccz4_status create_grid(const ccz4_grid_desc *d, const std::vector<int> &
     }
   }
   prepare_fill_halos(v.p);
+  if (v.p == 9) prepare_fused();
   if (mesh) prepare_shaped_mesh();
   else prepare_shaped_uniform();
   cudaError_t e = cudaDeviceSynchronize();
@@ -584,10 +585,30 @@ static ccz4_status stage_kernel(ccz4_grid *g, const ccz4_params *P, int stage, d
   return CCZ4_OK;
 }
 
+// One RK4 stage of a step: the halo fill and the stage kernel as two
+// launches, or (CCZ4_LAUNCH_FUSED) both in one cooperative launch; the
+// restriction after stage 3 stays a launch of its own.
+static ccz4_status step_stage(ccz4_grid *g, const ccz4_params *P, int stage, double dt, cudaStream_t s) {
+  if (!g->fused) {
+    CUDA_TRY(launch_fill_halos(g->v, g->buf[kStageIn[stage]], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], s,
+                               P->precision == CCZ4_PREC_MIXED));
+    return stage_kernel(g, P, stage, dt, s);
+  }
+  CUDA_TRY(launch_fused_stage(g->v, *P, stage, dt, g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX],
+                              g->buf[kStageIn[stage]], ini_ptr(g), g->buf[CCZ4_BUF_U], g->buf[CCZ4_BUF_ACC],
+                              g->buf[kStageOut[stage]], s));
+  if (stage == 3 && g->v.n_levels > 1) return restrict_levels(g, g->buf[kStageOut[stage]], s);
+  return CCZ4_OK;
+}
+
 extern "C" ccz4_status ccz4_set_launch(ccz4_grid *g, int mode) {
   if (check_grid(g)) return CCZ4_ERR_INVALID;
-  if (mode != CCZ4_LAUNCH_FLAT && mode != CCZ4_LAUNCH_QUEUE) {
+  if (mode != CCZ4_LAUNCH_FLAT && mode != CCZ4_LAUNCH_QUEUE && mode != CCZ4_LAUNCH_FUSED) {
     set_error("set_launch: unknown launch mode %d", mode);
+    return CCZ4_ERR_INVALID;
+  }
+  if (mode == CCZ4_LAUNCH_FUSED && g->v.p != 9) {
+    set_error("set_launch: the fused stage launch is compiled for 9^3 patches (this grid has %d^3)", g->v.p);
     return CCZ4_ERR_INVALID;
   }
   if (mode == CCZ4_LAUNCH_QUEUE && !g->d_queue) {
@@ -597,11 +618,13 @@ extern "C" ccz4_status ccz4_set_launch(ccz4_grid *g, int mode) {
     }
   }
   unsigned long long *q = mode == CCZ4_LAUNCH_QUEUE ? g->d_queue : nullptr;
-  if (q != g->v.queue && g->step_exec) {
+  const int fused = mode == CCZ4_LAUNCH_FUSED;
+  if ((q != g->v.queue || fused != g->fused) && g->step_exec) {
     cudaGraphExecDestroy(g->step_exec);  // the captured step used the other launch
     g->step_exec = nullptr;
   }
   g->v.queue = q;
+  g->fused = fused;
   return CCZ4_OK;
 }
 
@@ -657,9 +680,7 @@ extern "C" ccz4_status ccz4_step(ccz4_grid *g, const ccz4_params *P, double dt, 
   cudaStream_t s = (cudaStream_t)stream;
   for (int n = 0; n < n_steps; ++n)
     for (int st = 0; st < 4; ++st) {
-      CUDA_TRY(launch_fill_halos(g->v, g->buf[kStageIn[st]], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX], s,
-                                 P->precision == CCZ4_PREC_MIXED));
-      ccz4_status r = stage_kernel(g, P, st, dt, s);
+      ccz4_status r = step_stage(g, P, st, dt, s);
       if (r != CCZ4_OK) return r;
     }
   return CCZ4_OK;
@@ -677,16 +698,7 @@ static ccz4_status capture_step(ccz4_grid *g, const ccz4_params *P, double dt) {
   cudaGraph_t graph = nullptr;
   CUDA_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
   ccz4_status st = CCZ4_OK;
-  for (int s = 0; s < 4 && st == CCZ4_OK; ++s) {
-    cudaError_t e = launch_fill_halos(g->v, g->buf[kStageIn[s]], g->buf[CCZ4_BUF_TILE], g->buf[CCZ4_BUF_MIX],
-                                      g->cap_stream, P->precision == CCZ4_PREC_MIXED);
-    if (e != cudaSuccess) {
-      set_error("capture: halo fill launch failed: %s", cudaGetErrorString(e));
-      st = CCZ4_ERR_CUDA;
-      break;
-    }
-    st = stage_kernel(g, P, s, dt, g->cap_stream);
-  }
+  for (int s = 0; s < 4 && st == CCZ4_OK; ++s) st = step_stage(g, P, s, dt, g->cap_stream);
   cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
   if (st != CCZ4_OK) {
     if (graph) cudaGraphDestroy(graph);

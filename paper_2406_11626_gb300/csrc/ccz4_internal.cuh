@@ -212,6 +212,7 @@ struct ccz4_grid {
   ccz4_alloc_fn alloc;          // allocator of buf[] (NULL: cudaMalloc), kept for their release
   ccz4_dealloc_fn dealloc;
   void *alloc_ctx;
+  int fused;                    // CCZ4_LAUNCH_FUSED: one cooperative launch per RK stage (p = 9)
 };
 
 // Kernel launchers (one translation unit each).
@@ -222,6 +223,14 @@ cudaError_t launch_ghost_setup(const GridView &g, GhostGeo *out, cudaStream_t s)
 cudaError_t launch_fill_halos(const GridView &g, const double *src, double *tile, double *mix, cudaStream_t s,
                               bool fp32_weights = false);
 cudaError_t prepare_fill_halos(int p);
+// One cooperative launch per RK stage (rhs_fused.cu): the halo fill of every
+// patch, a grid-wide barrier, the interior points and the Sommerfeld ghost
+// cells; p = 9 only. prepare_fused raises its shared-memory limit (once per
+// grid, outside any stream capture).
+cudaError_t prepare_fused();
+cudaError_t launch_fused_stage(const GridView &g, const ccz4_params &P, int stage, double dt, double *tile,
+                               double *mix, const double *in, const double *ini, const double *U, double *acc,
+                               double *out, cudaStream_t s);
 // psi_4 at every interior point from the halo'd tiles: Re into out[0 .. n_points), Im into out[S ..),
 // the tetrad centred at centre (psi4.cu)
 cudaError_t launch_psi4(const GridView &g, const double *tile, const double centre[3], double *out, cudaStream_t s);

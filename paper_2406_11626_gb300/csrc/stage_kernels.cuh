@@ -315,11 +315,9 @@ __global__ void __launch_bounds__(128, (StageBlocks<R, SHAPE>::value)) interior_
 // ODE (Eq. exa_sommerfeld_inter) with the cell's static geometry from
 // g.ghost_geo, and the same stage update, no enforcement, FP64.
 template <int MODE>
-__global__ void __launch_bounds__(256) ghost_kernel(GridView g, ccz4_params P, const double *__restrict__ in,
-                                                    const double *__restrict__ ini, StageArgs a) {
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int v = blockIdx.y;
-  if (id >= g.n_ghost) return;
+__device__ __forceinline__ void ghost_point(const GridView &g, const ccz4_params &P, const double *__restrict__ in,
+                                            const double *__restrict__ ini, const StageArgs &a, long long id,
+                                            int v) {
   const GhostGeo *gg = g.ghost_geo + id;
   const long long sn = __ldg(&gg->sn);
   if (sn < 0) return;
@@ -342,6 +340,13 @@ __global__ void __launch_bounds__(256) ghost_kernel(GridView g, ccz4_params P, c
   const double un = rk_combine<(MODE < 0 ? 0 : MODE), double>(a.U[o], acc, k, a.dt);
   if (MODE < 3) a.acc[o] = acc;
   a.out[o] = un;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) ghost_kernel(GridView g, ccz4_params P, const double *__restrict__ in,
+                                                    const double *__restrict__ ini, StageArgs a) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id < g.n_ghost) ghost_point<MODE>(g, P, in, ini, a, id, blockIdx.y);
 }
 
 StencilCoef<double> coefs(double dx, const ccz4_params &P) {

@@ -214,7 +214,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--every", type=int, default=1)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--launch", default="flat", choices=["flat", "queue"])
+    ap.add_argument("--launch", default="flat", choices=["flat", "queue", "fused"])
     ap.add_argument("--track", action="store_true", help="follow the punctures with puncture trackers")
     ap.add_argument("--single-id-solve", action="store_true",
                     help="binary: initial data from the global solve alone, without the nested boxes")

@@ -47,15 +47,39 @@ def test_tune_descends_each_coordinate_and_caches(tmp_path):
     r = A.tune("puncture144", timer=_fake(calls), key_extra="fake-gpu", cache=cache)
     # the queue launch wins the first coordinate, so the stage shape (a flat-launch knob) is not swept
     assert (r["p"], r["launch"], r["stage_shape"], r["fill_shape"]) == (12, "queue", 0, 1)
-    assert len(calls) == 10 + 3     # 5 edges x 2 launches, then 3 more fill shapes
+    # 5 edges x flat and queue, the fused launch at p = 9 only, then 3 more fill shapes
+    assert len(calls) == 11 + 3
+    assert sum(1 for c in calls if c[1] == "fused") == 1 and (9, "fused", 0, 0) in calls
     assert A.tune("puncture144", timer=_fake(calls), key_extra="fake-gpu", cache=cache) == r
-    assert len(calls) == 13         # served from the cache
+    assert len(calls) == 14         # served from the cache
     r2 = A.tune("puncture144", timer=_fake(calls), key_extra="fake-gpu", cache=cache, launches=("flat",))
     assert (r2["p"], r2["launch"], r2["stage_shape"], r2["fill_shape"]) == (12, "flat", 2, 1)
-    assert len(calls) == 13 + 5 + 3 + 3     # 5 edges, 3 more stage shapes, 3 more fill shapes
+    assert len(calls) == 14 + 5 + 3 + 3     # 5 edges, 3 more stage shapes, 3 more fill shapes
     A.tune("puncture144", timer=_fake(calls), key_extra="fake-gpu", cache=cache, refresh=True)
-    assert len(calls) == 24 + 13
+    assert len(calls) == 25 + 14
     assert len(json.load(open(cache))) == 2     # one entry per key
+
+
+def test_tune_fused_launch_sweeps_no_shapes(tmp_path):
+    calls = []
+
+    def fake(cfg, precision, steps, warmup, launch, stage_shape, fill_shape):
+        calls.append((cfg.p, launch, stage_shape, fill_shape))
+        c = 0.7 if launch == "fused" else 1.0
+        return cfg.n_points * c * 1e-9, cfg.n_points
+
+    r = A.tune("puncture144", timer=fake, key_extra="fake-gpu", cache=str(tmp_path / "t.json"))
+    # the fused launch wins at p = 9; it has its own shapes, so none is swept after it
+    assert (r["p"], r["launch"], r["stage_shape"], r["fill_shape"]) == (9, "fused", 0, 0)
+    assert len(calls) == 11
+
+
+def test_compare_times_each_launch_in_turn():
+    calls = []
+    row = A.compare("puncture144", "mixed", ("flat", "fused"), steps=4, warmup=1, repeats=2, timer=_fake(calls))
+    assert [c[1] for c in calls] == ["flat", "fused", "flat", "fused"]
+    assert all(c[0] == 9 and c[2:] == (0, 0) for c in calls)
+    assert row["p"] == 9 and row["points"] == 144 ** 3 and len(row["flat"]) == len(row["fused"]) == 2
 
 
 def test_mesh_workloads_keep_their_patch_edge(tmp_path):

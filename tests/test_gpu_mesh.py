@@ -316,7 +316,9 @@ def test_queue_launch_is_bit_identical_to_flat(mesh):
 def test_fixed_edge_stage_kernel_is_bit_identical_to_the_general_one(prec, mesh):
     """Grids of 9^3 patches take the stage kernel compiled for that edge on
     the flat default launch; the queue launch and the other launch shapes
-    take the general one. Both compute the same steps bit for bit."""
+    take the general one; the fused launch runs the fill and the stage of
+    that edge in one cooperative kernel. All compute the same steps bit for
+    bit."""
     from paper_2406_11626_gb300 import ccz4 as C
     if mesh:
         cfg = I.multilevel_puncture_config(p=9, n_side=4, half_width=2.0, boxes=[((1, 1, 1), (3, 3, 3))])
@@ -325,7 +327,7 @@ def test_fixed_edge_stage_kernel_is_bit_identical_to_the_general_one(prec, mesh)
     U, G = I.initial_state(cfg)
     P = C.make_params(**cfg.params, precision=prec)
     out = []
-    for launch, shape in (("flat", 0), ("queue", 0), ("flat", 1)):
+    for launch, shape in (("flat", 0), ("queue", 0), ("flat", 1), ("fused", 0)):
         g = C.Grid.from_config(cfg)
         g.set_launch(launch)
         g.set_tuning(shape, 0)
@@ -395,3 +397,37 @@ def test_binary_mixed_run_tracks_fp64():
         for q in (0, 1):
             a, b = res["mixed"][k][q], res["fp64"][k][q]
             assert 0.5 < a / b < 2.0 and abs(a / b - 1.0) < 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("graph", [False, True])
+def test_fused_stage_launch_with_more_patches_than_blocks_is_bit_identical(prec, graph):
+    """The fused launch on 12^3 patches of 9^3 (more patches than resident
+    blocks, so each block fills several, and more 32-point items than warps)
+    with Sommerfeld ghost cells: plain steps and a replayed step graph equal
+    the separate fill and stage launches bit for bit."""
+    from paper_2406_11626_gb300 import ccz4 as C
+    cfg = I.single_puncture_config(p=9, n_side=12, half_width=6.0)
+    U, G = I.initial_state(cfg)
+    P = C.make_params(**cfg.params, precision=prec)
+    out = []
+    for launch in ("flat", "fused"):
+        g = C.Grid.from_config(cfg)
+        g.set_launch(launch)
+        g.upload(U, G)
+        g.upload(U, G, buf="INI")
+        (g.step_graph if graph else g.step)(P, cfg.dt, 3)
+        out.append(g.download("U"))
+        g.close()
+    np.testing.assert_array_equal(out[1][0], out[0][0])
+    np.testing.assert_array_equal(out[1][1], out[0][1])
+
+
+def test_fused_stage_launch_needs_9_cubed_patches():
+    from paper_2406_11626_gb300 import ccz4 as C
+    cfg = I.single_puncture_config(p=6, n_side=4, half_width=2.0)
+    g = C.Grid.from_config(cfg)
+    with pytest.raises(C.CCZ4Error, match="9\\^3"):
+        g.set_launch("fused")
+    g.set_launch("flat")
+    g.close()
