@@ -124,9 +124,13 @@ __host__ __device__ __forceinline__ double cvt<double, float>(const float &x) {
 #endif
 }
 
-// index of the symmetric pair (i, j) among xx, xy, xz, yy, yz, zz
+// index of the symmetric pair (i, j) among xx, xy, xz, yy, yz, zz. Written
+// without recursion: the index must fold to a constant as soon as the
+// loops around it are unrolled, or the arrays it indexes stay in local
+// memory (a recursive form left the mixed stage kernel a 624-byte stack
+// frame of such arrays).
 __host__ __device__ constexpr int S6(int i, int j) {
-  return i > j ? S6(j, i) : (i == 0 ? j : (i == 1 ? 2 + j : 5));
+  return i > j ? (j == 0 ? i : (j == 1 ? 2 + i : 5)) : (i == 0 ? j : (i == 1 ? 2 + j : 5));
 }
 
 // Tile loads through Nbhd (the stage kernel and the constraint monitors):
