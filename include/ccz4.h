@@ -542,7 +542,9 @@ ccz4_status ccz4_tracers_step(ccz4_tracers *t, int buf, double dt, void *stream)
 ccz4_status ccz4_tracers_read(ccz4_tracers *t, double *pos, double *values, void *stream);
 ccz4_status ccz4_tracers_free(ccz4_tracers *t);
 
-/* Launch shapes (a tuning choice; results are identical): the flat stage
+/* Launch shapes (a tuning choice; results are identical, but for SPLIT in
+   the mixed precision, whose FP32 algebra may round a few intermediate
+   values differently, within 1e-8 of a field's largest value): the flat stage
    kernel asks the default number of resident 128-thread blocks per SM
    (CCZ4_STAGE_SHAPE_DEFAULT: 4 in FP64, 3 in the mixed precision), one
    more (MORE_BLOCKS, fewer registers per thread) or one fewer

