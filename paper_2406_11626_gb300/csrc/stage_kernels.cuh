@@ -46,6 +46,14 @@
 #define CCZ4_SMEM_SPILL 1
 #endif
 
+// The last stage's enforcement reads the new g~ and A~ back from the output
+// (written there as soon as they are known, by the same thread) instead of
+// holding them in registers through the rest of the right-hand side, which
+// frees 12 registers for the algebra. 0: hold them.
+#ifndef CCZ4_ENFORCE_RELOAD
+#define CCZ4_ENFORCE_RELOAD 1
+#endif
+
 // State, accumulator and output of the stage update: streaming
 // (evict-first) loads and stores, each value is touched once, which leaves
 // L2 to the kernel's register spills; 0 for plain ones.
@@ -155,11 +163,11 @@ struct StageSink {
     double acc = MODE == 0 ? 0.0 : st_ld(a.acc + o);
     const double un = rk_combine<(MODE < 0 ? 0 : MODE), double>(st_ld(a.U + o), acc, k, a.dt);
     if (MODE < 3) st_st(a.acc + o, acc);
-    if (MODE == 3 && v >= GXX && v <= GZZ) {
+    if (!CCZ4_ENFORCE_RELOAD && MODE == 3 && v >= GXX && v <= GZZ) {
       ug[v - GXX] = un;
       return;
     }
-    if (MODE == 3 && v >= AXX && v <= AZZ) {
+    if (!CCZ4_ENFORCE_RELOAD && MODE == 3 && v >= AXX && v <= AZZ) {
       uA[v - AXX] = un;
       return;
     }
@@ -167,6 +175,13 @@ struct StageSink {
   }
   __device__ __forceinline__ void finish() {
     if (MODE != 3) return;
+    if (CCZ4_ENFORCE_RELOAD) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        ug[c] = st_ld(a.out + (GXX + c) * g.S + i);
+        uA[c] = st_ld(a.out + (AXX + c) * g.S + i);
+      }
+    }
     enforce_point<double>(ug, uA);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
