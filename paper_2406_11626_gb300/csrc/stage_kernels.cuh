@@ -357,11 +357,15 @@ __device__ __forceinline__ void ghost_point(const GridView &g, const ccz4_params
   a.out[o] = un;
 }
 
+// One thread per ghost cell, all fields: the cell's geometry is read once
+// and the 25 fields' loads are independent (consecutive cells, coalesced).
 template <int MODE>
 __global__ void __launch_bounds__(256) ghost_kernel(GridView g, ccz4_params P, const double *__restrict__ in,
                                                     const double *__restrict__ ini, StageArgs a) {
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id < g.n_ghost) ghost_point<MODE>(g, P, in, ini, a, id, blockIdx.y);
+  if (id >= g.n_ghost) return;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) ghost_point<MODE>(g, P, in, ini, a, id, v);
 }
 
 StencilCoef<double> coefs(double dx, const ccz4_params &P) {
@@ -419,8 +423,7 @@ cudaError_t launch_mode(const GridView &g, const ccz4_params &P, const double *t
     if (e != cudaSuccess) return e;
   }
   if (g.n_ghost > 0) {
-    const dim3 grid((unsigned)((g.n_ghost + 255) / 256), NV);
-    ghost_kernel<MODE><<<grid, 256, 0, s>>>(g, P, in, ini, a);
+    ghost_kernel<MODE><<<(unsigned)((g.n_ghost + 255) / 256), 256, 0, s>>>(g, P, in, ini, a);
     return cudaGetLastError();
   }
   return cudaSuccess;
